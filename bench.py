@@ -1,0 +1,378 @@
+"""Benchmark: amplitudes/s of the batched Berends-Giele recursion, n = 8
+gluons, d = D_s = 6, over F_p (p = 2^31 - 19) and complex FP64.
+
+One step = one bg_eval over a batch of E synthetic points (all steps of the
+hot path run inside that one kernel launch).  Inputs are resident in HBM
+before the timed region and larger than L2 (E = 2^22: 1.6 GB for F_p, 6.4 GB
+for C64), so no L2 flush is needed between steps.  Timing: W warm-up steps,
+then K steps bracketed by barrier + synchronize, timed with CUDA events on
+the launching stream; max over ranks.  The printed JSON line's headline
+``value`` is F_p amplitudes/s; the complex FP64 leg is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): each rank evaluates its own independent batch (weak
+scaling, no data-path collective); the process group only provides the
+barrier and the max over ranks of the elapsed time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2502_07060_gb300 import inputs as G  # noqa: E402
+
+N_LEG, D, DS = 8, 6, 6
+P = G.P_DEFAULT
+METRIC = "amplitudes/s for n=8 gluons, d=6 (F_p, C64); serving p50/p99 vs plain launches"
+
+
+def literal_tally(n, d, Ds):
+    """Field multiplications and additions of the literal recursion at
+    (n, d, D_s) (the oracle's tally, a closed combinatorial formula)."""
+    from math import comb
+    mul = comb(n, 3) * (3 * Ds + 3 * d) + comb(n, 4) * 6 * Ds + (comb(n, 2) - n) * (d + Ds) + Ds
+    add = None
+    return mul, add
+
+
+def kernel_mults(n, d, Ds):
+    """Field multiplications the CUDA kernel performs per amplitude in its
+    regrouped form (dots shared between V3 and V4, one scalar-vector product
+    per sub-current, batched inversion), input conversion included."""
+    N = n - 1
+    tot = 0
+    for m in range(2, N + 1):
+        ranges = N - m + 1
+        per = (m - 1) * Ds                       # adjacent dots
+        per += (m - 1) * 2 * d                   # P_A.J_B and P_B.J_A
+        per += (m - 1) * d                       # momentum part of V3
+        per += (m - 1) * 2 * Ds                  # prefix and suffix scalar-vector products
+        per += (m - 1) * (m - 2) // 2 * 2 * Ds   # gap dots and inner scalar-vector products
+        if m < N:
+            per += Ds + d                        # J = R / P^2 and P^2
+        tot += ranges * per
+    ns = N * (N + 1) // 2 - N - 1
+    tot += 3 * ns + 45                           # batched inverse + one Fermat power (~45)
+    tot += Ds                                    # final contraction
+    tot += N * d + n * Ds                        # conversion to Montgomery form
+    return tot
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (barrier and max over ranks only)
+# --------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def max_over_ranks(x, dist, device):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on the host cores
+# --------------------------------------------------------------------------
+
+def cpu_baseline(field, target_s=10.0):
+    from oracle import coracle
+    threads = coracle.max_threads()
+    m = 1 << 12
+    while True:
+        if field == "fp":
+            k, e = G.fp_batch(777, m, N_LEG, D, DS, P, 0)
+            t0 = time.perf_counter()
+            coracle.amp_fp(k, e, P, 0)
+        else:
+            k, e = G.c64_batch(777, m, N_LEG, D, DS, 0)
+            t0 = time.perf_counter()
+            coracle.amp_c64(k, e, 0)
+        dt = time.perf_counter() - t0
+        if dt >= target_s / 4 or m >= (1 << 20):
+            break
+        m = int(m * min(16.0, max(2.0, target_s / max(dt, 1e-3))))
+        m = 1 << max(12, min(20, m.bit_length() - 1))
+    return {"value": m / dt, "unit": "amplitudes/s", "cores": threads, "kind": "oracle",
+            "sample": f"{m} points of the n=8 d=D_s=6 {field} workload, C oracle (gcc -O2, OpenMP, "
+                      f"one point per iteration), {dt:.2f} s"}
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def time_steps(fn, steps, warmup, stream, dist, device):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    end.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = start.elapsed_time(end)
+    return max_over_ranks(ms, dist, device)
+
+
+def run_field(field, E, steps, warmup, rank, dist, device, seed):
+    import torch
+    from paper_2502_07060_gb300 import bg
+    if field == "fp":
+        k, e = G.fp_batch(seed, E, N_LEG, D, DS, P, 0)
+        plan = bg.Plan(N_LEG, D, DS, bg.FIELD_FP, P, bg.MOSTLY_MINUS)
+        hk = torch.from_numpy(k.view(np.int32))
+        he = torch.from_numpy(e.view(np.int32))
+    else:
+        k, e = G.c64_batch(seed, E, N_LEG, D, DS, 0)
+        plan = bg.Plan(N_LEG, D, DS, bg.FIELD_C64, 0, bg.MOSTLY_MINUS)
+        hk = torch.from_numpy(k)
+        he = torch.from_numpy(e)
+    del k, e
+    dk = hk.to(device)
+    de = he.to(device)
+    out = torch.empty(E, dtype=dk.dtype, device=device)
+    st = torch.empty(E, dtype=torch.uint8, device=device)
+    ws = plan.workspace(E, device)
+    stream = torch.cuda.current_stream(device)
+
+    def step():
+        plan.eval(dk, de, out=out, status=st, workspace=ws, stream=stream)
+
+    with ClockSampler(device.index if device.index is not None else 0) as clk:
+        ms = time_steps(step, steps, warmup, stream, dist, device)
+    clocks = clk.summary()
+
+    # end to end through the public API: pinned host inputs -> device ->
+    # kernel -> host result, every step
+    pk = hk.pin_memory()
+    pe = he.pin_memory()
+    hout = torch.empty(E, dtype=dk.dtype).pin_memory()
+    hst = torch.empty(E, dtype=torch.uint8).pin_memory()
+
+    def e2e_step():
+        dk.copy_(pk, non_blocking=True)
+        de.copy_(pe, non_blocking=True)
+        plan.eval(dk, de, out=out, status=st, workspace=ws, stream=stream)
+        hout.copy_(out, non_blocking=True)
+        hst.copy_(st, non_blocking=True)
+
+    e2e_steps = max(3, min(steps, 20))
+    ms_e2e = time_steps(e2e_step, e2e_steps, 2, stream, dist, device)
+    res = {
+        "ms_per_step": ms / steps,
+        "value_per_rank": E / (ms / steps / 1e3),
+        "e2e_ms_per_step": ms_e2e / e2e_steps,
+        "h2d_bytes": pk.numel() * pk.element_size() + pe.numel() * pe.element_size(),
+        "d2h_bytes": hout.numel() * hout.element_size() + hst.numel(),
+        "clocks": clocks,
+        "plan": plan.describe(),
+    }
+    del dk, de, out, st, ws
+    torch.cuda.empty_cache()
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--log2-points", type=int, default=22)
+    ap.add_argument("--log2-points-c64", type=int, default=22)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_env()
+    E = 1 << args.log2_points
+    Ec = 1 << args.log2_points_c64
+    config = {"workload": f"n={N_LEG} gluons, d=D_s={D}, mostly-minus metric, F_p p=2^31-19 and "
+                          f"complex FP64, seeded on-shell points, one transverse state per leg",
+              "points_per_step_per_gpu": E, "points_per_step_per_gpu_c64": Ec,
+              "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = args.steps
+        t_all = 0.0
+        done = 0
+        from oracle import coracle
+        m = 1 << 14
+        k, e = G.fp_batch(4242, m, N_LEG, D, DS, P, 0)
+        for _ in range(min(args.warmup, 1)):
+            coracle.amp_fp(k[:1024], e[:1024], P, 0)
+        for _ in range(min(steps, 10)):
+            t0 = time.perf_counter()
+            coracle.amp_fp(k, e, P, 0)
+            t_all += time.perf_counter() - t0
+            done += m
+        val = done / t_all
+        cores = coracle.max_threads()
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "amplitudes/s",
+                "n_gpus": world, "steps": min(steps, 10), "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_all / min(steps, 10), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": dict(config, reference_points_per_step=m),
+                "cpu_baseline": {"value": val, "unit": "amplitudes/s", "cores": cores,
+                                 "kind": "oracle",
+                                 "sample": f"{m} points per step of the F_p workload, C oracle"},
+                "e2e": {"value": val, "unit": "amplitudes/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+    fp = run_field("fp", E, args.steps, args.warmup, rank, dist, device, 1000 + rank)
+    c64_steps = max(3, args.steps // 5)
+    c64 = run_field("c64", Ec, c64_steps, args.warmup, rank, dist, device, 2000 + rank)
+
+    value = world * fp["value_per_rank"]
+    tally, _ = literal_tally(N_LEG, D, DS)
+    peaks = read_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0) or 2070.0
+    n_sm = torch.cuda.get_device_properties(device).multi_processor_count
+    # F_p roofline: integer-multiply pipe, 64 IMAD per SM per clock, three
+    # multiply instructions per Montgomery multiplication.
+    peak_mulmod = n_sm * 64 * sm_max * 1e6 / 3
+    achieved = fp["value_per_rank"] * tally
+    c64_flops = 6 * tally + 2 * 5348
+    peak_fp64 = n_sm * 2 * 2 * sm_max * 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": fp["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": config,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_mulmod,
+                     "unit": "field multiplications/s (F_p, literal tally)",
+                     "frac": achieved / peak_mulmod, "traffic": None,
+                     "ops_per_unit": tally, "kernel_ops_per_unit": kernel_mults(N_LEG, D, DS),
+                     "peak_derivation": f"{n_sm} SMs x 64 IMAD/clk x {sm_max:.0f} MHz / 3 IMAD per "
+                                        f"Montgomery multiplication"},
+        "c64": {"value": world * c64["value_per_rank"], "unit": "amplitudes/s",
+                "ms_per_step": c64["ms_per_step"], "points_per_step": Ec, "steps": c64_steps,
+                "dtype": "f64",
+                "roofline": {"bound": "alu", "achieved": c64["value_per_rank"] * c64_flops,
+                             "peak": peak_fp64, "unit": "FP64 FLOP/s (literal tally)",
+                             "frac": c64["value_per_rank"] * c64_flops / peak_fp64,
+                             "peak_derivation": f"{n_sm} SMs x 2 DFMA/clk x 2 x {sm_max:.0f} MHz"},
+                "e2e_value": world * Ec / (c64["e2e_ms_per_step"] / 1e3),
+                "clocks": c64["clocks"], "plan": c64["plan"]},
+        "e2e": {"value": world * E / (fp["e2e_ms_per_step"] / 1e3), "unit": "amplitudes/s",
+                "h2d_bytes_per_step": fp["h2d_bytes"], "d2h_bytes_per_step": fp["d2h_bytes"]},
+        "clocks": fp["clocks"],
+        "gpu_launches": args.steps,
+        "plan": fp["plan"],
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline("fp")
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

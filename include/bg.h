@@ -1,0 +1,151 @@
+/*
+ * bg.h -- C-ABI of libbg.so: batched Berends-Giele recursion for
+ * colour-ordered n-gluon tree amplitudes on GB300 (sm_103a).
+ *
+ * Method: arXiv:2502.07060.  Sec. 2.2 defines the off-shell currents
+ *   J(i,j) = (-i / P_{i,j}^2) [ sum V3(P_A,P_B) J_A J_B + sum V4 J_A J_B J_C ],
+ * the three- and four-gluon vertices V3, V4 and the range momenta
+ * P_{i,j} = k_i + ... + k_j; the amplitude is the (n-1)-leg current with its
+ * propagator removed, contracted with the last polarisation.  Sec. 2.3 fixes
+ * the d-dimensional setting (momenta in d dimensions, states embedded by zero
+ * padding, mostly-minus metric); Sec. 3 the number types (F_p with p < 2^31,
+ * complex double) and the parallelisation along the event dimension; Sec. 3.1
+ * the alternating metric diag(1,-1,1,-1,...).
+ *
+ * Value returned for each point and state assignment:
+ *     A = eps_n . R_top,     R_top = i^-1 x (bracket of the (n-1)-leg current)
+ * i.e. the paper's amplitude divided by i (no factor of i is needed, so the
+ * same code serves p = 3 mod 4).  With the states eps1/eps2 of Sec. 2.3,
+ * A(1-,2-,3+..n+) = (-1)^n 2^(n-3) <12>^4 / (<12><23>...<n1>).
+ *
+ * Conventions: all momenta outgoing, sum_i k_i = 0; array leg index l <-> leg
+ * l+1 in colour order; leg n (index n-1) is the contracted leg.  F_p values are
+ * canonical residues in [0, p) stored as uint32; complex values are FP64
+ * (re, im) pairs (16 bytes, CUDA double2 / torch.complex128).
+ *
+ * Ownership: the caller owns every buffer passed to bg_eval; bg_eval allocates
+ * nothing.  A plan holds host memory and, when n_assign > 1, one small device
+ * copy of the state-assignment table, made on the device current at
+ * bg_plan_create and freed by bg_plan_destroy.
+ *
+ * Errors: every entry point returns a bg_status.  Argument errors are detected
+ * on the host before any launch (BG_ERR_INVALID_ARG / BG_ERR_UNSUPPORTED) and
+ * leave all buffers untouched; CUDA launch errors return BG_ERR_CUDA.
+ * Data-dependent failures never trap: a singular propagator (P_{i,j}^2 = 0 for
+ * an internal range) sets status[e] = 1 and out = 0 for that point.
+ * bg_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef BG_H
+#define BG_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BG_VERSION 1
+
+typedef enum {
+    BG_OK = 0,
+    BG_ERR_INVALID_ARG = 1,   /* null pointer, size or parameter out of range  */
+    BG_ERR_UNSUPPORTED = 2,   /* valid request this build has no kernel for    */
+    BG_ERR_NOMEM = 3,         /* host or device allocation failed (plan only)  */
+    BG_ERR_CUDA = 4,          /* CUDA runtime error (launch, device mismatch)  */
+    BG_ERR_TIMEOUT = 5,       /* reserved for serving waits                    */
+    BG_ERR_BUSY = 6           /* reserved for serving admission                */
+} bg_status;
+
+typedef enum {
+    BG_FIELD_C64 = 0,         /* complex FP64 (Sec. 3, double precision)        */
+    BG_FIELD_FP = 1           /* prime field F_p, odd prime p < 2^31 (Sec. 3)  */
+} bg_field;
+
+typedef enum {
+    BG_METRIC_MOSTLY_MINUS = 0,   /* diag(+,-,...,-)      (Sec. 2.3)           */
+    BG_METRIC_ALTERNATING = 1     /* diag(+,-,+,-,...)    (Sec. 3.1)           */
+} bg_metric;
+
+typedef struct bg_plan bg_plan;   /* opaque; immutable after creation; may be
+                                     shared by threads and streams            */
+
+/*
+ * bg_plan_create -- validate and fix one (n, d, D_s, field, p, metric, states)
+ * configuration.  Host-side work, plus one device copy of `assign` when
+ * n_assign > 1.
+ *
+ *   n        number of gluons, 4 <= n <= 12
+ *   d        momentum dimension, 4 <= d <= 8 (Sec. 2.3)
+ *   D_s      polarisation dimension, d <= D_s <= 8 (zero-padding embedding)
+ *   field    BG_FIELD_FP or BG_FIELD_C64
+ *   p        the prime for BG_FIELD_FP (odd prime, 3 <= p < 2^31, checked by
+ *            a deterministic Miller-Rabin test); must be 0 for BG_FIELD_C64
+ *   metric   BG_METRIC_*
+ *   n_states S >= 1: states supplied per leg (eps layout [E][n][S][D_s])
+ *   n_assign H >= 1: state assignments evaluated per point (out [E][H]);
+ *            H * n <= 2^20
+ *   assign   host array [H][n] of state indices < S, copied by the call; may
+ *            be NULL only when H == 1 (then every leg uses state 0)
+ *   out      receives the plan
+ */
+bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p,
+                         bg_metric metric, int n_states, int n_assign,
+                         const uint8_t* assign, bg_plan** out);
+
+/* bg_plan_destroy -- free a plan (NULL is accepted).  No kernel of this plan
+ * may still be running. */
+bg_status bg_plan_destroy(bg_plan* plan);
+
+/*
+ * bg_workspace_size -- device workspace bytes bg_eval needs for E points
+ * (0 when the plan's kernel keeps its current table in shared memory).  The
+ * size is at most the value for E = INT64_MAX and is independent of E once E
+ * exceeds the number of resident threads.
+ */
+bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes);
+
+/*
+ * bg_eval -- evaluate E points on `stream` (asynchronous, one kernel launch;
+ * the results are valid once the stream reaches the call).
+ *
+ *   E          number of phase-space points, E >= 0 (E == 0: no launch)
+ *   momenta    device [E][n][d]: uint32 residues (FP) or double2 (C64)
+ *   eps        device [E][n][S][D_s], same element type (S = n_states)
+ *   out        device [E][H]: uint32 in [0,p) (FP) or double2 (C64)
+ *   status     device [E] uint8 or NULL: 0 ok, 1 singular propagator
+ *   workspace  device buffer of >= bg_workspace_size(plan, E) bytes, 256-byte
+ *              aligned, or NULL when that size is 0; concurrent calls need
+ *              distinct workspaces
+ *   stream     CUDA stream (0 = legacy default stream)
+ *
+ * Buffers must be on the device that is current at the call, and momenta,
+ * eps and out must be aligned to their element size.  Preconditions not
+ * checked on the device: canonical F_p inputs (< p), sum k = 0, k_i^2 = 0,
+ * eps_i . k_i = 0 (violations give well-defined but meaningless numbers).
+ */
+bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta,
+                  const void* eps, void* out, uint8_t* status,
+                  void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* bg_plan_describe -- NUL-terminated one-line description of the kernel the
+ * plan launches (variant, block size, shared memory, workspace per thread)
+ * written to buf[0..len); returns BG_ERR_INVALID_ARG when it does not fit. */
+bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len);
+
+/* bg_strerror -- static string for a status code. */
+const char* bg_strerror(bg_status s);
+
+/* bg_last_error -- thread-local detail of the last failing call on this
+ * thread ("" if none). */
+const char* bg_last_error(void);
+
+/* bg_version -- BG_VERSION of the library binary. */
+int bg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BG_H */

@@ -1,0 +1,178 @@
+"""ctypes binding of ``libbg.so`` (C-ABI in ``include/bg.h``).
+
+Argument marshalling only: torch tensors are passed as raw device pointers
+and ``torch.cuda.Stream`` objects as ``cudaStream_t``; every step of the
+recursion runs in the library's CUDA kernel.  Importing this module loads the
+library and raises ``ImportError`` when it has not been built (there is no CPU
+fallback).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+BG_OK = 0
+BG_ERR_INVALID_ARG = 1
+BG_ERR_UNSUPPORTED = 2
+BG_ERR_NOMEM = 3
+BG_ERR_CUDA = 4
+BG_ERR_TIMEOUT = 5
+BG_ERR_BUSY = 6
+
+FIELD_C64 = 0
+FIELD_FP = 1
+MOSTLY_MINUS = 0
+ALTERNATING = 1
+
+# bg_plan_create / bg_eval / ... as declared in include/bg.h
+EXPORTED = ("bg_plan_create", "bg_plan_destroy", "bg_workspace_size", "bg_eval",
+            "bg_plan_describe", "bg_strerror", "bg_last_error", "bg_version")
+
+LIB_PATH = _build.LIB
+
+
+def load_library(path=None):
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libbg.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    lib.bg_plan_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(vp)]
+    lib.bg_plan_create.restype = ctypes.c_int
+    lib.bg_plan_destroy.argtypes = [vp]
+    lib.bg_plan_destroy.restype = ctypes.c_int
+    lib.bg_workspace_size.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
+    lib.bg_workspace_size.restype = ctypes.c_int
+    lib.bg_eval.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    lib.bg_eval.restype = ctypes.c_int
+    lib.bg_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.bg_plan_describe.restype = ctypes.c_int
+    lib.bg_strerror.argtypes = [ctypes.c_int]
+    lib.bg_strerror.restype = ctypes.c_char_p
+    lib.bg_last_error.argtypes = []
+    lib.bg_last_error.restype = ctypes.c_char_p
+    lib.bg_version.argtypes = []
+    lib.bg_version.restype = ctypes.c_int
+    return lib
+
+
+_lib = load_library()
+
+
+class BGError(RuntimeError):
+    def __init__(self, status, detail):
+        self.status = status
+        super().__init__(f"{_lib.bg_strerror(status).decode()}: {detail}")
+
+
+def _check(status):
+    if status != BG_OK:
+        raise BGError(status, _lib.bg_last_error().decode())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """One (n, d, D_s, field, p, metric, states) configuration (bg_plan)."""
+
+    def __init__(self, n, d, Ds, field, p=0, metric=MOSTLY_MINUS, n_states=1, assign=None):
+        self.n, self.d, self.Ds = n, d, Ds
+        self.field, self.p, self.metric = field, p, metric
+        self.n_states = n_states
+        buf = None
+        H = 1
+        if assign is not None:
+            import numpy as np
+            a = np.ascontiguousarray(assign, dtype=np.uint8)
+            if a.ndim != 2 or a.shape[1] != n:
+                raise ValueError("assign must have shape [H][n]")
+            H = a.shape[0]
+            self._assign = a
+            buf = a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        self.n_assign = H
+        h = ctypes.c_void_p()
+        _check(_lib.bg_plan_create(n, d, Ds, field, p, metric, n_states, H, buf, ctypes.byref(h)))
+        self._h = h
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.bg_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def describe(self):
+        buf = ctypes.create_string_buffer(512)
+        _check(_lib.bg_plan_describe(self._h, buf, 512))
+        return buf.value.decode()
+
+    def workspace_size(self, E):
+        b = ctypes.c_size_t()
+        _check(_lib.bg_workspace_size(self._h, E, ctypes.byref(b)))
+        return b.value
+
+    def workspace(self, E, device=None):
+        """A cached device workspace of at least workspace_size(E) bytes."""
+        need = self.workspace_size(E)
+        if need == 0:
+            return None
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device=device or "cuda")
+        return self._ws
+
+    @property
+    def io_dtype(self):
+        return torch.int32 if self.field == FIELD_FP else torch.complex128
+
+    def eval(self, momenta, eps, out=None, status=None, workspace=None, stream=None):
+        """Amplitudes of E points.  momenta [E][n][d] and eps [E][n][(S)][D_s]
+        as device tensors (int32/uint32 residues for F_p, complex128 for C64).
+        Returns (out [E] or [E][H], status [E] uint8)."""
+        E = momenta.shape[0]
+        dev = momenta.device
+        if out is None:
+            shape = (E,) if self.n_assign == 1 else (E, self.n_assign)
+            out = torch.empty(shape, dtype=momenta.dtype, device=dev)
+        if status is None:
+            status = torch.empty(E, dtype=torch.uint8, device=dev)
+        for t in (momenta, eps, out, status):
+            if not t.is_contiguous():
+                raise ValueError("tensors must be contiguous")
+        if workspace is None:
+            workspace = self.workspace(E, dev)
+        ws_bytes = workspace.numel() if workspace is not None else 0
+        _check(_lib.bg_eval(self._h, E, _ptr(momenta), _ptr(eps), _ptr(out), _ptr(status),
+                            _ptr(workspace), ws_bytes, _stream_handle(stream)))
+        return out, status
+
+
+def strerror(status):
+    return _lib.bg_strerror(status).decode()
+
+
+def version():
+    return _lib.bg_version()

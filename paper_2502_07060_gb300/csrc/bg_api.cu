@@ -1,0 +1,346 @@
+// bg_api.cu -- the C-ABI of libbg.so (declared in include/bg.h): plan
+// validation, kernel selection and the single launch of bg_eval.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdlib>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/bg.h"
+#include "bg_instances.cuh"
+
+#define BG_REG(TAG, N) void bg_register_##TAG##_n##N(std::vector<bgk::KernelEntry>&);
+BG_REG(fp, 4) BG_REG(fp, 5) BG_REG(fp, 6) BG_REG(fp, 7) BG_REG(fp, 8) BG_REG(fp, 9)
+BG_REG(fp, 10) BG_REG(fp, 11) BG_REG(fp, 12)
+BG_REG(c64, 4) BG_REG(c64, 5) BG_REG(c64, 6) BG_REG(c64, 7) BG_REG(c64, 8) BG_REG(c64, 9)
+BG_REG(c64, 10) BG_REG(c64, 11) BG_REG(c64, 12)
+#undef BG_REG
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bg_status fail(bg_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+const std::vector<bgk::KernelEntry>& registry() {
+    static std::vector<bgk::KernelEntry> v;
+    static std::once_flag once;
+    std::call_once(once, [] {
+#define BG_ADD(TAG, N) bg_register_##TAG##_n##N(v);
+        BG_ADD(fp, 4) BG_ADD(fp, 5) BG_ADD(fp, 6) BG_ADD(fp, 7) BG_ADD(fp, 8) BG_ADD(fp, 9)
+        BG_ADD(fp, 10) BG_ADD(fp, 11) BG_ADD(fp, 12)
+        BG_ADD(c64, 4) BG_ADD(c64, 5) BG_ADD(c64, 6) BG_ADD(c64, 7) BG_ADD(c64, 8) BG_ADD(c64, 9)
+        BG_ADD(c64, 10) BG_ADD(c64, 11) BG_ADD(c64, 12)
+#undef BG_ADD
+    });
+    return v;
+}
+
+uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t m) { return (a * b) % m; }   // a, b < 2^31
+
+uint64_t powmod64(uint64_t a, uint64_t e, uint64_t m) {
+    uint64_t r = 1 % m;
+    a %= m;
+    while (e) {
+        if (e & 1) r = mulmod64(r, a, m);
+        a = mulmod64(a, a, m);
+        e >>= 1;
+    }
+    return r;
+}
+
+// Deterministic Miller-Rabin for n < 2^32 (bases 2, 3, 5, 7 suffice below 3.2e9).
+bool is_prime_u32(uint32_t n) {
+    if (n < 2) return false;
+    for (uint32_t q : {2u, 3u, 5u, 7u}) {
+        if (n == q) return true;
+        if (n % q == 0) return false;
+    }
+    uint64_t d = n - 1;
+    int r = 0;
+    while ((d & 1) == 0) { d >>= 1; ++r; }
+    for (uint64_t a : {2ull, 3ull, 5ull, 7ull}) {
+        uint64_t x = powmod64(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int i = 1; i < r; ++i) {
+            x = mulmod64(x, x, n);
+            if (x == n - 1) { comp = false; break; }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+int round_dim(int x) { return x <= 4 ? 4 : (x <= 6 ? 6 : 8); }
+
+bg_status check_device_ptr(const void* ptr, const char* what, int device) {
+    cudaPointerAttributes attr;
+    cudaError_t err = cudaPointerGetAttributes(&attr, ptr);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BG_ERR_INVALID_ARG, "%s: not a CUDA pointer (%s)", what, cudaGetErrorString(err));
+    }
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return fail(BG_ERR_INVALID_ARG, "%s: must be device memory", what);
+    if (attr.type == cudaMemoryTypeDevice && attr.device != device)
+        return fail(BG_ERR_INVALID_ARG, "%s: lives on device %d, current device is %d", what,
+                    attr.device, device);
+    return BG_OK;
+}
+
+}  // namespace
+
+struct bg_plan {
+    int n, d, Ds;
+    bg_field field;
+    uint32_t p;
+    bg_metric metric;
+    int S, H;
+    std::vector<uint8_t> assign;      // host copy [H][n]
+    uint8_t* d_assign = nullptr;      // device copy when H > 1
+    int device = -1;                  // device of d_assign / attribute setup
+    const bgk::KernelEntry* entry = nullptr;
+    bgk::FieldFp fp{};
+    bgk::FieldC64 c64{};
+    int sm_count = 0;
+    int blocks_per_sm = 0;
+    size_t smem_bytes = 0;            // dynamic shared memory per block
+};
+
+extern "C" {
+
+const char* bg_strerror(bg_status s) {
+    switch (s) {
+        case BG_OK: return "success";
+        case BG_ERR_INVALID_ARG: return "invalid argument";
+        case BG_ERR_UNSUPPORTED: return "unsupported configuration";
+        case BG_ERR_NOMEM: return "out of memory";
+        case BG_ERR_CUDA: return "CUDA error";
+        case BG_ERR_TIMEOUT: return "timed out";
+        case BG_ERR_BUSY: return "busy";
+    }
+    return "unknown status";
+}
+
+const char* bg_last_error(void) { return g_last_error.c_str(); }
+
+int bg_version(void) { return BG_VERSION; }
+
+bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_metric metric,
+                         int n_states, int n_assign, const uint8_t* assign, bg_plan** out) {
+    g_last_error.clear();
+    if (!out) return fail(BG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 4 || n > 12) return fail(BG_ERR_INVALID_ARG, "n = %d outside [4, 12]", n);
+    if (d < 4 || d > 8) return fail(BG_ERR_INVALID_ARG, "d = %d outside [4, 8]", d);
+    if (D_s < d || D_s > 8) return fail(BG_ERR_INVALID_ARG, "D_s = %d outside [d, 8]", D_s);
+    if (field != BG_FIELD_FP && field != BG_FIELD_C64)
+        return fail(BG_ERR_INVALID_ARG, "unknown field %d", (int)field);
+    if (metric != BG_METRIC_MOSTLY_MINUS && metric != BG_METRIC_ALTERNATING)
+        return fail(BG_ERR_INVALID_ARG, "unknown metric %d", (int)metric);
+    if (field == BG_FIELD_FP) {
+        if (p < 3 || p >= (1u << 31) || !is_prime_u32(p))
+            return fail(BG_ERR_INVALID_ARG, "p = %u is not an odd prime below 2^31", p);
+    } else if (p != 0) {
+        return fail(BG_ERR_INVALID_ARG, "p must be 0 for the complex field");
+    }
+    if (n_states < 1 || n_states > 255) return fail(BG_ERR_INVALID_ARG, "n_states = %d", n_states);
+    if (n_assign < 1 || (int64_t)n_assign * n > (1 << 20))
+        return fail(BG_ERR_INVALID_ARG, "n_assign = %d", n_assign);
+    if (n_assign > 1 && !assign) return fail(BG_ERR_INVALID_ARG, "assign is NULL with n_assign > 1");
+    if (assign) {
+        for (int64_t i = 0; i < (int64_t)n_assign * n; ++i)
+            if (assign[i] >= n_states)
+                return fail(BG_ERR_INVALID_ARG, "assign[%lld] = %d >= n_states", (long long)i, assign[i]);
+    }
+
+    const int D = round_dim(D_s > d ? D_s : d);
+    const bgk::KernelEntry* best = nullptr;
+    for (const auto& e : registry()) {
+        if (e.field != (int)field || e.n != n || e.metric != (int)metric || e.D != D) continue;
+        if (!best) best = &e;
+        else if (field == BG_FIELD_FP && !e.global_table && best->global_table) best = &e;
+    }
+    if (const char* force = getenv("BG_TABLE")) {     // placement override for experiments
+        const bool want_global = strcmp(force, "global") == 0;
+        for (const auto& e : registry())
+            if (e.field == (int)field && e.n == n && e.metric == (int)metric && e.D == D &&
+                e.global_table == want_global)
+                best = &e;
+    }
+    if (!best) return fail(BG_ERR_UNSUPPORTED, "no kernel for n=%d D=%d field=%d metric=%d", n, D,
+                           (int)field, (int)metric);
+
+    bg_plan* pl = new (std::nothrow) bg_plan();
+    if (!pl) return fail(BG_ERR_NOMEM, "host allocation failed");
+    pl->n = n; pl->d = d; pl->Ds = D_s; pl->field = field; pl->p = p; pl->metric = metric;
+    pl->S = n_states; pl->H = n_assign; pl->entry = best;
+    if (assign) pl->assign.assign(assign, assign + (size_t)n_assign * n);
+    if (field == BG_FIELD_FP) {
+        uint32_t inv = p;                         // p^-1 mod 2^32 by Newton iteration
+        for (int i = 0; i < 5; ++i) inv *= 2u - p * inv;
+        pl->fp.p = p;
+        pl->fp.pinv = 0u - inv;
+        const uint64_t r1 = (uint64_t(1) << 32) % p;
+        pl->fp.one = (uint32_t)r1;
+        pl->fp.r2 = (uint32_t)mulmod64(r1, r1, p);
+        pl->fp.pm2 = p - 2;
+    }
+
+    if (cudaGetDevice(&pl->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete pl;
+        return fail(BG_ERR_CUDA, "no CUDA device");
+    }
+    cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device);
+    pl->smem_bytes = best->global_table ? 0 : (size_t)best->words * best->block * best->elem_bytes;
+    if (pl->smem_bytes > 0) {
+        cudaError_t err = cudaFuncSetAttribute(best->func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)pl->smem_bytes);
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            delete pl;
+            return fail(BG_ERR_UNSUPPORTED, "shared memory %zu B: %s", pl->smem_bytes, cudaGetErrorString(err));
+        }
+    }
+    int occ = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, best->func, best->block,
+                                                                    pl->smem_bytes);
+    if (err != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        delete pl;
+        return fail(BG_ERR_UNSUPPORTED, "kernel cannot be resident (%s)", cudaGetErrorString(err));
+    }
+    pl->blocks_per_sm = occ;
+    if (n_assign > 1) {
+        size_t bytes = pl->assign.size();
+        if (cudaMalloc(&pl->d_assign, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            delete pl;
+            return fail(BG_ERR_NOMEM, "device allocation of %zu B failed", bytes);
+        }
+        if (cudaMemcpy(pl->d_assign, pl->assign.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(pl->d_assign);
+            delete pl;
+            return fail(BG_ERR_CUDA, "copy of the assignment table failed");
+        }
+    }
+    *out = pl;
+    return BG_OK;
+}
+
+bg_status bg_plan_destroy(bg_plan* plan) {
+    if (!plan) return BG_OK;
+    if (plan->d_assign) cudaFree(plan->d_assign);
+    delete plan;
+    return BG_OK;
+}
+
+static int64_t resident_blocks(const bg_plan* pl) { return (int64_t)pl->blocks_per_sm * pl->sm_count; }
+
+bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes) {
+    if (!plan || !bytes || E < 0) return fail(BG_ERR_INVALID_ARG, "bad argument to bg_workspace_size");
+    *bytes = 0;
+    if (!plan->entry->global_table || E == 0) return BG_OK;
+    const int64_t items = E * plan->H;
+    const int B = plan->entry->block;
+    int64_t blocks = (items + B - 1) / B;
+    if (blocks > resident_blocks(plan)) blocks = resident_blocks(plan);
+    *bytes = (size_t)blocks * B * plan->entry->words * plan->entry->elem_bytes;
+    return BG_OK;
+}
+
+bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
+    if (!plan || !buf) return fail(BG_ERR_INVALID_ARG, "bad argument to bg_plan_describe");
+    const auto* e = plan->entry;
+    int w = snprintf(buf, len,
+                     "field=%s n=%d d=%d D_s=%d kernel_D=%d metric=%s table=%s block=%d "
+                     "blocks_per_sm=%d smem=%zu words_per_thread=%d elem_bytes=%d",
+                     plan->field == BG_FIELD_FP ? "fp" : "c64", plan->n, plan->d, plan->Ds, e->D,
+                     plan->metric == BG_METRIC_MOSTLY_MINUS ? "mostly_minus" : "alternating",
+                     e->global_table ? "global" : "shared", e->block, plan->blocks_per_sm,
+                     plan->smem_bytes, e->words, e->elem_bytes);
+    if (w < 0 || (size_t)w >= len) return fail(BG_ERR_INVALID_ARG, "buffer too small");
+    return BG_OK;
+}
+
+bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
+                  uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+    g_last_error.clear();
+    if (!plan) return fail(BG_ERR_INVALID_ARG, "plan is NULL");
+    if (E < 0) return fail(BG_ERR_INVALID_ARG, "E = %lld < 0", (long long)E);
+    if (E == 0) return BG_OK;
+    if (!momenta || !eps || !out) return fail(BG_ERR_INVALID_ARG, "momenta, eps and out must be non-NULL");
+    if (E > (int64_t(1) << 40) / plan->H) return fail(BG_ERR_INVALID_ARG, "E too large");
+    const size_t elem = plan->field == BG_FIELD_FP ? 4 : 16;
+    if (((uintptr_t)momenta | (uintptr_t)eps | (uintptr_t)out) % elem)
+        return fail(BG_ERR_INVALID_ARG, "momenta, eps and out must be aligned to %zu bytes", elem);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BG_ERR_CUDA, "no current CUDA device");
+    }
+    if (plan->d_assign && dev != plan->device)
+        return fail(BG_ERR_CUDA, "plan was created on device %d, current device is %d", plan->device, dev);
+    bg_status st;
+    if ((st = check_device_ptr(momenta, "momenta", dev)) != BG_OK) return st;
+    if ((st = check_device_ptr(eps, "eps", dev)) != BG_OK) return st;
+    if ((st = check_device_ptr(out, "out", dev)) != BG_OK) return st;
+    if (status && (st = check_device_ptr(status, "status", dev)) != BG_OK) return st;
+
+    const bgk::KernelEntry* e = plan->entry;
+    size_t need = 0;
+    bg_workspace_size(plan, E, &need);
+    if (need > 0) {
+        if (!workspace || workspace_bytes < need)
+            return fail(BG_ERR_INVALID_ARG, "workspace of %zu B needed, %zu B given", need, workspace_bytes);
+        if ((uintptr_t)workspace % 256) return fail(BG_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+        if ((st = check_device_ptr(workspace, "workspace", dev)) != BG_OK) return st;
+    }
+    if (dev != plan->device && plan->smem_bytes > 0) {
+        cudaError_t err = cudaFuncSetAttribute(e->func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)plan->smem_bytes);
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BG_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
+        }
+    }
+
+    bgk::LaunchArgs a;
+    a.E = E;
+    a.H = plan->H;
+    a.S = plan->S;
+    a.d_in = plan->d;
+    a.ds_in = plan->Ds;
+    a.k = momenta;
+    a.eps = eps;
+    a.out = out;
+    a.status = status;
+    a.assign = plan->d_assign;
+    a.ws = workspace;
+    const int64_t items = E * plan->H;
+    int64_t blocks = (items + e->block - 1) / e->block;
+    const int64_t cap = e->global_table ? resident_blocks(plan) : resident_blocks(plan) * 256;
+    if (blocks > cap) blocks = cap;
+    const void* fparams = plan->field == BG_FIELD_FP ? (const void*)&plan->fp : (const void*)&plan->c64;
+    e->launch(fparams, a, dim3((unsigned)blocks), plan->smem_bytes, stream);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(BG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(err));
+    return BG_OK;
+}
+
+}  // extern "C"

@@ -31,6 +31,7 @@ canonical residues in [0, p) stored as uint32 (uint64 inside).
 
 from __future__ import annotations
 
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -74,8 +75,8 @@ def fneg(a, p):
     return (np.uint64(p) - _u64(a)) % np.uint64(p)
 
 
-def finv(a, p):
-    """Elementwise inverse by Fermat's little theorem (a^(p-2)); 0 -> 0."""
+def _fermat_inv(a, p):
+    """Elementwise a^(p-2) by square-and-multiply (0 -> 0)."""
     a = _u64(a)
     r = np.ones_like(a)
     e = p - 2
@@ -84,6 +85,37 @@ def finv(a, p):
         if (e >> bit) & 1:
             r = (r * a) % np.uint64(p)
     return r
+
+
+def finv(a, p, width=64):
+    """Elementwise inverse mod p (0 -> 0).  Montgomery's simultaneous
+    inversion along rows of ``width`` elements: prefix products, one Fermat
+    inverse per row, then the backward sweep (about 3 products per element
+    instead of ~45)."""
+    a = _u64(a)
+    shape = a.shape
+    flat = a.reshape(-1)
+    m = flat.size
+    if m < 4 * width:
+        return _fermat_inv(flat, p).reshape(shape)
+    zero = flat == 0
+    x = np.where(zero, np.uint64(1), flat)
+    rows = -(-m // width)
+    pad = rows * width - m
+    X = np.concatenate([x, np.ones(pad, dtype=np.uint64)]).reshape(rows, width)
+    pref = np.empty_like(X)
+    pref[:, 0] = X[:, 0]
+    for j in range(1, width):
+        pref[:, j] = (pref[:, j - 1] * X[:, j]) % np.uint64(p)
+    r = _fermat_inv(pref[:, -1], p)
+    out = np.empty_like(X)
+    for j in range(width - 1, 0, -1):
+        out[:, j] = (pref[:, j - 1] * r) % np.uint64(p)
+        r = (r * X[:, j]) % np.uint64(p)
+    out[:, 0] = r
+    out = out.reshape(-1)[:m]
+    out[zero] = 0
+    return out.reshape(shape)
 
 
 def fdot(a, b, eta, p):
@@ -118,27 +150,23 @@ def fp_null_vectors(rng, shape, d, p, metric=MOSTLY_MINUS):
     """Uniform random null vectors in F_p^d, array shape ``shape + (d,)``."""
     shape = tuple(shape)
     if metric == MOSTLY_MINUS:
+        # E' (1 + |t|^2, 2t, 1 - |t|^2) with E' uniform in F_p^x: the
+        # stereographic vector E (1, 2t/(1+|t|^2), (1-|t|^2)/(1+|t|^2)) with
+        # E = E' (1 + |t|^2), which is again uniform when 1 + |t|^2 != 0.
         out = np.empty(shape + (d,), dtype=np.uint64)
-        todo = np.ones(shape, dtype=bool)
-        while todo.any():
-            m = int(todo.sum())
-            t = _fp_uniform(rng, (m, d - 2), p)
+        flat = out.reshape(-1, d)
+        m = flat.shape[0]
+        t = _fp_uniform(rng, (m, d - 2), p)
+        s = fmul(t, t, p).sum(axis=-1) % np.uint64(p)
+        bad = fadd(s, 1, p) == 0
+        while bad.any():
+            t[bad] = _fp_uniform(rng, (int(bad.sum()), d - 2), p)
             s = fmul(t, t, p).sum(axis=-1) % np.uint64(p)
-            den = fadd(s, 1, p)
-            good = den != 0
-            t, s, den = t[good], s[good], den[good]
-            inv = finv(den, p)
-            E = _fp_uniform(rng, (len(t),), p, nonzero=True)
-            k = np.empty((len(t), d), dtype=np.uint64)
-            k[:, 0] = E
-            scale = fmul(E, inv, p)
-            k[:, 1:d - 1] = fmul(fmul(t, 2, p), scale[:, None], p)
-            k[:, d - 1] = fmul(fsub(1, s, p), scale, p)
-            idx = np.flatnonzero(todo.ravel())[:len(t)]
-            out.reshape(-1, d)[idx] = k
-            flat = todo.ravel()
-            flat[idx] = False
-            todo = flat.reshape(shape)
+            bad = fadd(s, 1, p) == 0
+        E = _fp_uniform(rng, (m,), p, nonzero=True)
+        flat[:, 0] = fmul(E, fadd(s, 1, p), p)
+        flat[:, 1:d - 1] = fmul(fmul(t, 2, p), E[:, None], p)
+        flat[:, d - 1] = fmul(E, fsub(1, s, p), p)
         return out
     eta = metric_diag(d, metric)
     q = np.zeros(d, dtype=np.uint64)
@@ -220,15 +248,51 @@ def fp_transverse_states(rng, k, Ds, p, metric=MOSTLY_MINUS, S=1):
     return eps
 
 
-def fp_batch(seed, E, n, d, Ds, p=P_DEFAULT, metric=MOSTLY_MINUS, S=1):
+CHUNK = 1 << 16   # points per independently seeded generation chunk
+
+
+def _chunk_rng(seed, c):
+    """Chunk c of a batch draws from Philox seeded by (seed, c)."""
+    return np.random.Generator(np.random.Philox(np.random.SeedSequence([int(seed), int(c)])))
+
+
+def _fp_chunk(seed, c, m, n, d, Ds, p, metric, S):
+    rng = _chunk_rng(seed, c)
+    k = fp_massless_point(rng, m, n, d, p, metric)
+    eps = fp_transverse_states(rng, k, Ds, p, metric, S)
+    return k.astype(np.uint32), (eps[:, :, 0, :] if S == 1 else eps).astype(np.uint32)
+
+
+def _c64_chunk(seed, c, m, n, d, Ds, metric, S):
+    rng = _chunk_rng(seed, c)
+    k = c64_massless_point(rng, m, n, d, metric)
+    eps = c64_transverse_states(rng, k, Ds, metric, S)
+    return k.astype(np.complex128), (eps[:, :, 0, :] if S == 1 else eps)
+
+
+def _run_chunks(fn, seed, E, args, workers):
+    """Evaluate fn(seed, c, m, *args) for every chunk, in order; with
+    workers > 1 the chunks run in a process pool started with 'spawn' (safe
+    next to a CUDA context).  Results do not depend on ``workers``."""
+    jobs = [(seed, c, min(CHUNK, E - c * CHUNK)) + tuple(args) for c in range(-(-E // CHUNK))]
+    if workers is None:
+        workers = 1 if E <= 4 * CHUNK else min(16, os.cpu_count() or 1)
+    if workers <= 1 or len(jobs) <= 1:
+        return [fn(*j) for j in jobs]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(fn, *zip(*jobs)))
+
+
+def fp_batch(seed, E, n, d, Ds, p=P_DEFAULT, metric=MOSTLY_MINUS, S=1, workers=None):
     """Seeded F_p batch: (k uint32 [E][n][d], eps uint32 [E][n][Ds]) when S == 1,
     else eps uint32 [E][n][S][Ds]."""
-    rng = np.random.Generator(np.random.Philox(seed))
-    k = fp_massless_point(rng, E, n, d, p, metric)
-    eps = fp_transverse_states(rng, k, Ds, p, metric, S)
-    if S == 1:
-        eps = eps[:, :, 0, :]
-    return k.astype(np.uint32), np.ascontiguousarray(eps.astype(np.uint32))
+    parts = _run_chunks(_fp_chunk, seed, E, (n, d, Ds, p, metric, S), workers)
+    if not parts:
+        return (np.empty((0, n, d), np.uint32),
+                np.empty((0, n, Ds) if S == 1 else (0, n, S, Ds), np.uint32))
+    return np.concatenate([a for a, _ in parts]), np.concatenate([b for _, b in parts])
 
 
 # --------------------------------------------------------------------------
@@ -299,15 +363,14 @@ def c64_transverse_states(rng, k, Ds, metric=MOSTLY_MINUS, S=1):
     return v - a[..., None] * kpS - b[..., None] * qS
 
 
-def c64_batch(seed, E, n, d, Ds, metric=MOSTLY_MINUS, S=1):
+def c64_batch(seed, E, n, d, Ds, metric=MOSTLY_MINUS, S=1, workers=None):
     """Seeded complex batch: (k complex128 [E][n][d] with zero imaginary part,
     eps complex128 [E][n][Ds]) when S == 1, else eps [E][n][S][Ds]."""
-    rng = np.random.Generator(np.random.Philox(seed))
-    k = c64_massless_point(rng, E, n, d, metric)
-    eps = c64_transverse_states(rng, k, Ds, metric, S)
-    if S == 1:
-        eps = eps[:, :, 0, :]
-    return k.astype(np.complex128), np.ascontiguousarray(eps)
+    parts = _run_chunks(_c64_chunk, seed, E, (n, d, Ds, metric, S), workers)
+    if not parts:
+        return (np.empty((0, n, d), np.complex128),
+                np.empty((0, n, Ds) if S == 1 else (0, n, S, Ds), np.complex128))
+    return np.concatenate([a for a, _ in parts]), np.concatenate([b for _, b in parts])
 
 
 # --------------------------------------------------------------------------

@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path through the C-ABI against the oracle.
+
+F_p: bit-exact against the C oracle (itself pinned against the exact Python
+oracle).  C64: |A_gpu - A_ref| <= 1e-10 max(|A_ref|, S_pt) (reading G8),
+A_ref from the FP64 C oracle.  Sizes span several thread blocks and a ragged
+tail; both shared-memory and global-scratch table placements are exercised.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle import coracle as C
+from paper_2502_07060_gb300 import inputs as G
+
+pytestmark = pytest.mark.gpu
+
+P = G.P_DEFAULT
+PM = G.P_MERSENNE
+TOL_C64 = 1e-10
+
+
+def _bg():
+    from paper_2502_07060_gb300 import bg
+    return bg
+
+
+def _dev_u32(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+
+
+def _dev_c(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
+
+
+def run_fp(k, eps, p, metric, n_states=1, assign=None, table=None):
+    bg = _bg()
+    E, n, d = k.shape
+    Ds = eps.shape[-1]
+    old = os.environ.get("BG_TABLE")
+    if table:
+        os.environ["BG_TABLE"] = table
+    try:
+        plan = bg.Plan(n, d, Ds, bg.FIELD_FP, p, metric, n_states, assign)
+    finally:
+        if table:
+            if old is None:
+                del os.environ["BG_TABLE"]
+            else:
+                os.environ["BG_TABLE"] = old
+    out, st = plan.eval(_dev_u32(k), _dev_u32(eps))
+    import torch
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint32), st.cpu().numpy(), plan
+
+
+def run_c64(k, eps, metric, n_states=1, assign=None):
+    bg = _bg()
+    E, n, d = k.shape
+    Ds = eps.shape[-1]
+    plan = bg.Plan(n, d, Ds, bg.FIELD_C64, 0, metric, n_states, assign)
+    out, st = plan.eval(_dev_c(k), _dev_c(eps))
+    import torch
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), st.cpu().numpy(), plan
+
+
+FP_CASES = [
+    (4, 4, 4, 0, P), (5, 4, 4, 0, P), (5, 5, 6, 1, PM), (6, 4, 4, 1, PM), (6, 6, 6, 0, P),
+    (7, 4, 6, 0, P), (7, 7, 7, 0, P), (8, 6, 6, 0, P), (8, 4, 4, 1, PM), (8, 8, 8, 0, P),
+    (9, 6, 6, 0, P), (10, 4, 4, 0, P), (10, 6, 8, 1, P), (11, 8, 8, 0, P), (12, 4, 4, 1, PM),
+    (12, 8, 8, 0, P),
+]
+
+
+@pytest.mark.parametrize("n,d,Ds,metric,p", FP_CASES)
+def test_fp_bit_exact(n, d, Ds, metric, p):
+    E = 3 * 128 + 37                       # several blocks and a ragged tail
+    k, eps = G.fp_batch(100 + n * 3 + d, E, n, d, Ds, p, metric)
+    ref, rst = C.amp_fp(k, eps, p, metric)
+    out, st, plan = run_fp(k, eps, p, metric)
+    assert np.array_equal(st, rst)
+    assert np.array_equal(out, ref), plan.describe()
+
+
+@pytest.mark.parametrize("n", [8, 9])
+@pytest.mark.parametrize("table", ["shared", "global"])
+def test_fp_table_placements_agree(n, table):
+    E = 1000
+    k, eps = G.fp_batch(7 + n, E, n, 6, 6, P, 0)
+    ref, _ = C.amp_fp(k, eps, P, 0)
+    out, _, plan = run_fp(k, eps, P, 0, table=table)
+    assert ("table=global" in plan.describe()) == (table == "global")
+    assert np.array_equal(out, ref)
+
+
+def _c64_close(out, ref, spt=None):
+    scale = np.abs(ref) if spt is None else np.maximum(np.abs(ref), spt)
+    err = np.abs(out - ref)
+    return err <= TOL_C64 * scale, err / np.maximum(scale, 1e-300)
+
+
+C64_CASES = [(4, 4, 4, 0), (5, 4, 4, 0), (6, 6, 6, 0), (7, 4, 6, 1), (8, 6, 6, 0), (8, 8, 8, 1),
+             (9, 4, 4, 0), (10, 6, 6, 0), (11, 8, 8, 0), (12, 4, 4, 0), (12, 8, 8, 1)]
+
+
+@pytest.mark.parametrize("n,d,Ds,metric", C64_CASES)
+def test_c64_within_tolerance(n, d, Ds, metric):
+    E = 2 * 64 + 29
+    k, eps = G.c64_batch(200 + n + d, E, n, d, Ds, metric)
+    ref, rst = C.amp_c64(k, eps, metric)
+    out, st, plan = run_c64(k, eps, metric)
+    assert np.array_equal(st, rst)
+    ok, rel = _c64_close(out, ref)
+    assert ok.all(), f"max rel err {rel.max():.3e} ({plan.describe()})"
+
+
+def test_golden_rational_fixtures_mod_p():
+    """Exact rational amplitudes written by the oracle (tests/golden), reduced
+    mod p, are reproduced bit-exactly on the GPU."""
+    import json
+    from fractions import Fraction
+    path = os.path.join(os.path.dirname(__file__), "golden", "rational_amplitudes.json")
+    for c in json.load(open(path))["cases"]:
+        for p in (P, PM):
+            def red(x):
+                f = Fraction(x)
+                return f.numerator % p * pow(f.denominator % p, -1, p) % p
+            k = np.array([[[red(x) for x in v] for v in c["k"]]], dtype=np.uint32)
+            eps = np.array([[[red(x) for x in v] for v in c["eps"]]], dtype=np.uint32)
+            out, st, _ = run_fp(k, eps, p, c["metric"])
+            assert st[0] == 0 and int(out[0]) == red(c["amplitude"])
+
+
+def test_singular_propagator_status_on_gpu():
+    from tests.test_oracle_c import singular_fp_point
+    k1, e1 = singular_fp_point(3, 8, 6, 6)
+    k, eps = G.fp_batch(5, 200, 8, 6, 6)
+    k[77], eps[77] = k1[0], e1[0]
+    out, st, _ = run_fp(k, eps, P, 0)
+    ref, rst = C.amp_fp(k, eps, P, 0)
+    assert st[77] == 1 and out[77] == 0 and rst[77] == 1
+    assert np.array_equal(out, ref) and np.array_equal(st, rst)
+
+
+@pytest.mark.parametrize("field", ["fp", "c64"])
+def test_state_assignment_table(field):
+    """S = 2 states per leg and all H = 2^n assignments in one launch equal
+    the oracle on each explicitly materialised assignment."""
+    n, d, Ds, E = 6, 4, 4, 45
+    H = 1 << n
+    assign = np.array([[(h >> l) & 1 for l in range(n)] for h in range(H)], dtype=np.uint8)
+    if field == "fp":
+        k, eps = G.fp_batch(9, E, n, d, Ds, PM, 1, S=2)
+        out, st, _ = run_fp(k, eps, PM, 1, n_states=2, assign=assign)
+    else:
+        k, eps = G.c64_batch(9, E, n, d, Ds, 0, S=2)
+        out, st, _ = run_c64(k, eps, 0, n_states=2, assign=assign)
+    assert out.shape == (E, H)
+    idx = np.arange(n)
+    for h in range(H):
+        e_h = eps[:, idx, assign[h], :]
+        if field == "fp":
+            ref, _ = C.amp_fp(k, e_h, PM, 1)
+            assert np.array_equal(out[:, h], ref)
+        else:
+            ref, _ = C.amp_c64(k, e_h, 0)
+            assert _c64_close(out[:, h], ref)[0].all()
+
+
+def test_ward_identity_on_gpu_full_batch():
+    """Property at any size: eps_i -> k_i gives exactly 0 for every point."""
+    E, n, d = 1 << 16, 8, 6
+    k, eps = G.fp_batch(12, E, n, d, d)
+    for i in (0, 3, n - 1):
+        e2 = eps.copy()
+        e2[:, i, :] = k[:, i, :]
+        out, st, _ = run_fp(k, e2, P, 0)
+        assert not out.any()
+
+
+def test_empty_and_single_point():
+    import torch
+    bg = _bg()
+    plan = bg.Plan(8, 6, 6, bg.FIELD_FP, P)
+    e = torch.empty((0, 8, 6), dtype=torch.int32, device="cuda")
+    out, st = plan.eval(e, e)
+    assert out.numel() == 0
+    k, eps = G.fp_batch(1, 1, 8, 6, 6)
+    out, st, _ = run_fp(k, eps, P, 0)
+    ref, _ = C.amp_fp(k, eps, P, 0)
+    assert np.array_equal(out, ref)
+
+
+def test_eval_rejects_host_pointers_and_small_workspace():
+    import torch
+    bg = _bg()
+    plan = bg.Plan(8, 6, 6, bg.FIELD_FP, P)
+    k = torch.zeros((4, 8, 6), dtype=torch.int32)             # host tensors
+    with pytest.raises(bg.BGError) as ei:
+        plan.eval(k, k, out=torch.zeros(4, dtype=torch.int32, device="cuda"))
+    assert ei.value.status == bg.BG_ERR_INVALID_ARG
+    c = bg.Plan(8, 6, 6, bg.FIELD_C64, 0)
+    kd = torch.zeros((1000, 8, 6), dtype=torch.complex128, device="cuda")
+    need = c.workspace_size(1000)
+    assert need > 0
+    small = torch.empty(need // 2, dtype=torch.uint8, device="cuda")
+    with pytest.raises(bg.BGError):
+        c.eval(kd, kd, workspace=small)
+
+
+def test_full_size_metric_workload_sampled():
+    """The benchmark workload (n = 8, d = D_s = 6, 2^22 points, F_p and C64) in
+    the benchmark's launch configuration; sampled points against the oracle."""
+    E = 1 << 22
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(E, 4096, replace=False))
+    k, eps = G.fp_batch(2025, E, 8, 6, 6, P, 0)
+    out, st, _ = run_fp(k, eps, P, 0)
+    ref, rst = C.amp_fp(k[sample], eps[sample], P, 0)
+    assert np.array_equal(out[sample], ref) and np.array_equal(st[sample], rst)
+    del k, eps
+    kc, ec = G.c64_batch(2026, E, 8, 6, 6, 0)
+    outc, _, _ = run_c64(kc, ec, 0)
+    refc, _ = C.amp_c64(kc[sample], ec[sample], 0)
+    assert _c64_close(outc[sample], refc)[0].all()

@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/bg.h declares; host-side argument validation works without a GPU."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bg_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2502_07060_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("bg_plan_create", "bg_plan_destroy", "bg_eval", "bg_workspace_size",
+              "bg_plan_describe", "bg_strerror", "bg_last_error", "bg_version"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header():
+    from paper_2502_07060_gb300 import bg
+    assert sorted(bg.EXPORTED) == sorted(n for n in _declared())
+
+
+def test_strerror_and_version(lib):
+    lib.bg_strerror.restype = ctypes.c_char_p
+    assert lib.bg_strerror(0) == b"success"
+    assert lib.bg_strerror(1) == b"invalid argument"
+    assert lib.bg_version() == 1
+
+
+def _create(lib, n=8, d=6, Ds=6, field=1, p=2147483629, metric=0, S=1, H=1, assign=None):
+    h = ctypes.c_void_p()
+    lib.bg_plan_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    return lib.bg_plan_create(n, d, Ds, field, p, metric, S, H, assign, ctypes.byref(h))
+
+
+@pytest.mark.parametrize("kw", [
+    dict(n=3), dict(n=13), dict(d=3), dict(d=9), dict(Ds=5), dict(Ds=9),
+    dict(p=2147483647 * 2 + 1), dict(p=2147483649), dict(p=4), dict(p=2147483627),  # not prime
+    dict(field=2), dict(metric=2), dict(field=0, p=7), dict(S=0), dict(H=0), dict(H=2),
+])
+def test_plan_rejects_bad_arguments_on_host(lib, kw):
+    assert _create(lib, **kw) == 1          # BG_ERR_INVALID_ARG before any CUDA call
+
+
+def test_eval_rejects_null_plan(lib):
+    lib.bg_eval.argtypes = [ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 5 + \
+        [ctypes.c_size_t, ctypes.c_void_p]
+    assert lib.bg_eval(None, 1, None, None, None, None, None, 0, None) == 1
