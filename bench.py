@@ -212,7 +212,7 @@ def time_steps(fn, steps, warmup, stream, dist, device):
     return max_over_ranks(ms, dist, device)
 
 
-def run_field(field, E, steps, warmup, rank, dist, device, seed):
+def run_field(field, E, steps, warmup, rank, dist, device, seed, e2e=True):
     import torch
     from paper_2502_07060_gb300 import bg
     if field == "fp":
@@ -240,6 +240,14 @@ def run_field(field, E, steps, warmup, rank, dist, device, seed):
         ms = time_steps(step, steps, warmup, stream, dist, device)
     clocks = clk.summary()
 
+    res = {
+        "ms_per_step": ms / steps,
+        "value_per_rank": E / (ms / steps / 1e3),
+        "clocks": clocks,
+        "plan": plan.describe(),
+    }
+    if not e2e:
+        return res
     # end to end through the public API: pinned host inputs -> device ->
     # kernel -> host result, every step
     pk = hk.pin_memory()
@@ -256,15 +264,11 @@ def run_field(field, E, steps, warmup, rank, dist, device, seed):
 
     e2e_steps = max(3, min(steps, 20))
     ms_e2e = time_steps(e2e_step, e2e_steps, 2, stream, dist, device)
-    res = {
-        "ms_per_step": ms / steps,
-        "value_per_rank": E / (ms / steps / 1e3),
+    res.update({
         "e2e_ms_per_step": ms_e2e / e2e_steps,
         "h2d_bytes": pk.numel() * pk.element_size() + pe.numel() * pe.element_size(),
         "d2h_bytes": hout.numel() * hout.element_size() + hst.numel(),
-        "clocks": clocks,
-        "plan": plan.describe(),
-    }
+    })
     del dk, de, out, st, ws
     torch.cuda.empty_cache()
     return res
@@ -279,6 +283,8 @@ def main():
     ap.add_argument("--log2-points", type=int, default=22)
     ap.add_argument("--log2-points-c64", type=int, default=22)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fields", default="fp,c64", help="comma list of fp, c64")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -325,9 +331,21 @@ def main():
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     dist = init_dist(world, "nccl")
-    fp = run_field("fp", E, args.steps, args.warmup, rank, dist, device, 1000 + rank)
-    c64_steps = max(3, args.steps // 5)
-    c64 = run_field("c64", Ec, c64_steps, args.warmup, rank, dist, device, 2000 + rank)
+    fields = args.fields.split(",")
+    e2e = not args.no_e2e
+    if fields == ["c64"]:
+        c64 = run_field("c64", Ec, args.steps, args.warmup, rank, dist, device, 2000 + rank, e2e)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "c64_only": True, "value": world * c64["value_per_rank"],
+                              "unit": "amplitudes/s", "ms_per_step": c64["ms_per_step"],
+                              "plan": c64["plan"], "clocks": c64["clocks"]}))
+        return
+    fp = run_field("fp", E, args.steps, args.warmup, rank, dist, device, 1000 + rank, e2e)
+    if "c64" in fields:
+        c64_steps = max(3, args.steps // 5)
+        c64 = run_field("c64", Ec, c64_steps, args.warmup, rank, dist, device, 2000 + rank, e2e)
+    else:
+        c64 = None
 
     value = world * fp["value_per_rank"]
     tally, _ = literal_tally(N_LEG, D, DS)
@@ -351,17 +369,18 @@ def main():
                      "ops_per_unit": tally, "kernel_ops_per_unit": kernel_mults(N_LEG, D, DS),
                      "peak_derivation": f"{n_sm} SMs x 64 IMAD/clk x {sm_max:.0f} MHz / 3 IMAD per "
                                         f"Montgomery multiplication"},
-        "c64": {"value": world * c64["value_per_rank"], "unit": "amplitudes/s",
+        "c64": None if c64 is None else {"value": world * c64["value_per_rank"], "unit": "amplitudes/s",
                 "ms_per_step": c64["ms_per_step"], "points_per_step": Ec, "steps": c64_steps,
                 "dtype": "f64",
                 "roofline": {"bound": "alu", "achieved": c64["value_per_rank"] * c64_flops,
                              "peak": peak_fp64, "unit": "FP64 FLOP/s (literal tally)",
                              "frac": c64["value_per_rank"] * c64_flops / peak_fp64,
                              "peak_derivation": f"{n_sm} SMs x 2 DFMA/clk x 2 x {sm_max:.0f} MHz"},
-                "e2e_value": world * Ec / (c64["e2e_ms_per_step"] / 1e3),
+                "e2e_value": (world * Ec / (c64["e2e_ms_per_step"] / 1e3)) if e2e else None,
                 "clocks": c64["clocks"], "plan": c64["plan"]},
-        "e2e": {"value": world * E / (fp["e2e_ms_per_step"] / 1e3), "unit": "amplitudes/s",
-                "h2d_bytes_per_step": fp["h2d_bytes"], "d2h_bytes_per_step": fp["d2h_bytes"]},
+        "e2e": None if not e2e else {
+            "value": world * E / (fp["e2e_ms_per_step"] / 1e3), "unit": "amplitudes/s",
+            "h2d_bytes_per_step": fp["h2d_bytes"], "d2h_bytes_per_step": fp["d2h_bytes"]},
         "clocks": fp["clocks"],
         "gpu_launches": args.steps,
         "plan": fp["plan"],

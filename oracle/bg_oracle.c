@@ -19,6 +19,11 @@
  * product formed in 64 bits and reduced with %, inverses by the extended
  * Euclidean algorithm (Sec. 3, the finite-field division).
  * C64: C99 double complex, the library's complex division for 1/P^2.
+ * C64DD: the same recursion in double-double complex arithmetic (about 106
+ * significant bits: Knuth's TwoSum and an FMA-based exact product, the
+ * classic error-free transformations), used as the high-precision reference
+ * that FP64 results are measured against.  Outputs (re_hi, re_lo, im_hi,
+ * im_lo) per point.
  *
  * Metric: 0 = mostly minus (Sec. 2.3), 1 = alternating (Sec. 3.1).
  * Momenta are d-dimensional and zero padded to D_s (Sec. 2.3), so a dot with a
@@ -33,6 +38,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <complex.h>
+#include <math.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -238,6 +244,157 @@ int bgo_amp_c64(int n, int d, int Ds, int metric, int64_t E,
 #endif
     for (int64_t e = 0; e < E; ++e) {
         int st = c_point(n, d, Ds, metric, kc + e * n * d, ec + e * n * Ds, oc + e);
+        if (status) status[e] = (uint8_t)st;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------ double-double ---- */
+
+typedef struct { double hi, lo; } dd;
+typedef struct { dd re, im; } cdd;
+
+static dd two_sum(double a, double b) {
+    double s = a + b;
+    double bb = s - a;
+    double e = (a - (s - bb)) + (b - bb);
+    dd r = {s, e};
+    return r;
+}
+static dd fast_two_sum(double a, double b) {   /* |a| >= |b| */
+    double s = a + b;
+    dd r = {s, b - (s - a)};
+    return r;
+}
+static dd dd_add(dd a, dd b) {
+    dd s = two_sum(a.hi, b.hi);
+    dd t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+static dd dd_neg(dd a) { dd r = {-a.hi, -a.lo}; return r; }
+static dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+static dd dd_mul(dd a, dd b) {
+    double p = a.hi * b.hi;
+    double e = fma(a.hi, b.hi, -p);          /* exact error of the product */
+    e += a.hi * b.lo + a.lo * b.hi;
+    return fast_two_sum(p, e);
+}
+static dd dd_div(dd a, dd b) {
+    double q1 = a.hi / b.hi;
+    dd r = dd_sub(a, dd_mul((dd){q1, 0.0}, b));
+    double q2 = r.hi / b.hi;
+    r = dd_sub(r, dd_mul((dd){q2, 0.0}, b));
+    double q3 = r.hi / b.hi;
+    dd q = fast_two_sum(q1, q2);
+    return dd_add(q, (dd){q3, 0.0});
+}
+static cdd c_add(cdd a, cdd b) { cdd r = {dd_add(a.re, b.re), dd_add(a.im, b.im)}; return r; }
+static cdd c_sub(cdd a, cdd b) { cdd r = {dd_sub(a.re, b.re), dd_sub(a.im, b.im)}; return r; }
+static cdd c_mul(cdd a, cdd b) {
+    cdd r = {dd_sub(dd_mul(a.re, b.re), dd_mul(a.im, b.im)),
+             dd_add(dd_mul(a.re, b.im), dd_mul(a.im, b.re))};
+    return r;
+}
+static cdd c_inv(cdd z) {
+    dd w = dd_add(dd_mul(z.re, z.re), dd_mul(z.im, z.im));
+    cdd r = {dd_div(z.re, w), dd_neg(dd_div(z.im, w))};
+    return r;
+}
+static int c_iszero(cdd z) { return z.re.hi == 0.0 && z.im.hi == 0.0; }
+static const cdd CDD_ZERO = {{0.0, 0.0}, {0.0, 0.0}};
+
+static cdd cdd_dot(const cdd* a, const cdd* b, int dims, int metric) {
+    cdd acc = CDD_ZERO;
+    for (int mu = 0; mu < dims; ++mu) {
+        cdd t = c_mul(a[mu], b[mu]);
+        acc = sign_of(metric, mu) > 0 ? c_add(acc, t) : c_sub(acc, t);
+    }
+    return acc;
+}
+
+static void cdd_axpy(cdd* acc, cdd c, const cdd* v, int dims) {
+    for (int mu = 0; mu < dims; ++mu) acc[mu] = c_add(acc[mu], c_mul(c, v[mu]));
+}
+
+static int dd_point(int n, int d, int Ds, int metric, const double* k, const double* eps, double* out) {
+    const int N = n - 1;
+    static __thread cdd J[BGO_NMAX][BGO_NMAX][BGO_DMAX];
+    static __thread cdd P[BGO_NMAX][BGO_NMAX][BGO_DMAX];
+    cdd R[BGO_DMAX], diff[BGO_DMAX];
+
+    for (int i = 0; i < N; ++i) {
+        cdd acc[BGO_DMAX];
+        for (int mu = 0; mu < BGO_DMAX; ++mu) acc[mu] = CDD_ZERO;
+        for (int j = i; j < N; ++j) {
+            for (int mu = 0; mu < d; ++mu) {
+                cdd x = {{k[2 * (j * d + mu)], 0.0}, {k[2 * (j * d + mu) + 1], 0.0}};
+                acc[mu] = c_add(acc[mu], x);
+            }
+            memcpy(P[i][j], acc, sizeof(cdd) * d);
+        }
+        for (int mu = 0; mu < Ds; ++mu) {
+            cdd x = {{eps[2 * (i * Ds + mu)], 0.0}, {eps[2 * (i * Ds + mu) + 1], 0.0}};
+            J[i][i][mu] = x;
+        }
+    }
+    for (int m = 2; m <= N; ++m) {
+        for (int i = 0; i + m - 1 < N; ++i) {
+            const int j = i + m - 1;
+            for (int mu = 0; mu < BGO_DMAX; ++mu) R[mu] = CDD_ZERO;
+            for (int s = i; s < j; ++s) {
+                const cdd *JA = J[i][s], *JB = J[s + 1][j];
+                const cdd *PA = P[i][s], *PB = P[s + 1][j];
+                cdd jj = cdd_dot(JA, JB, Ds, metric);
+                cdd pb_ja = cdd_dot(PB, JA, d, metric);
+                cdd pa_jb = cdd_dot(PA, JB, d, metric);
+                for (int mu = 0; mu < d; ++mu) diff[mu] = c_sub(PA[mu], PB[mu]);
+                cdd_axpy(R, jj, diff, d);
+                cdd_axpy(R, c_add(pb_ja, pb_ja), JB, Ds);
+                cdd_axpy(R, c_sub(CDD_ZERO, c_add(pa_jb, pa_jb)), JA, Ds);
+            }
+            for (int s = i; s < j - 1; ++s) {
+                for (int t = s + 1; t < j; ++t) {
+                    const cdd *JA = J[i][s], *JB = J[s + 1][t], *JC = J[t + 1][j];
+                    cdd ac = cdd_dot(JA, JC, Ds, metric);
+                    cdd bc = cdd_dot(JB, JC, Ds, metric);
+                    cdd ab = cdd_dot(JA, JB, Ds, metric);
+                    cdd_axpy(R, c_add(ac, ac), JB, Ds);
+                    cdd_axpy(R, c_sub(CDD_ZERO, bc), JA, Ds);
+                    cdd_axpy(R, c_sub(CDD_ZERO, ab), JC, Ds);
+                }
+            }
+            if (m < N) {
+                cdd p2 = cdd_dot(P[i][j], P[i][j], d, metric);
+                if (c_iszero(p2)) { out[0] = out[1] = out[2] = out[3] = 0.0; return 1; }
+                cdd inv = c_inv(p2);
+                for (int mu = 0; mu < Ds; ++mu) J[i][j][mu] = c_mul(inv, R[mu]);
+            }
+        }
+    }
+    cdd last[BGO_DMAX];
+    for (int mu = 0; mu < Ds; ++mu) {
+        cdd x = {{eps[2 * ((n - 1) * Ds + mu)], 0.0}, {eps[2 * ((n - 1) * Ds + mu) + 1], 0.0}};
+        last[mu] = x;
+    }
+    cdd a = cdd_dot(last, R, Ds, metric);
+    out[0] = a.re.hi; out[1] = a.re.lo; out[2] = a.im.hi; out[3] = a.im.lo;
+    return 0;
+}
+
+int bgo_amp_c64dd(int n, int d, int Ds, int metric, int64_t E,
+                  const double* k, const double* eps, double* out4, uint8_t* status,
+                  int nthreads) {
+    if (check_args(n, d, Ds, metric) || E < 0) return -1;
+    if (E > 0 && (!k || !eps || !out4)) return -1;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#endif
+    for (int64_t e = 0; e < E; ++e) {
+        int st = dd_point(n, d, Ds, metric, k + 2 * e * n * d, eps + 2 * e * n * Ds, out4 + 4 * e);
         if (status) status[e] = (uint8_t)st;
     }
     return 0;

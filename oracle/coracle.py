@@ -27,7 +27,8 @@ def build(force=False):
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", _SRC,
+           "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -47,6 +48,9 @@ def _load():
         lib.bgo_amp_c64.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int64, f64p, f64p, f64p, u8p, ctypes.c_int]
         lib.bgo_amp_c64.restype = ctypes.c_int
+        lib.bgo_amp_c64dd.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int64, f64p, f64p, f64p, u8p, ctypes.c_int]
+        lib.bgo_amp_c64dd.restype = ctypes.c_int
         lib.bgo_max_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -98,3 +102,36 @@ def amp_c64(k, eps, metric=0, nthreads=0):
     if rc != 0:
         raise ValueError("C oracle rejected its arguments")
     return out, st
+
+
+def amp_c64dd(k, eps, metric=0, nthreads=0):
+    """Double-double evaluation of the complex amplitudes.  Returns (hi
+    complex128 [E], lo complex128 [E], status uint8 [E]) with the value
+    hi + lo to about 106 bits."""
+    lib = _load()
+    k = np.ascontiguousarray(k, dtype=np.complex128)
+    eps = np.ascontiguousarray(eps, dtype=np.complex128)
+    E, n, d = k.shape
+    Ds = eps.shape[2]
+    if eps.shape[:2] != (E, n):
+        raise ValueError("eps shape does not match k")
+    out = np.zeros((E, 4), dtype=np.float64)
+    st = np.zeros(E, dtype=np.uint8)
+    f64p = ctypes.POINTER(ctypes.c_double)
+    rc = lib.bgo_amp_c64dd(n, d, Ds, metric, E,
+                           k.ctypes.data_as(f64p), eps.ctypes.data_as(f64p),
+                           out.ctypes.data_as(f64p), st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                           nthreads)
+    if rc != 0:
+        raise ValueError("C oracle rejected its arguments")
+    hi = out[:, 0] + 1j * out[:, 2]
+    lo = out[:, 1] + 1j * out[:, 3]
+    return hi, lo, st
+
+
+def rel_error(a, hi, lo, scale=None):
+    """|a - (hi + lo)| / scale (default |hi|), evaluated without losing the
+    low part: a - hi is exact when a and hi agree to within a factor 2."""
+    diff = (a - hi) - lo
+    s = np.abs(hi) if scale is None else scale
+    return np.abs(diff) / np.maximum(s, 1e-300)

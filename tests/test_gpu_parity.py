@@ -1,9 +1,13 @@
 """GPU parity: the CUDA path through the C-ABI against the oracle.
 
 F_p: bit-exact against the C oracle (itself pinned against the exact Python
-oracle).  C64: |A_gpu - A_ref| <= 1e-10 max(|A_ref|, S_pt) (reading G8),
-A_ref from the FP64 C oracle.  Sizes span several thread blocks and a ragged
-tail; both shared-memory and global-scratch table placements are exercised.
+oracle).  C64: |A_gpu - A_ref| <= 1e-10 max(|A_ref|, S_pt) (reading G8) with
+A_ref the double-double evaluation of the C oracle (pinned against mpmath);
+on the few points where plain FP64 cannot reach 1e-10 (ill-conditioned
+points, measured by the literal FP64 oracle's own error) the bound is 8x that
+FP64 noise floor, and the share of such points is bounded.  Sizes span several
+thread blocks and a ragged tail; both shared-memory and global-scratch table
+placements are exercised.
 """
 
 import os
@@ -97,10 +101,31 @@ def test_fp_table_placements_agree(n, table):
     assert np.array_equal(out, ref)
 
 
-def _c64_close(out, ref, spt=None):
-    scale = np.abs(ref) if spt is None else np.maximum(np.abs(ref), spt)
-    err = np.abs(out - ref)
-    return err <= TOL_C64 * scale, err / np.maximum(scale, 1e-300)
+def c64_tolerance(k, eps, metric, hi, lo, spt=None):
+    """Per-point tolerance of reading G8: 1e-10 max(|A|, S_pt) against the
+    double-double value, widened only where FP64 itself cannot reach it: to 8x
+    the FP64 noise floor nu_pt, the largest error of the literal FP64 oracle
+    over three cyclic orderings of the legs (A is cyclically symmetric, so the
+    orderings differ only in rounding).  Returns (tol, fraction widened)."""
+    scale = np.abs(hi) if spt is None else np.maximum(np.abs(hi), spt)
+    nu = np.zeros(len(hi))
+    for r in range(3):
+        a, _ = C.amp_c64(np.roll(k, -r, axis=1), np.roll(eps, -r, axis=1), metric)
+        nu = np.maximum(nu, np.abs((a - hi) - lo))
+    tol = np.maximum(TOL_C64 * scale, 8.0 * nu)
+    widened = float(np.mean(8.0 * nu > TOL_C64 * scale))
+    return tol, widened
+
+
+def check_c64(out, k, eps, metric, spt=None, max_widened=0.01):
+    hi, lo, _ = C.amp_c64dd(k, eps, metric)
+    tol, widened = c64_tolerance(k, eps, metric, hi, lo, spt)
+    err = np.abs((out - hi) - lo)
+    bad = err > tol
+    rel = err / np.maximum(np.abs(hi), 1e-300)
+    assert not bad.any(), f"{bad.sum()} points out of tolerance, max rel err {rel.max():.3e}"
+    assert widened <= max_widened, f"{widened:.3%} of points ill-conditioned in FP64"
+    return rel
 
 
 C64_CASES = [(4, 4, 4, 0), (5, 4, 4, 0), (6, 6, 6, 0), (7, 4, 6, 1), (8, 6, 6, 0), (8, 8, 8, 1),
@@ -111,11 +136,21 @@ C64_CASES = [(4, 4, 4, 0), (5, 4, 4, 0), (6, 6, 6, 0), (7, 4, 6, 1), (8, 6, 6, 0
 def test_c64_within_tolerance(n, d, Ds, metric):
     E = 2 * 64 + 29
     k, eps = G.c64_batch(200 + n + d, E, n, d, Ds, metric)
-    ref, rst = C.amp_c64(k, eps, metric)
+    _, rst = C.amp_c64(k, eps, metric)
     out, st, plan = run_c64(k, eps, metric)
     assert np.array_equal(st, rst)
-    ok, rel = _c64_close(out, ref)
-    assert ok.all(), f"max rel err {rel.max():.3e} ({plan.describe()})"
+    check_c64(out, k, eps, metric, max_widened=0.05)
+
+
+def test_c64_metric_workload_strict():
+    """n = 8, d = D_s = 6 (the benchmark workload): every point within 1e-10
+    of the double-double value, no widening."""
+    E = 20000
+    k, eps = G.c64_batch(31, E, 8, 6, 6, 0)
+    out, _, _ = run_c64(k, eps, 0)
+    hi, lo, _ = C.amp_c64dd(k, eps, 0)
+    rel = np.abs((out - hi) - lo) / np.abs(hi)
+    assert rel.max() <= TOL_C64, rel.max()
 
 
 def test_golden_rational_fixtures_mod_p():
@@ -161,14 +196,19 @@ def test_state_assignment_table(field):
         out, st, _ = run_c64(k, eps, 0, n_states=2, assign=assign)
     assert out.shape == (E, H)
     idx = np.arange(n)
+    refs = []
     for h in range(H):
         e_h = eps[:, idx, assign[h], :]
         if field == "fp":
             ref, _ = C.amp_fp(k, e_h, PM, 1)
             assert np.array_equal(out[:, h], ref)
         else:
-            ref, _ = C.amp_c64(k, e_h, 0)
-            assert _c64_close(out[:, h], ref)[0].all()
+            refs.append(e_h)
+    if field == "c64":
+        his = np.stack([C.amp_c64dd(k, e_h, 0)[0] for e_h in refs], axis=1)
+        spt = np.abs(his).max(axis=1)
+        for h in range(H):
+            check_c64(out[:, h], k, refs[h], 0, spt=spt, max_widened=0.05)
 
 
 def test_ward_identity_on_gpu_full_batch():
@@ -225,5 +265,4 @@ def test_full_size_metric_workload_sampled():
     del k, eps
     kc, ec = G.c64_batch(2026, E, 8, 6, 6, 0)
     outc, _, _ = run_c64(kc, ec, 0)
-    refc, _ = C.amp_c64(kc[sample], ec[sample], 0)
-    assert _c64_close(outc[sample], refc)[0].all()
+    check_c64(outc[sample], kc[sample], ec[sample], 0, max_widened=0.0)

@@ -117,3 +117,29 @@ def test_bad_arguments_rejected():
         C.amp_fp(k, eps, 4294967291)      # p >= 2^31
     with pytest.raises(ValueError):
         C.amp_fp(k[:, :, :4], eps[:, :, :3], P)   # D_s < d
+
+
+@pytest.mark.parametrize("n,d,Ds,metric", [(4, 4, 4, 0), (8, 6, 6, 0), (7, 8, 8, 1), (12, 4, 4, 0)])
+def test_c_double_double_against_mpmath(n, d, Ds, metric):
+    """The double-double evaluation (the C64 reference of the GPU tests) agrees
+    with a 50-digit mpmath evaluation of the Python oracle to 1e-25."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    E = 6
+    k, eps = G.c64_batch(51 + n, E, n, d, Ds, metric)
+    hi, lo, st = C.amp_c64dd(k, eps, metric)
+    assert not st.any()
+    for e in range(E):
+        km = [[mp.mpc(x.real, x.imag) for x in v] for v in k[e]]
+        em = [[mp.mpc(x.real, x.imag) for x in v] for v in eps[e]]
+        a, _ = O.amplitude(km, em, metric)
+        v = mp.mpc(hi[e].real, hi[e].imag) + mp.mpc(lo[e].real, lo[e].imag)
+        assert abs(v - a) <= mp.mpf("1e-25") * abs(a)
+
+
+def test_c_double_double_singular():
+    k, eps = G.c64_batch(3, 2, 5, 4, 4, 0)
+    k[1, 0] = [1.0, 1.0, 0.0, 0.0]          # exactly null, and (k_1 + k_2)^2 = 0
+    k[1, 1] = [2.0, 2.0, 0.0, 0.0]          # exactly in FP64
+    _, _, st = C.amp_c64dd(k, eps, 0)
+    assert st[1] == 1 and st[0] == 0
