@@ -14,11 +14,13 @@
 #include "bg_instances.cuh"
 
 #define BG_REG(TAG, N) void bg_register_##TAG##_n##N(std::vector<bgk::KernelEntry>&);
-BG_REG(fp, 4) BG_REG(fp, 5) BG_REG(fp, 6) BG_REG(fp, 7) BG_REG(fp, 8) BG_REG(fp, 9)
-BG_REG(fp, 10) BG_REG(fp, 11) BG_REG(fp, 12)
-BG_REG(c64, 4) BG_REG(c64, 5) BG_REG(c64, 6) BG_REG(c64, 7) BG_REG(c64, 8) BG_REG(c64, 9)
-BG_REG(c64, 10) BG_REG(c64, 11) BG_REG(c64, 12)
+BG_REG(fp, 5) BG_REG(fp, 6) BG_REG(fp, 7) BG_REG(fp, 8)
 #undef BG_REG
+#define BG_REGC(TAG, D, DS) void bg_register_compact_##TAG##_##D##_##DS(std::vector<bgk::KernelEntry>&);
+BG_REGC(fp, 4, 4) BG_REGC(fp, 4, 6) BG_REGC(fp, 4, 8) BG_REGC(fp, 6, 6) BG_REGC(fp, 6, 8) BG_REGC(fp, 8, 8)
+BG_REGC(c64, 4, 4) BG_REGC(c64, 4, 6) BG_REGC(c64, 4, 8) BG_REGC(c64, 6, 6) BG_REGC(c64, 6, 8)
+BG_REGC(c64, 8, 8)
+#undef BG_REGC
 
 namespace {
 
@@ -39,10 +41,12 @@ const std::vector<bgk::KernelEntry>& registry() {
     static std::once_flag once;
     std::call_once(once, [] {
 #define BG_ADD(TAG, N) bg_register_##TAG##_n##N(v);
-        BG_ADD(fp, 4) BG_ADD(fp, 5) BG_ADD(fp, 6) BG_ADD(fp, 7) BG_ADD(fp, 8) BG_ADD(fp, 9)
-        BG_ADD(fp, 10) BG_ADD(fp, 11) BG_ADD(fp, 12)
-        BG_ADD(c64, 4) BG_ADD(c64, 5) BG_ADD(c64, 6) BG_ADD(c64, 7) BG_ADD(c64, 8) BG_ADD(c64, 9)
-        BG_ADD(c64, 10) BG_ADD(c64, 11) BG_ADD(c64, 12)
+        BG_ADD(fp, 5) BG_ADD(fp, 6) BG_ADD(fp, 7) BG_ADD(fp, 8)
+#define BG_ADDC(TAG, D, DS) bg_register_compact_##TAG##_##D##_##DS(v);
+        BG_ADDC(fp, 4, 4) BG_ADDC(fp, 4, 6) BG_ADDC(fp, 4, 8) BG_ADDC(fp, 6, 6) BG_ADDC(fp, 6, 8)
+        BG_ADDC(fp, 8, 8) BG_ADDC(c64, 4, 4) BG_ADDC(c64, 4, 6) BG_ADDC(c64, 4, 8) BG_ADDC(c64, 6, 6)
+        BG_ADDC(c64, 6, 8) BG_ADDC(c64, 8, 8)
+#undef BG_ADDC
 #undef BG_ADD
     });
     return v;
@@ -113,8 +117,11 @@ struct bg_plan {
     uint8_t* d_assign = nullptr;      // device copy when H > 1
     int device = -1;                  // device of d_assign / attribute setup
     const bgk::KernelEntry* entry = nullptr;
-    bgk::FieldFp fp{};
+    int words = 0;                    // table elements per thread
+    bgk::FieldFp fp{};                // unrolled kernels
     bgk::FieldC64 c64{};
+    bgk::FpOps fpo{};                 // compact kernels
+    bgk::C64Ops c64o{};
     int sm_count = 0;
     int blocks_per_sm = 0;
     size_t smem_bytes = 0;            // dynamic shared memory per block
@@ -167,37 +174,68 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
                 return fail(BG_ERR_INVALID_ARG, "assign[%lld] = %d >= n_states", (long long)i, assign[i]);
     }
 
-    const int D = round_dim(D_s > d ? D_s : d);
+    // Kernel choice: the compact kernel (run-time n) by default; the unrolled
+    // per-n kernel on request (BG_KERNEL=unrolled, F_p only, n <= 8).  Table
+    // placement: shared memory when two blocks fit on an SM, else global
+    // scratch (BG_TABLE=shared|global overrides).
+    const char* kenv = getenv("BG_KERNEL");
+    const bool want_unrolled = kenv && strcmp(kenv, "unrolled") == 0;
+    const char* tenv = getenv("BG_TABLE");
+    const int Dk = round_dim(d), DSk = round_dim(D_s);
     const bgk::KernelEntry* best = nullptr;
-    for (const auto& e : registry()) {
-        if (e.field != (int)field || e.n != n || e.metric != (int)metric || e.D != D) continue;
-        if (!best) best = &e;
-        else if (field == BG_FIELD_FP && !e.global_table && best->global_table) best = &e;
-    }
-    if (const char* force = getenv("BG_TABLE")) {     // placement override for experiments
-        const bool want_global = strcmp(force, "global") == 0;
+    int words = 0;
+    if (want_unrolled) {
+        const int Du = round_dim(D_s > d ? D_s : d);
         for (const auto& e : registry())
-            if (e.field == (int)field && e.n == n && e.metric == (int)metric && e.D == D &&
-                e.global_table == want_global)
+            if (!e.compact && e.field == (int)field && e.n == n && e.metric == (int)metric && e.D == Du)
                 best = &e;
+        if (best) words = best->words;
+    } else {
+        const bgk::Geometry geo{n - 1};
+        words = geo.words(Dk, DSk);
+        const size_t elem = field == BG_FIELD_FP ? 4 : 16;
+        bool want_global = true;
+        if (tenv) {
+            want_global = strcmp(tenv, "global") == 0;
+        } else if (field == BG_FIELD_FP) {
+            const size_t smem = (size_t)words * bgk::kBlockFpCompactSmem * elem;
+            want_global = smem > 110 * 1024;     // fewer than two blocks per SM
+        }
+        for (const auto& e : registry())
+            if (e.compact && e.field == (int)field && e.D == Dk && e.DS == DSk &&
+                e.metric == (int)metric && e.global_table == want_global)
+                best = &e;
+        if (!best)      // C64 has only the global placement
+            for (const auto& e : registry())
+                if (e.compact && e.field == (int)field && e.D == Dk && e.DS == DSk &&
+                    e.metric == (int)metric)
+                    best = &e;
     }
-    if (!best) return fail(BG_ERR_UNSUPPORTED, "no kernel for n=%d D=%d field=%d metric=%d", n, D,
-                           (int)field, (int)metric);
+    if (!best) return fail(BG_ERR_UNSUPPORTED, "no kernel for n=%d d=%d D_s=%d field=%d metric=%d", n, d,
+                           D_s, (int)field, (int)metric);
 
     bg_plan* pl = new (std::nothrow) bg_plan();
     if (!pl) return fail(BG_ERR_NOMEM, "host allocation failed");
     pl->n = n; pl->d = d; pl->Ds = D_s; pl->field = field; pl->p = p; pl->metric = metric;
-    pl->S = n_states; pl->H = n_assign; pl->entry = best;
+    pl->S = n_states; pl->H = n_assign; pl->entry = best; pl->words = words;
     if (assign) pl->assign.assign(assign, assign + (size_t)n_assign * n);
     if (field == BG_FIELD_FP) {
         uint32_t inv = p;                         // p^-1 mod 2^32 by Newton iteration
         for (int i = 0; i < 5; ++i) inv *= 2u - p * inv;
+        const uint64_t r1 = (uint64_t(1) << 32) % p;
+        const uint64_t r2 = mulmod64(r1, r1, p);
+        const uint64_t r3 = mulmod64(r2, r1, p);
         pl->fp.p = p;
         pl->fp.pinv = 0u - inv;
-        const uint64_t r1 = (uint64_t(1) << 32) % p;
         pl->fp.one = (uint32_t)r1;
-        pl->fp.r2 = (uint32_t)mulmod64(r1, r1, p);
+        pl->fp.r2 = (uint32_t)r2;
         pl->fp.pm2 = p - 2;
+        pl->fpo.p = p;
+        pl->fpo.pinv = 0u - inv;
+        pl->fpo.one = (uint32_t)r1;
+        pl->fpo.r2 = (uint32_t)r2;
+        pl->fpo.r3 = (uint32_t)r3;
+        pl->fpo.pm2 = p - 2;
     }
 
     if (cudaGetDevice(&pl->device) != cudaSuccess) {
@@ -206,7 +244,7 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
         return fail(BG_ERR_CUDA, "no CUDA device");
     }
     cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device);
-    pl->smem_bytes = best->global_table ? 0 : (size_t)best->words * best->block * best->elem_bytes;
+    pl->smem_bytes = best->global_table ? 0 : (size_t)words * best->block * best->elem_bytes;
     if (pl->smem_bytes > 0) {
         cudaError_t err = cudaFuncSetAttribute(best->func, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)pl->smem_bytes);
@@ -260,7 +298,7 @@ bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes) {
     const int B = plan->entry->block;
     int64_t blocks = (items + B - 1) / B;
     if (blocks > resident_blocks(plan)) blocks = resident_blocks(plan);
-    *bytes = (size_t)blocks * B * plan->entry->words * plan->entry->elem_bytes;
+    *bytes = (size_t)blocks * B * plan->words * plan->entry->elem_bytes;
     return BG_OK;
 }
 
@@ -268,12 +306,13 @@ bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
     if (!plan || !buf) return fail(BG_ERR_INVALID_ARG, "bad argument to bg_plan_describe");
     const auto* e = plan->entry;
     int w = snprintf(buf, len,
-                     "field=%s n=%d d=%d D_s=%d kernel_D=%d metric=%s table=%s block=%d "
-                     "blocks_per_sm=%d smem=%zu words_per_thread=%d elem_bytes=%d",
-                     plan->field == BG_FIELD_FP ? "fp" : "c64", plan->n, plan->d, plan->Ds, e->D,
+                     "field=%s n=%d d=%d D_s=%d kernel=%s kernel_D=%d kernel_D_s=%d metric=%s "
+                     "table=%s block=%d blocks_per_sm=%d smem=%zu words_per_thread=%d elem_bytes=%d",
+                     plan->field == BG_FIELD_FP ? "fp" : "c64", plan->n, plan->d, plan->Ds,
+                     e->compact ? "compact" : "unrolled", e->D, e->DS,
                      plan->metric == BG_METRIC_MOSTLY_MINUS ? "mostly_minus" : "alternating",
                      e->global_table ? "global" : "shared", e->block, plan->blocks_per_sm,
-                     plan->smem_bytes, e->words, e->elem_bytes);
+                     plan->smem_bytes, plan->words, e->elem_bytes);
     if (w < 0 || (size_t)w >= len) return fail(BG_ERR_INVALID_ARG, "buffer too small");
     return BG_OK;
 }
@@ -320,24 +359,27 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const voi
         }
     }
 
-    bgk::LaunchArgs a;
-    a.E = E;
-    a.H = plan->H;
-    a.S = plan->S;
-    a.d_in = plan->d;
-    a.ds_in = plan->Ds;
-    a.k = momenta;
-    a.eps = eps;
-    a.out = out;
-    a.status = status;
-    a.assign = plan->d_assign;
-    a.ws = workspace;
     const int64_t items = E * plan->H;
     int64_t blocks = (items + e->block - 1) / e->block;
     const int64_t cap = e->global_table ? resident_blocks(plan) : resident_blocks(plan) * 256;
     if (blocks > cap) blocks = cap;
-    const void* fparams = plan->field == BG_FIELD_FP ? (const void*)&plan->fp : (const void*)&plan->c64;
-    e->launch(fparams, a, dim3((unsigned)blocks), plan->smem_bytes, stream);
+    if (e->compact) {
+        bgk::CompactArgs a;
+        a.E = E; a.H = plan->H; a.S = plan->S; a.n = plan->n;
+        a.d_in = plan->d; a.ds_in = plan->Ds;
+        a.k = momenta; a.eps = eps; a.out = out; a.status = status;
+        a.assign = plan->d_assign; a.ws = workspace;
+        const void* fparams = plan->field == BG_FIELD_FP ? (const void*)&plan->fpo : (const void*)&plan->c64o;
+        e->launch(fparams, &a, dim3((unsigned)blocks), plan->smem_bytes, stream);
+    } else {
+        bgk::LaunchArgs a;
+        a.E = E; a.H = plan->H; a.S = plan->S;
+        a.d_in = plan->d; a.ds_in = plan->Ds;
+        a.k = momenta; a.eps = eps; a.out = out; a.status = status;
+        a.assign = plan->d_assign; a.ws = workspace;
+        const void* fparams = plan->field == BG_FIELD_FP ? (const void*)&plan->fp : (const void*)&plan->c64;
+        e->launch(fparams, &a, dim3((unsigned)blocks), plan->smem_bytes, stream);
+    }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return fail(BG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(err));
     return BG_OK;

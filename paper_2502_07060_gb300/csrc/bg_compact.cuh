@@ -1,0 +1,267 @@
+// bg_compact.cuh -- Berends-Giele recursion, one point (and state assignment)
+// per thread, with the number of legs a RUN-TIME parameter.
+//
+// Method (arXiv:2502.07060, Sec. 2.2): currents over consecutive leg ranges,
+//   J(i,j) = (-i/P_ij^2) [ sum_s V3(P_A,P_B) J_A J_B + sum_{s<t} V4 J_A J_B J_C ],
+// vertices V3, V4 of Sec. 2.2; with every vertex i cancelled against the -i of
+// the propagator,
+//   R(i,j) = sum_s   (J_A.J_B)(P_A - P_B) + 2(P_B.J_A) J_B - 2(P_A.J_B) J_A
+//          + sum_s<t 2(J_A.J_C) J_B - (J_B.J_C) J_A - (J_A.J_B) J_C,
+//   J(i,j) = R(i,j) / P_ij^2 (internal ranges),   A = eps_n . R(1, n-1).
+//
+// The sum is regrouped by the sub-current each term multiplies (an identity,
+// exact over F_p):
+//   prefix  A = [i, s]:   -2 P_A.J_[s+1,j] - SA([s+1,j])
+//   suffix  C = [t+1, j]: +2 P_C.J_[i,t]   - SA([i,t])
+//   inner   B = [s+1, t]:  2 J_[i,s].J_[t+1,j]
+//   plus the momentum part sum_s (J_A.J_B)(P_A - P_B),
+// where SA(X) = sum over the splits X = Y|Z of J_Y.J_Z is accumulated while X
+// itself is built and stored next to its current.  Per range of length m this
+// costs m(m+1)/2 - 1 vector updates instead of 2(m-1) + 3 C(m-1,2).
+//
+// Per-point table (element w of thread t at [w * BLOCK + t]: conflict-free in
+// shared memory, coalesced in global memory), for N = n - 1 legs:
+//   currents of length 1..N-1 (D_s each), prefix sums K_0..K_N of the momenta
+//   (D each; P_{i,j} = K_{j+1} - K_i), SA and 1/P^2 per internal range.
+// Shared-memory placement keeps the table on chip; global placement keeps it
+// in a scratch buffer that one resident wave of blocks reuses (L2 resident).
+//
+// Only the component loops are unrolled; the loops over lengths, ranges and
+// splits run at run time, so one compact kernel serves every n and stays in
+// the instruction cache.
+#pragma once
+#include <cstdint>
+
+#include "bg_field.cuh"
+
+namespace bgk {
+
+struct CompactArgs {
+    int64_t E;                  // points
+    int H;                      // state assignments per point
+    int S;                      // states per leg
+    int n;                      // gluons (4..12)
+    int d_in, ds_in;            // dimensions of the inputs (<= D, D_s)
+    const void* k;              // [E][n][d_in]
+    const void* eps;            // [E][n][S][ds_in]
+    void* out;                  // [E][H]
+    uint8_t* status;            // [E] or null
+    const uint8_t* assign;      // device [H][n] or null (H == 1)
+    void* ws;                   // global table (global placement)
+};
+
+// Table geometry for N = n - 1 recursion legs (host and device).
+struct Geometry {
+    int N;
+    __host__ __device__ int jbase(int len) const { return ((len - 1) * (2 * N + 2 - len)) >> 1; }
+    __host__ __device__ int nj() const { return jbase(N); }              // currents, length 1..N-1
+    __host__ __device__ int ns() const { return jbase(N) - N; }          // internal ranges
+    __host__ __device__ int sbase(int len) const { return jbase(len) - N; }
+    __host__ __device__ int off_k(int DS) const { return nj() * DS; }
+    __host__ __device__ int off_sa(int D, int DS) const { return off_k(DS) + (N + 1) * D; }
+    __host__ __device__ int off_inv(int D, int DS) const { return off_sa(D, DS) + ns(); }
+    __host__ __device__ int words(int D, int DS) const { return off_inv(D, DS) + ns(); }
+};
+
+template <class F, int D, int DS, int METRIC, int BLOCK, bool GLOBAL_TABLE>
+__global__ void __launch_bounds__(BLOCK)
+bg_compact_kernel(const F f, const CompactArgs a) {
+    using T = typename F::T;
+    using C = typename F::C;
+    using Acc = typename F::A;
+    using io_t = typename F::io_t;
+
+    const int NLEG = a.n;
+    const Geometry g{NLEG - 1};
+    const int N = g.N;
+    const int W = g.words(D, DS);
+    const int OFF_K = g.off_k(DS), OFF_SA = g.off_sa(D, DS), OFF_INV = g.off_inv(D, DS);
+
+    extern __shared__ __align__(16) unsigned char bg_smem[];
+    T* base;
+    if constexpr (GLOBAL_TABLE) {
+        base = reinterpret_cast<T*>(a.ws) + static_cast<size_t>(blockIdx.x) * W * BLOCK + threadIdx.x;
+    } else {
+        base = reinterpret_cast<T*>(bg_smem) + threadIdx.x;
+    }
+    // vector accessors: element mu of a vector at word w is base[(w + mu) * BLOCK]
+    auto jvec = [&](int len, int start) { return base + (g.jbase(len) + start) * DS * BLOCK; };
+    auto kvec = [&](int t) { return base + (OFF_K + t * D) * BLOCK; };
+    auto load = [&](const T* p, T* v, int cnt) {
+#pragma unroll
+        for (int mu = 0; mu < DS; ++mu)
+            if (mu < cnt) v[mu] = p[mu * BLOCK];
+    };
+
+    const io_t* kin = static_cast<const io_t*>(a.k);
+    const io_t* ein = static_cast<const io_t*>(a.eps);
+    io_t* out = static_cast<io_t*>(a.out);
+    const int64_t total = a.E * a.H;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * BLOCK;
+
+    for (int64_t u = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; u < total; u += stride) {
+        int64_t e = u;
+        int h = 0;
+        if (a.H > 1) {
+            e = u / a.H;
+            h = static_cast<int>(u - e * a.H);
+        }
+        // a1: momenta -> prefix sums K_0 = 0, K_{l+1} = K_l + k_l (leg n unused:
+        // P_{1,n-1} = -k_n never enters); polarisations -> currents of length 1.
+        {
+            const io_t* kp = kin + e * NLEG * a.d_in;
+            T Kacc[D];
+#pragma unroll
+            for (int mu = 0; mu < D; ++mu) {
+                Kacc[mu] = f.zero();
+                base[(OFF_K + mu) * BLOCK] = Kacc[mu];
+            }
+#pragma unroll 1
+            for (int l = 0; l < N; ++l) {
+#pragma unroll
+                for (int mu = 0; mu < D; ++mu) {
+                    if (mu < a.d_in) Kacc[mu] = f.tadd(Kacc[mu], f.from_io(kp[l * a.d_in + mu]));
+                    base[(OFF_K + (l + 1) * D + mu) * BLOCK] = Kacc[mu];
+                }
+            }
+        }
+        T eL[DS];
+#pragma unroll 1
+        for (int l = 0; l < NLEG; ++l) {
+            const int s = (a.assign != nullptr) ? a.assign[h * NLEG + l] : 0;
+            const io_t* ep = ein + ((e * NLEG + l) * a.S + s) * a.ds_in;
+            T v[DS];
+#pragma unroll
+            for (int mu = 0; mu < DS; ++mu) v[mu] = (mu < a.ds_in) ? f.from_io(ep[mu]) : f.zero();
+            if (l < N) {
+                T* dst = base + l * DS * BLOCK;     // current (1, l)
+#pragma unroll
+                for (int mu = 0; mu < DS; ++mu) dst[mu * BLOCK] = v[mu];
+            } else {
+#pragma unroll
+                for (int mu = 0; mu < DS; ++mu) eL[mu] = v[mu];
+            }
+        }
+        // a2: P^2 of every internal range (length 2..N-1), flat index sbase(m) + i
+        T* X = base + OFF_SA * BLOCK;     // P^2 inputs of the inverse (reuses SA slots)
+        T* Y = base + OFF_INV * BLOCK;    // 1/P^2
+#pragma unroll 1
+        for (int m = 2; m < N; ++m) {
+#pragma unroll 1
+            for (int i = 0; i + m - 1 < N; ++i) {
+                T Ka[D], Kb[D], P[D];
+                load(kvec(i), Ka, D);
+                load(kvec(i + m), Kb, D);
+#pragma unroll
+                for (int mu = 0; mu < D; ++mu) P[mu] = f.tsub(Kb[mu], Ka[mu]);
+                X[(g.sbase(m) + i) * BLOCK] = f.inv_input(f.template dot<D, METRIC>(P, P));
+            }
+        }
+        // a3: all inverses.  F_p: Montgomery simultaneous inversion (prefix
+        // products, one Fermat inverse, backward sweep); C64: per range.
+        bool singular = false;
+        const int NS = g.ns();
+        if constexpr (F::kIsFp) {
+            T c = X[0];
+            Y[0] = c;
+#pragma unroll 1
+            for (int s = 1; s < NS; ++s) {
+                c = f.inv_mul(c, X[s * BLOCK]);
+                Y[s * BLOCK] = c;
+            }
+            singular = f.is_zero(c);
+            T r = f.inv_scalar(c);
+#pragma unroll 1
+            for (int s = NS - 1; s > 0; --s) {
+                const T x = X[s * BLOCK];
+                Y[s * BLOCK] = f.inv_store(f.inv_mul(Y[(s - 1) * BLOCK], r));
+                r = f.inv_mul(r, x);
+            }
+            Y[0] = f.inv_store(r);
+        } else {
+#pragma unroll 1
+            for (int s = 0; s < NS; ++s) {
+                const T x = X[s * BLOCK];
+                singular |= f.is_zero(x);
+                Y[s * BLOCK] = f.inv_scalar(x);
+            }
+        }
+
+        // a4: the recursion, by increasing length m
+        io_t result = f.zero_io();
+#pragma unroll 1
+        for (int m = 2; m <= N; ++m) {
+#pragma unroll 1
+            for (int i = 0; i + m - 1 < N; ++i) {
+                T Ki[D], Kj[D];
+                load(kvec(i), Ki, D);
+                load(kvec(i + m), Kj, D);
+                Acc acc[DS];
+                f.template acc_zero<DS>(acc);
+                C sa = f.czero();
+#pragma unroll 1
+                for (int b = 0; b < m - 1; ++b) {
+                    const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
+                    T pb[DS], sf[DS], Kt[D], PA[D], PB[D], dP[D];
+                    load(jvec(lenA, i), pb, DS);
+                    load(jvec(lenB, i + b + 1), sf, DS);
+                    load(kvec(i + b + 1), Kt, D);
+#pragma unroll
+                    for (int mu = 0; mu < D; ++mu) {
+                        PA[mu] = f.tsub(Kt[mu], Ki[mu]);
+                        PB[mu] = f.tsub(Kj[mu], Kt[mu]);
+                        dP[mu] = f.tsub(PA[mu], PB[mu]);
+                    }
+                    // three-gluon vertex of the split at s = i + b
+                    const C adj = f.template dot<DS, METRIC>(pb, sf);
+                    const C pa_jb = f.template dot<D, METRIC>(PA, sf);
+                    const C pb_ja = f.template dot<D, METRIC>(PB, pb);
+                    sa = f.cadd(sa, adj);
+                    C csuf = f.cdbl(pb_ja);
+                    if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(base[(OFF_SA + g.sbase(lenA) + i) * BLOCK]));
+                    C cpre = f.cneg(f.cdbl(pa_jb));
+                    if (lenB >= 2)
+                        cpre = f.csub(cpre, f.t_to_c(base[(OFF_SA + g.sbase(lenB) + i + b + 1) * BLOCK]));
+                    f.template acc2<DS>(acc, csuf, sf, cpre, pb);
+                    f.template acc1<D>(acc, adj, dP);
+                    // four-gluon vertex: prefix [i, i+a], inner [i+a+1, i+b], suffix sf
+                    int q = 0;
+#pragma unroll 1
+                    for (; q + 1 < b; q += 2) {
+                        T pa0[DS], pa1[DS], in0[DS], in1[DS];
+                        load(jvec(q + 1, i), pa0, DS);
+                        load(jvec(q + 2, i), pa1, DS);
+                        load(jvec(b - q, i + q + 1), in0, DS);
+                        load(jvec(b - q - 1, i + q + 2), in1, DS);
+                        const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
+                        const C g1 = f.cdbl(f.template dot<DS, METRIC>(pa1, sf));
+                        f.template acc2<DS>(acc, g0, in0, g1, in1);
+                    }
+                    if (q < b) {
+                        T pa0[DS], in0[DS];
+                        load(jvec(q + 1, i), pa0, DS);
+                        load(jvec(b - q, i + q + 1), in0, DS);
+                        const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
+                        f.template acc1<DS>(acc, g0, in0);
+                    }
+                }
+                if (m < N) {
+                    const int sidx = g.sbase(m) + i;
+                    T J[DS];
+                    f.template finish<DS>(acc, Y[sidx * BLOCK], J);
+                    T* dst = jvec(m, i);
+#pragma unroll
+                    for (int mu = 0; mu < DS; ++mu) dst[mu * BLOCK] = J[mu];
+                    base[(OFF_SA + sidx) * BLOCK] = f.c_to_t(sa);
+                } else {
+                    // a5: contract the top bracket with the last polarisation
+                    result = f.template amplitude<DS, METRIC>(acc, eL);
+                }
+            }
+        }
+        out[u] = singular ? f.zero_io() : result;
+        if (a.status != nullptr && h == 0) a.status[e] = singular ? 1 : 0;
+    }
+}
+
+}  // namespace bgk

@@ -1,0 +1,228 @@
+// bg_field.cuh -- arithmetic policies of the compact recursion kernel.
+//
+// Both policies expose the same operations so that bg_compact.cuh is written
+// once:
+//   T   stored element (table entries: currents, momenta, SA, 1/P^2)
+//   C   coefficient (result of a dot product, scalar arithmetic)
+//   A   accumulator element of R(i,j)
+//   dot<D, METRIC>(a, b)          metric dot over D components -> C
+//   cadd / csub / cdbl / cneg     coefficient arithmetic
+//   acc1<K>(acc, c, v)            acc[0..K) += c v
+//   acc2<K>(acc, c1, v1, c2, v2)  acc[0..K) += c1 v1 + c2 v2
+//   finish(acc, inv) -> T[]       J = R / P^2 from the accumulator
+//   amplitude(acc, eps_last)      A = eps_n . R_top
+//
+// F_p (Sec. 3: p < 2^31, every intermediate reduced mod p).  Montgomery
+// representation with R = 2^32; a value "at level L" is x R^L mod p.
+//   * stored table entries are at level 1 and fully reduced (< p);
+//   * redc(t) = t R^-1 mod p in [0, 2p) for t < p 2^32: one 32-bit multiply
+//     (m = lo(t) (-p^-1)) and one 32x32+64 multiply-add whose high word is
+//     the result;
+//   * a product of two reduced values is < p^2 and a sum of two is < 2 p^2 <
+//     p 2^32, so products are reduced in PAIRS: two multiply-adds, one redc;
+//   * a dot product sums its redc outputs (level 1) in 64 bits and applies
+//     one more redc: the coefficient is at level 0, in [0, p];
+//   * R(i,j) accumulates redc outputs of (level 0 coefficient) x (level 1
+//     entry) products, i.e. level-0 terms, in 64 bits; finish() applies redc
+//     (level -1) and multiplies by 1/P^2 stored at level 3, giving level 1;
+//   * metric signs: terms with eta = -1 are summed as products with the
+//     negated operand (p - a), so every pair is a plain sum.
+// C64 (Sec. 3, complex double): FMA-based complex arithmetic; dot products and
+// accumulations are 4 FP64 FMAs per complex term; the metric sign becomes the
+// sign of an FMA operand.
+#pragma once
+#include <cstdint>
+
+namespace bgk {
+
+template <int METRIC>
+__host__ __device__ constexpr int msign(int mu) {
+    return METRIC == 0 ? (mu == 0 ? 1 : -1) : ((mu & 1) ? -1 : 1);
+}
+
+struct FpOps {
+    using T = uint32_t;
+    using C = uint32_t;
+    using A = uint64_t;
+    using io_t = uint32_t;
+    static constexpr bool kIsFp = true;
+
+    uint32_t p, pinv, r2, r3, one, pm2;   // r2 = R^2, r3 = R^3, one = R (mod p)
+
+    __device__ __forceinline__ uint32_t redc(uint64_t t) const {
+        const uint32_t m = static_cast<uint32_t>(t) * pinv;
+        return static_cast<uint32_t>((static_cast<uint64_t>(m) * p + t) >> 32);
+    }
+    __device__ __forceinline__ uint32_t fold(uint32_t x) const { return min(x, x - p); }
+    // full Montgomery product of reduced operands, level la + lb - 1, in [0, p)
+    __device__ __forceinline__ uint32_t mmul(uint32_t a, uint32_t b) const {
+        return fold(redc(static_cast<uint64_t>(a) * b));
+    }
+    __device__ __forceinline__ uint32_t madd(uint32_t a, uint32_t b) const { return fold(a + b); }
+    __device__ __forceinline__ uint32_t msub(uint32_t a, uint32_t b) const {
+        const uint32_t d = a - b;
+        return min(d, d + p);
+    }
+
+    __device__ __forceinline__ T zero() const { return 0u; }
+    __device__ __forceinline__ T from_io(io_t x) const { return mmul(x, r2); }      // level 1
+    __device__ __forceinline__ T tadd(T a, T b) const { return madd(a, b); }
+    __device__ __forceinline__ T tsub(T a, T b) const { return msub(a, b); }
+
+    // sum_mu eta_mu a_mu b_mu -> level 0, in [0, p].  All terms of the sign
+    // that occurs most often are summed directly; the others use p - a.
+    template <int D, int METRIC>
+    __device__ __forceinline__ C dot(const T* a, const T* b) const {
+        constexpr int nneg = []() { int c = 0; for (int mu = 0; mu < D; ++mu) c += msign<METRIC>(mu) < 0; return c; }();
+        constexpr int flip = (nneg * 2 > D) ? -1 : 1;   // sign that is NOT negated
+        uint64_t S = 0;
+        uint64_t t = 0;
+        int c = 0;
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) {
+            const uint32_t x = (msign<METRIC>(mu) == flip) ? a[mu] : (p - a[mu]);
+            t += static_cast<uint64_t>(x) * b[mu];
+            if (++c == 2) { S += redc(t); t = 0; c = 0; }
+        }
+        if (c) S += redc(t);
+        const uint32_t r = fold(redc(S));          // flip * dot, level 0, [0, p)
+        return flip > 0 ? r : p - r;               // [0, p]
+    }
+    __device__ __forceinline__ C cadd(C a, C b) const { return madd(a, b); }        // [0, p)
+    __device__ __forceinline__ C csub(C a, C b) const { return msub(a, b); }        // [0, p]
+    __device__ __forceinline__ C cdbl(C a) const { return fold(a + a); }            // a <= p -> [0, p]
+    __device__ __forceinline__ C cneg(C a) const { return p - a; }                  // [0, p]
+    __device__ __forceinline__ C czero() const { return 0u; }
+    __device__ __forceinline__ T c_to_t(C a) const { return fold(a); }              // stored SA
+    __device__ __forceinline__ C t_to_c(T a) const { return a; }
+
+    template <int K>
+    __device__ __forceinline__ void acc_zero(A* acc) const {
+#pragma unroll
+        for (int mu = 0; mu < K; ++mu) acc[mu] = 0;
+    }
+    template <int K>
+    __device__ __forceinline__ void acc1(A* acc, C c, const T* v) const {
+#pragma unroll
+        for (int mu = 0; mu < K; ++mu) acc[mu] += redc(static_cast<uint64_t>(c) * v[mu]);
+    }
+    template <int K>
+    __device__ __forceinline__ void acc2(A* acc, C c1, const T* v1, C c2, const T* v2) const {
+#pragma unroll
+        for (int mu = 0; mu < K; ++mu)
+            acc[mu] += redc(static_cast<uint64_t>(c1) * v1[mu] + static_cast<uint64_t>(c2) * v2[mu]);
+    }
+    // J = R / P^2: redc(acc) is level -1; times 1/P^2 at level 3 -> level 1.
+    template <int K>
+    __device__ __forceinline__ void finish(const A* acc, T inv3, T* out) const {
+#pragma unroll
+        for (int mu = 0; mu < K; ++mu) out[mu] = mmul(redc(acc[mu]), inv3);
+    }
+    template <int K, int METRIC>
+    __device__ __forceinline__ io_t amplitude(const A* acc, const T* eps_last) const {
+        T r[K];
+#pragma unroll
+        for (int mu = 0; mu < K; ++mu) r[mu] = mmul(redc(acc[mu]), r3);   // level 1
+        const C a = dot<K, METRIC>(eps_last, r);                           // level 0 = canonical
+        return a == p ? 0u : a;
+    }
+    // P^2 (level 0 coefficient) -> level 1 input of the batched inverse
+    __device__ __forceinline__ T inv_input(C p2) const { return mmul(fold(p2), r2); }
+    __device__ __forceinline__ T inv_mul(T a, T b) const { return mmul(a, b); }
+    __device__ __forceinline__ T inv_scalar(T x) const {     // x^(p-2), level 1 in and out
+        T r = one;
+#pragma unroll 1
+        for (int bit = 30; bit >= 0; --bit) {
+            r = mmul(r, r);
+            if ((pm2 >> bit) & 1u) r = mmul(r, x);
+        }
+        return r;
+    }
+    __device__ __forceinline__ T inv_store(T inv1) const { return mmul(inv1, r3); }   // level 3
+    __device__ __forceinline__ bool is_zero(T x) const { return x == 0u; }
+    __device__ __forceinline__ io_t zero_io() const { return 0u; }
+};
+
+struct C64Ops {
+    using T = double2;
+    using C = double2;
+    using A = double2;
+    using io_t = double2;
+    static constexpr bool kIsFp = false;
+
+    __device__ __forceinline__ T zero() const { return make_double2(0.0, 0.0); }
+    __device__ __forceinline__ T from_io(io_t x) const { return x; }
+    __device__ __forceinline__ T tadd(T a, T b) const { return make_double2(a.x + b.x, a.y + b.y); }
+    __device__ __forceinline__ T tsub(T a, T b) const { return make_double2(a.x - b.x, a.y - b.y); }
+
+    template <int D, int METRIC>
+    __device__ __forceinline__ C dot(const T* a, const T* b) const {
+        double re = 0.0, im = 0.0;
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) {
+            if (msign<METRIC>(mu) > 0) {
+                re = fma(a[mu].x, b[mu].x, re);
+                re = fma(-a[mu].y, b[mu].y, re);
+                im = fma(a[mu].x, b[mu].y, im);
+                im = fma(a[mu].y, b[mu].x, im);
+            } else {
+                re = fma(-a[mu].x, b[mu].x, re);
+                re = fma(a[mu].y, b[mu].y, re);
+                im = fma(-a[mu].x, b[mu].y, im);
+                im = fma(-a[mu].y, b[mu].x, im);
+            }
+        }
+        return make_double2(re, im);
+    }
+    __device__ __forceinline__ C cadd(C a, C b) const { return make_double2(a.x + b.x, a.y + b.y); }
+    __device__ __forceinline__ C csub(C a, C b) const { return make_double2(a.x - b.x, a.y - b.y); }
+    __device__ __forceinline__ C cdbl(C a) const { return make_double2(a.x + a.x, a.y + a.y); }
+    __device__ __forceinline__ C cneg(C a) const { return make_double2(-a.x, -a.y); }
+    __device__ __forceinline__ C czero() const { return make_double2(0.0, 0.0); }
+    __device__ __forceinline__ T c_to_t(C a) const { return a; }
+    __device__ __forceinline__ C t_to_c(T a) const { return a; }
+
+    template <int K>
+    __device__ __forceinline__ void acc_zero(A* acc) const {
+#pragma unroll
+        for (int mu = 0; mu < K; ++mu) acc[mu] = make_double2(0.0, 0.0);
+    }
+    template <int K>
+    __device__ __forceinline__ void acc1(A* acc, C c, const T* v) const {
+#pragma unroll
+        for (int mu = 0; mu < K; ++mu) {
+            acc[mu].x = fma(c.x, v[mu].x, acc[mu].x);
+            acc[mu].x = fma(-c.y, v[mu].y, acc[mu].x);
+            acc[mu].y = fma(c.x, v[mu].y, acc[mu].y);
+            acc[mu].y = fma(c.y, v[mu].x, acc[mu].y);
+        }
+    }
+    template <int K>
+    __device__ __forceinline__ void acc2(A* acc, C c1, const T* v1, C c2, const T* v2) const {
+        acc1<K>(acc, c1, v1);
+        acc1<K>(acc, c2, v2);
+    }
+    template <int K>
+    __device__ __forceinline__ void finish(const A* acc, T inv, T* out) const {
+#pragma unroll
+        for (int mu = 0; mu < K; ++mu)
+            out[mu] = make_double2(fma(acc[mu].x, inv.x, -acc[mu].y * inv.y),
+                                   fma(acc[mu].x, inv.y, acc[mu].y * inv.x));
+    }
+    template <int K, int METRIC>
+    __device__ __forceinline__ io_t amplitude(const A* acc, const T* eps_last) const {
+        return dot<K, METRIC>(eps_last, acc);
+    }
+    __device__ __forceinline__ T inv_input(C p2) const { return p2; }
+    __device__ __forceinline__ T inv_mul(T a, T b) const { return a; }   // unused
+    __device__ __forceinline__ T inv_scalar(T z) const {                  // 1/z = conj(z)/|z|^2
+        const double w = fma(z.x, z.x, z.y * z.y);
+        const double r = __drcp_rn(w);
+        return make_double2(z.x * r, -z.y * r);
+    }
+    __device__ __forceinline__ T inv_store(T v) const { return v; }
+    __device__ __forceinline__ bool is_zero(T z) const { return z.x == 0.0 && z.y == 0.0; }
+    __device__ __forceinline__ io_t zero_io() const { return make_double2(0.0, 0.0); }
+};
+
+}  // namespace bgk

@@ -10,26 +10,30 @@
 
 #include <vector>
 
+#include "bg_compact.cuh"
 #include "bg_kernel.cuh"
 
 namespace bgk {
 
 struct KernelEntry {
     int field;          // 0 = C64, 1 = F_p (bg_field)
-    int n, D, DS, metric;
+    int n;              // gluons; 0 for the compact kernel (any n)
+    int D, DS, metric;
     bool global_table;  // table in global scratch (true) or shared memory
+    bool compact;       // run-time n (bg_compact_kernel) or unrolled per n
     int block;          // threads per block
-    int words;          // table elements per thread
+    int words;          // table elements per thread (unrolled kernels)
     int elem_bytes;     // sizeof(T)
     const void* func;   // the __global__ function
-    void (*launch)(const void* field_params, const LaunchArgs& a, dim3 grid, size_t smem,
+    // launch(field params, args (LaunchArgs or CompactArgs), grid, smem, stream)
+    void (*launch)(const void* field_params, const void* args, dim3 grid, size_t smem,
                    cudaStream_t stream);
 };
 
 template <class F, int NLEG, int D, int DS, int M, int B, bool G>
-void launch_impl(const void* fp, const LaunchArgs& a, dim3 grid, size_t smem, cudaStream_t s) {
+void launch_impl(const void* fp, const void* args, dim3 grid, size_t smem, cudaStream_t s) {
     const F& f = *static_cast<const F*>(fp);
-    bg_recursion_kernel<F, NLEG, D, DS, M, B, G><<<grid, B, smem, s>>>(f, a);
+    bg_recursion_kernel<F, NLEG, D, DS, M, B, G><<<grid, B, smem, s>>>(f, *static_cast<const LaunchArgs*>(args));
 }
 
 template <class F, int NLEG, int D, int DS, int M, int B, bool G>
@@ -41,11 +45,36 @@ KernelEntry make_entry() {
     e.DS = DS;
     e.metric = M;
     e.global_table = G;
+    e.compact = false;
     e.block = B;
     e.words = Frame<NLEG - 1, D, DS>::WORDS;
     e.elem_bytes = sizeof(typename F::T);
     e.func = reinterpret_cast<const void*>(&bg_recursion_kernel<F, NLEG, D, DS, M, B, G>);
     e.launch = &launch_impl<F, NLEG, D, DS, M, B, G>;
+    return e;
+}
+
+template <class F, int D, int DS, int M, int B, bool G>
+void launch_compact(const void* fp, const void* args, dim3 grid, size_t smem, cudaStream_t s) {
+    const F& f = *static_cast<const F*>(fp);
+    bg_compact_kernel<F, D, DS, M, B, G><<<grid, B, smem, s>>>(f, *static_cast<const CompactArgs*>(args));
+}
+
+template <class F, int D, int DS, int M, int B, bool G>
+KernelEntry make_compact() {
+    KernelEntry e;
+    e.field = F::kIsFp ? 1 : 0;
+    e.n = 0;
+    e.D = D;
+    e.DS = DS;
+    e.metric = M;
+    e.global_table = G;
+    e.compact = true;
+    e.block = B;
+    e.words = 0;
+    e.elem_bytes = sizeof(typename F::T);
+    e.func = reinterpret_cast<const void*>(&bg_compact_kernel<F, D, DS, M, B, G>);
+    e.launch = &launch_compact<F, D, DS, M, B, G>;
     return e;
 }
 
@@ -56,34 +85,53 @@ constexpr int kBlockFpSmem = 64;
 constexpr int kBlockFpGlobal = 128;
 constexpr int kBlockC64 = 64;
 
-// Table placement per n: F_p keeps the table in shared memory up to n = 9
-// and in global scratch from n = 8 (both are built for n = 8, 9 so they can
-// be compared); C64 always uses global scratch (16-byte elements).
-template <int NLEG, int D, int M, bool FP>
-void add_dims(std::vector<KernelEntry>& v) {
+// Unrolled kernels (one per n) are built for F_p with the table in shared
+// memory; they are kept to compare against the compact kernel.
+template <int NLEG, int D, int M>
+void add_unrolled(std::vector<KernelEntry>& v) {
+    v.push_back(make_entry<FieldFp, NLEG, D, D, M, kBlockFpSmem, false>());
+}
+
+template <int NLEG>
+void register_unrolled(std::vector<KernelEntry>& v) {
+    add_unrolled<NLEG, 4, 0>(v);
+    add_unrolled<NLEG, 6, 0>(v);
+    add_unrolled<NLEG, 8, 0>(v);
+    add_unrolled<NLEG, 4, 1>(v);
+    add_unrolled<NLEG, 6, 1>(v);
+    add_unrolled<NLEG, 8, 1>(v);
+}
+
+// Compact kernels: every (D, D_s) pair with D <= D_s in {4, 6, 8}, both
+// metrics; F_p with shared or global table, C64 with global table.
+constexpr int kBlockFpCompactSmem = 64;
+constexpr int kBlockFpCompactGlobal = 128;
+constexpr int kBlockC64Compact = 64;
+
+template <int D, int DS, int M, bool FP>
+void add_compact_dims(std::vector<KernelEntry>& v) {
     if constexpr (FP) {
-        if constexpr (NLEG <= 9) v.push_back(make_entry<FieldFp, NLEG, D, D, M, kBlockFpSmem, false>());
-        if constexpr (NLEG >= 8) v.push_back(make_entry<FieldFp, NLEG, D, D, M, kBlockFpGlobal, true>());
+        v.push_back(make_compact<FpOps, D, DS, M, kBlockFpCompactSmem, false>());
+        v.push_back(make_compact<FpOps, D, DS, M, kBlockFpCompactGlobal, true>());
     } else {
-        v.push_back(make_entry<FieldC64, NLEG, D, D, M, kBlockC64, true>());
+        v.push_back(make_compact<C64Ops, D, DS, M, kBlockC64Compact, true>());
     }
 }
 
-// (D, D_s) are compiled square, D = D_s in {4, 6, 8}; a request (d, D_s)
-// runs on the smallest instance with D >= max(d, D_s), zero padded.
-template <int NLEG, bool FP>
-void register_n(std::vector<KernelEntry>& v) {
-    add_dims<NLEG, 4, 0, FP>(v);
-    add_dims<NLEG, 6, 0, FP>(v);
-    add_dims<NLEG, 8, 0, FP>(v);
-    add_dims<NLEG, 4, 1, FP>(v);
-    add_dims<NLEG, 6, 1, FP>(v);
-    add_dims<NLEG, 8, 1, FP>(v);
+template <int D, int DS, bool FP>
+void register_compact(std::vector<KernelEntry>& v) {
+    add_compact_dims<D, DS, 0, FP>(v);
+    add_compact_dims<D, DS, 1, FP>(v);
 }
 
 }  // namespace bgk
 
 #define BG_DEFINE_REGISTRY(NLEG, FP, TAG)                                     \
     void bg_register_##TAG##_n##NLEG(std::vector<bgk::KernelEntry>& v) {      \
-        bgk::register_n<NLEG, FP>(v);                                         \
+        bgk::register_unrolled<NLEG>(v);                                      \
+    }
+
+#define BG_DEFINE_COMPACT(D, DS, FP, TAG)                                     \
+    void bg_register_compact_##TAG##_##D##_##DS(std::vector<bgk::KernelEntry>& v) { \
+        bgk::register_compact<D, DS, FP>(v);                                  \
     }

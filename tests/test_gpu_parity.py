@@ -40,21 +40,30 @@ def _dev_c(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
 
 
-def run_fp(k, eps, p, metric, n_states=1, assign=None, table=None):
+class _env:
+    """Temporarily set BG_TABLE / BG_KERNEL (read at plan creation)."""
+
+    def __init__(self, **kv):
+        self.kv = {k: v for k, v in kv.items() if v is not None}
+
+    def __enter__(self):
+        self.old = {k: os.environ.get(k) for k in self.kv}
+        os.environ.update(self.kv)
+
+    def __exit__(self, *exc):
+        for k, v in self.old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def run_fp(k, eps, p, metric, n_states=1, assign=None, table=None, kernel=None):
     bg = _bg()
     E, n, d = k.shape
     Ds = eps.shape[-1]
-    old = os.environ.get("BG_TABLE")
-    if table:
-        os.environ["BG_TABLE"] = table
-    try:
+    with _env(BG_TABLE=table, BG_KERNEL=kernel):
         plan = bg.Plan(n, d, Ds, bg.FIELD_FP, p, metric, n_states, assign)
-    finally:
-        if table:
-            if old is None:
-                del os.environ["BG_TABLE"]
-            else:
-                os.environ["BG_TABLE"] = old
     out, st = plan.eval(_dev_u32(k), _dev_u32(eps))
     import torch
     torch.cuda.synchronize()
@@ -90,7 +99,7 @@ def test_fp_bit_exact(n, d, Ds, metric, p):
     assert np.array_equal(out, ref), plan.describe()
 
 
-@pytest.mark.parametrize("n", [8, 9])
+@pytest.mark.parametrize("n", [5, 8, 9, 12])
 @pytest.mark.parametrize("table", ["shared", "global"])
 def test_fp_table_placements_agree(n, table):
     E = 1000
@@ -98,6 +107,18 @@ def test_fp_table_placements_agree(n, table):
     ref, _ = C.amp_fp(k, eps, P, 0)
     out, _, plan = run_fp(k, eps, P, 0, table=table)
     assert ("table=global" in plan.describe()) == (table == "global")
+    assert np.array_equal(out, ref)
+
+
+@pytest.mark.parametrize("n,d,metric", [(5, 4, 0), (6, 6, 1), (7, 8, 0), (8, 6, 0), (8, 4, 1)])
+def test_fp_unrolled_kernel_bit_exact(n, d, metric):
+    """The per-n unrolled kernel (kept for comparison) is bit-exact too."""
+    E = 2 * 64 + 13
+    p = P if metric == 0 else PM
+    k, eps = G.fp_batch(300 + n, E, n, d, d, p, metric)
+    ref, _ = C.amp_fp(k, eps, p, metric)
+    out, _, plan = run_fp(k, eps, p, metric, kernel="unrolled")
+    assert "kernel=unrolled" in plan.describe()
     assert np.array_equal(out, ref)
 
 
