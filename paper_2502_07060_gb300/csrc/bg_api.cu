@@ -10,8 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/bg.h"
-#include "bg_instances.cuh"
+#include "bg_internal.h"
 
 #define BG_REG(TAG, N) void bg_register_##TAG##_n##N(std::vector<bgk::KernelEntry>&);
 BG_REG(fp, 5) BG_REG(fp, 6) BG_REG(fp, 7) BG_REG(fp, 8)
@@ -23,8 +22,10 @@ BG_REGC(c64, 8, 8)
 #undef BG_REGC
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
+
+namespace bgi {
 
 bg_status fail(bg_status s, const char* fmt, ...) {
     char buf[512];
@@ -52,9 +53,9 @@ const std::vector<bgk::KernelEntry>& registry() {
     return v;
 }
 
-uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t m) { return (a * b) % m; }   // a, b < 2^31
+static uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t m) { return (a * b) % m; }   // a, b < 2^31
 
-uint64_t powmod64(uint64_t a, uint64_t e, uint64_t m) {
+static uint64_t powmod64(uint64_t a, uint64_t e, uint64_t m) {
     uint64_t r = 1 % m;
     a %= m;
     while (e) {
@@ -66,7 +67,7 @@ uint64_t powmod64(uint64_t a, uint64_t e, uint64_t m) {
 }
 
 // Deterministic Miller-Rabin for n < 2^32 (bases 2, 3, 5, 7 suffice below 3.2e9).
-bool is_prime_u32(uint32_t n) {
+static bool is_prime_u32(uint32_t n) {
     if (n < 2) return false;
     for (uint32_t q : {2u, 3u, 5u, 7u}) {
         if (n == q) return true;
@@ -88,8 +89,6 @@ bool is_prime_u32(uint32_t n) {
     return true;
 }
 
-int round_dim(int x) { return x <= 4 ? 4 : (x <= 6 ? 6 : 8); }
-
 bg_status check_device_ptr(const void* ptr, const char* what, int device) {
     cudaPointerAttributes attr;
     cudaError_t err = cudaPointerGetAttributes(&attr, ptr);
@@ -105,27 +104,16 @@ bg_status check_device_ptr(const void* ptr, const char* what, int device) {
     return BG_OK;
 }
 
-}  // namespace
+int round_dim(int x) { return x <= 4 ? 4 : (x <= 6 ? 6 : 8); }
 
-struct bg_plan {
-    int n, d, Ds;
-    bg_field field;
-    uint32_t p;
-    bg_metric metric;
-    int S, H;
-    std::vector<uint8_t> assign;      // host copy [H][n]
-    uint8_t* d_assign = nullptr;      // device copy when H > 1
-    int device = -1;                  // device of d_assign / attribute setup
-    const bgk::KernelEntry* entry = nullptr;
-    int words = 0;                    // table elements per thread
-    bgk::FieldFp fp{};                // unrolled kernels
-    bgk::FieldC64 c64{};
-    bgk::FpOps fpo{};                 // compact kernels
-    bgk::C64Ops c64o{};
-    int sm_count = 0;
-    int blocks_per_sm = 0;
-    size_t smem_bytes = 0;            // dynamic shared memory per block
-};
+}  // namespace bgi
+
+using bgi::check_device_ptr;
+using bgi::fail;
+using bgi::registry;
+using bgi::round_dim;
+using bgi::is_prime_u32;
+using bgi::mulmod64;
 
 extern "C" {
 
