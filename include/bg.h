@@ -129,6 +129,32 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta,
                   const void* eps, void* out, uint8_t* status,
                   void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
+/*
+ * bg_eval_noalloc -- the same evaluation as bg_eval, for callers that cannot
+ * allocate device memory: a framework that owns the device-memory budget
+ * through its own allocator, a latency-critical loop that cannot afford the
+ * implicit synchronisation of cudaMalloc, or code running where CUDA
+ * allocation calls are not permitted.  The paper has no counterpart; this is
+ * an interface convenience of this library.
+ *
+ * The call allocates nothing.  Its scratch table is a statically sized
+ * device array of 64 MiB inside libbg.so, present on every device that loads
+ * the library until the process exits.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the array: calls whose kernels overlap on the GPU race, so order them on
+ * one stream.  Nothing in the array needs to start at zero.
+ *
+ *   plan, E, momenta, eps, out, status, stream: as for bg_eval (buffers on
+ *   the current device, caller-owned).  Returns BG_ERR_INVALID_ARG when
+ *   E * n_assign exceeds 2^40 work items, BG_ERR_UNSUPPORTED when one thread
+ *   block's table would not fit in the 64 MiB array; fewer blocks run at once
+ *   than with bg_eval when the array limits residency.
+ */
+bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void* momenta,
+                          const void* eps, void* out, uint8_t* status,
+                          cudaStream_t stream);
+
 /* bg_plan_describe -- NUL-terminated one-line description of the kernel the
  * plan launches (variant, block size, shared memory, workspace per thread)
  * written to buf[0..len); returns BG_ERR_INVALID_ARG when it does not fit. */

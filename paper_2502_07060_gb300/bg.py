@@ -31,7 +31,7 @@ ALTERNATING = 1
 
 # bg_plan_create / bg_eval / ... as declared in include/bg.h
 EXPORTED = ("bg_plan_create", "bg_plan_destroy", "bg_workspace_size", "bg_eval",
-            "bg_plan_describe", "bg_strerror", "bg_last_error", "bg_version")
+            "bg_eval_noalloc", "bg_plan_describe", "bg_strerror", "bg_last_error", "bg_version")
 
 LIB_PATH = _build.LIB
 
@@ -52,6 +52,8 @@ def load_library(path=None):
     lib.bg_workspace_size.restype = ctypes.c_int
     lib.bg_eval.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.bg_eval.restype = ctypes.c_int
+    lib.bg_eval_noalloc.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, vp]
+    lib.bg_eval_noalloc.restype = ctypes.c_int
     lib.bg_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.bg_plan_describe.restype = ctypes.c_int
     lib.bg_strerror.argtypes = [ctypes.c_int]
@@ -167,6 +169,22 @@ class Plan:
         ws_bytes = workspace.numel() if workspace is not None else 0
         _check(_lib.bg_eval(self._h, E, _ptr(momenta), _ptr(eps), _ptr(out), _ptr(status),
                             _ptr(workspace), ws_bytes, _stream_handle(stream)))
+        return out, status
+
+
+    def eval_noalloc(self, momenta, eps, out=None, status=None, stream=None):
+        """bg_eval_noalloc: the same result as eval() without any device
+        allocation by the library (scratch in its static device array).
+        ``out``/``status`` are allocated here by torch only when not given."""
+        E = momenta.shape[0]
+        dev = momenta.device
+        if out is None:
+            shape = (E,) if self.n_assign == 1 else (E, self.n_assign)
+            out = torch.empty(shape, dtype=momenta.dtype, device=dev)
+        if status is None:
+            status = torch.empty(E, dtype=torch.uint8, device=dev)
+        _check(_lib.bg_eval_noalloc(self._h, E, _ptr(momenta), _ptr(eps), _ptr(out), _ptr(status),
+                                    _stream_handle(stream)))
         return out, status
 
 
