@@ -19,8 +19,7 @@
 // itself is built and stored next to its current.  Per range of length m this
 // costs m(m+1)/2 - 1 vector updates instead of 2(m-1) + 3 C(m-1,2).
 //
-// Per-point table (element w of thread t at [w * BLOCK + t]: conflict-free in
-// shared memory, coalesced in global memory), for N = n - 1 legs:
+// Per-point table for N = n - 1 legs (layout: TableIO below):
 //   currents of length 1..N-1 (D_s each), prefix sums K_0..K_N of the momenta
 //   (D each; P_{i,j} = K_{j+1} - K_i), SA and 1/P^2 per internal range.
 // Shared-memory placement keeps the table on chip; global placement keeps it
@@ -50,17 +49,73 @@ struct CompactArgs {
     void* ws;                   // global table (global placement)
 };
 
-// Table geometry for N = n - 1 recursion legs (host and device).
+// Table geometry for N = n - 1 recursion legs (host and device), in table
+// elements per thread.  Region starts are rounded up to 4 elements so that
+// vector accesses stay aligned.
 struct Geometry {
     int N;
+    __host__ __device__ static int up4(int x) { return (x + 3) & ~3; }
     __host__ __device__ int jbase(int len) const { return ((len - 1) * (2 * N + 2 - len)) >> 1; }
     __host__ __device__ int nj() const { return jbase(N); }              // currents, length 1..N-1
     __host__ __device__ int ns() const { return jbase(N) - N; }          // internal ranges
     __host__ __device__ int sbase(int len) const { return jbase(len) - N; }
-    __host__ __device__ int off_k(int DS) const { return nj() * DS; }
-    __host__ __device__ int off_sa(int D, int DS) const { return off_k(DS) + (N + 1) * D; }
+    __host__ __device__ int off_k(int DS) const { return up4(nj() * DS); }
+    __host__ __device__ int off_sa(int D, int DS) const { return off_k(DS) + up4((N + 1) * D); }
     __host__ __device__ int off_inv(int D, int DS) const { return off_sa(D, DS) + ns(); }
     __host__ __device__ int words(int D, int DS) const { return off_inv(D, DS) + ns(); }
+};
+
+// Vector access to the table.  VEC (F_p): a thread's K-component vector is
+// contiguous ([slot][thread][K]); it is read with 16- or 8-byte accesses, and
+// consecutive threads' vectors are adjacent, so a warp's access is contiguous
+// (coalesced in global memory, bank-conflict free in shared memory).  Not VEC
+// (C64, 16-byte elements): component mu of slot s of thread t is at
+// [(s * K + mu) * BLOCK + t], one 16-byte access per component.
+template <class T, bool VEC, int BLOCK>
+struct TableIO {
+    template <int K>
+    __device__ static __forceinline__ T* vec(T* region, int slot) {
+        if constexpr (VEC) return region + slot * BLOCK * K;      // region already offset by t*K
+        else return region + slot * K * BLOCK;                    // region already offset by t
+    }
+    template <int K>
+    __device__ static __forceinline__ void load(const T* p, T* v) {
+        if constexpr (VEC) {
+            if constexpr (K % 4 == 0) {
+#pragma unroll
+                for (int q = 0; q < K / 4; ++q) {
+                    const uint4 x = reinterpret_cast<const uint4*>(p)[q];
+                    v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < K / 2; ++q) {
+                    const uint2 x = reinterpret_cast<const uint2*>(p)[q];
+                    v[2 * q] = x.x; v[2 * q + 1] = x.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int mu = 0; mu < K; ++mu) v[mu] = p[mu * BLOCK];
+        }
+    }
+    template <int K>
+    __device__ static __forceinline__ void store(T* p, const T* v) {
+        if constexpr (VEC) {
+            if constexpr (K % 4 == 0) {
+#pragma unroll
+                for (int q = 0; q < K / 4; ++q)
+                    reinterpret_cast<uint4*>(p)[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < K / 2; ++q)
+                    reinterpret_cast<uint2*>(p)[q] = make_uint2(v[2 * q], v[2 * q + 1]);
+            }
+        } else {
+#pragma unroll
+            for (int mu = 0; mu < K; ++mu) p[mu * BLOCK] = v[mu];
+        }
+    }
 };
 
 template <class F, int D, int DS, int METRIC, int BLOCK, bool GLOBAL_TABLE>
@@ -78,20 +133,21 @@ bg_compact_kernel(const F f, const CompactArgs a) {
     const int OFF_K = g.off_k(DS), OFF_SA = g.off_sa(D, DS), OFF_INV = g.off_inv(D, DS);
 
     extern __shared__ __align__(16) unsigned char bg_smem[];
-    T* base;
+    T* tab;                                   // this block's table
     if constexpr (GLOBAL_TABLE) {
-        base = reinterpret_cast<T*>(a.ws) + static_cast<size_t>(blockIdx.x) * W * BLOCK + threadIdx.x;
+        tab = reinterpret_cast<T*>(a.ws) + static_cast<size_t>(blockIdx.x) * W * BLOCK;
     } else {
-        base = reinterpret_cast<T*>(bg_smem) + threadIdx.x;
+        tab = reinterpret_cast<T*>(bg_smem);
     }
-    // vector accessors: element mu of a vector at word w is base[(w + mu) * BLOCK]
-    auto jvec = [&](int len, int start) { return base + (g.jbase(len) + start) * DS * BLOCK; };
-    auto kvec = [&](int t) { return base + (OFF_K + t * D) * BLOCK; };
-    auto load = [&](const T* p, T* v, int cnt) {
-#pragma unroll
-        for (int mu = 0; mu < DS; ++mu)
-            if (mu < cnt) v[mu] = p[mu * BLOCK];
-    };
+    constexpr bool VEC = F::kIsFp;
+    using IO = TableIO<T, VEC, BLOCK>;
+    const int t = threadIdx.x;
+    T* Jr = tab + (VEC ? t * DS : t);                              // currents
+    T* Kr = tab + OFF_K * BLOCK + (VEC ? t * D : t);               // prefix sums
+    T* Sr = tab + OFF_SA * BLOCK + t;                              // SA per internal range
+    T* Ir = tab + OFF_INV * BLOCK + t;                             // 1/P^2 per internal range
+    auto jvec = [&](int len, int start) { return IO::template vec<DS>(Jr, g.jbase(len) + start); };
+    auto kvec = [&](int i) { return IO::template vec<D>(Kr, i); };
 
     const io_t* kin = static_cast<const io_t*>(a.k);
     const io_t* ein = static_cast<const io_t*>(a.eps);
@@ -112,17 +168,14 @@ bg_compact_kernel(const F f, const CompactArgs a) {
             const io_t* kp = kin + e * NLEG * a.d_in;
             T Kacc[D];
 #pragma unroll
-            for (int mu = 0; mu < D; ++mu) {
-                Kacc[mu] = f.zero();
-                base[(OFF_K + mu) * BLOCK] = Kacc[mu];
-            }
+            for (int mu = 0; mu < D; ++mu) Kacc[mu] = f.zero();
+            IO::template store<D>(kvec(0), Kacc);
 #pragma unroll 1
             for (int l = 0; l < N; ++l) {
 #pragma unroll
-                for (int mu = 0; mu < D; ++mu) {
+                for (int mu = 0; mu < D; ++mu)
                     if (mu < a.d_in) Kacc[mu] = f.tadd(Kacc[mu], f.from_io(kp[l * a.d_in + mu]));
-                    base[(OFF_K + (l + 1) * D + mu) * BLOCK] = Kacc[mu];
-                }
+                IO::template store<D>(kvec(l + 1), Kacc);
             }
         }
         T eL[DS];
@@ -134,24 +187,22 @@ bg_compact_kernel(const F f, const CompactArgs a) {
 #pragma unroll
             for (int mu = 0; mu < DS; ++mu) v[mu] = (mu < a.ds_in) ? f.from_io(ep[mu]) : f.zero();
             if (l < N) {
-                T* dst = base + l * DS * BLOCK;     // current (1, l)
-#pragma unroll
-                for (int mu = 0; mu < DS; ++mu) dst[mu * BLOCK] = v[mu];
+                IO::template store<DS>(jvec(1, l), v);     // current (1, l)
             } else {
 #pragma unroll
                 for (int mu = 0; mu < DS; ++mu) eL[mu] = v[mu];
             }
         }
         // a2: P^2 of every internal range (length 2..N-1), flat index sbase(m) + i
-        T* X = base + OFF_SA * BLOCK;     // P^2 inputs of the inverse (reuses SA slots)
-        T* Y = base + OFF_INV * BLOCK;    // 1/P^2
+        T* X = Sr;     // P^2 inputs of the inverse (reuses the SA slots)
+        T* Y = Ir;     // 1/P^2
 #pragma unroll 1
         for (int m = 2; m < N; ++m) {
 #pragma unroll 1
             for (int i = 0; i + m - 1 < N; ++i) {
                 T Ka[D], Kb[D], P[D];
-                load(kvec(i), Ka, D);
-                load(kvec(i + m), Kb, D);
+                IO::template load<D>(kvec(i), Ka);
+                IO::template load<D>(kvec(i + m), Kb);
 #pragma unroll
                 for (int mu = 0; mu < D; ++mu) P[mu] = f.tsub(Kb[mu], Ka[mu]);
                 X[(g.sbase(m) + i) * BLOCK] = f.inv_input(f.template dot<D, METRIC>(P, P));
@@ -194,8 +245,8 @@ bg_compact_kernel(const F f, const CompactArgs a) {
 #pragma unroll 1
             for (int i = 0; i + m - 1 < N; ++i) {
                 T Ki[D], Kj[D];
-                load(kvec(i), Ki, D);
-                load(kvec(i + m), Kj, D);
+                IO::template load<D>(kvec(i), Ki);
+                IO::template load<D>(kvec(i + m), Kj);
                 Acc acc[DS];
                 f.template acc_zero<DS>(acc);
                 C sa = f.czero();
@@ -203,9 +254,9 @@ bg_compact_kernel(const F f, const CompactArgs a) {
                 for (int b = 0; b < m - 1; ++b) {
                     const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
                     T pb[DS], sf[DS], Kt[D], PA[D], PB[D], dP[D];
-                    load(jvec(lenA, i), pb, DS);
-                    load(jvec(lenB, i + b + 1), sf, DS);
-                    load(kvec(i + b + 1), Kt, D);
+                    IO::template load<DS>(jvec(lenA, i), pb);
+                    IO::template load<DS>(jvec(lenB, i + b + 1), sf);
+                    IO::template load<D>(kvec(i + b + 1), Kt);
 #pragma unroll
                     for (int mu = 0; mu < D; ++mu) {
                         PA[mu] = f.tsub(Kt[mu], Ki[mu]);
@@ -218,10 +269,10 @@ bg_compact_kernel(const F f, const CompactArgs a) {
                     const C pb_ja = f.template dot<D, METRIC>(PB, pb);
                     sa = f.cadd(sa, adj);
                     C csuf = f.cdbl(pb_ja);
-                    if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(base[(OFF_SA + g.sbase(lenA) + i) * BLOCK]));
+                    if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(Sr[(g.sbase(lenA) + i) * BLOCK]));
                     C cpre = f.cneg(f.cdbl(pa_jb));
                     if (lenB >= 2)
-                        cpre = f.csub(cpre, f.t_to_c(base[(OFF_SA + g.sbase(lenB) + i + b + 1) * BLOCK]));
+                        cpre = f.csub(cpre, f.t_to_c(Sr[(g.sbase(lenB) + i + b + 1) * BLOCK]));
                     f.template acc2<DS>(acc, csuf, sf, cpre, pb);
                     f.template acc1<D>(acc, adj, dP);
                     // four-gluon vertex: prefix [i, i+a], inner [i+a+1, i+b], suffix sf
@@ -229,18 +280,18 @@ bg_compact_kernel(const F f, const CompactArgs a) {
 #pragma unroll 1
                     for (; q + 1 < b; q += 2) {
                         T pa0[DS], pa1[DS], in0[DS], in1[DS];
-                        load(jvec(q + 1, i), pa0, DS);
-                        load(jvec(q + 2, i), pa1, DS);
-                        load(jvec(b - q, i + q + 1), in0, DS);
-                        load(jvec(b - q - 1, i + q + 2), in1, DS);
+                        IO::template load<DS>(jvec(q + 1, i), pa0);
+                        IO::template load<DS>(jvec(q + 2, i), pa1);
+                        IO::template load<DS>(jvec(b - q, i + q + 1), in0);
+                        IO::template load<DS>(jvec(b - q - 1, i + q + 2), in1);
                         const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
                         const C g1 = f.cdbl(f.template dot<DS, METRIC>(pa1, sf));
                         f.template acc2<DS>(acc, g0, in0, g1, in1);
                     }
                     if (q < b) {
                         T pa0[DS], in0[DS];
-                        load(jvec(q + 1, i), pa0, DS);
-                        load(jvec(b - q, i + q + 1), in0, DS);
+                        IO::template load<DS>(jvec(q + 1, i), pa0);
+                        IO::template load<DS>(jvec(b - q, i + q + 1), in0);
                         const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
                         f.template acc1<DS>(acc, g0, in0);
                     }
@@ -249,10 +300,8 @@ bg_compact_kernel(const F f, const CompactArgs a) {
                     const int sidx = g.sbase(m) + i;
                     T J[DS];
                     f.template finish<DS>(acc, Y[sidx * BLOCK], J);
-                    T* dst = jvec(m, i);
-#pragma unroll
-                    for (int mu = 0; mu < DS; ++mu) dst[mu * BLOCK] = J[mu];
-                    base[(OFF_SA + sidx) * BLOCK] = f.c_to_t(sa);
+                    IO::template store<DS>(jvec(m, i), J);
+                    Sr[sidx * BLOCK] = f.c_to_t(sa);
                 } else {
                     // a5: contract the top bracket with the last polarisation
                     result = f.template amplitude<DS, METRIC>(acc, eL);
