@@ -130,6 +130,36 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta,
                   void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 /*
+ * bg_host_staging_size -- device staging bytes that bg_eval_host needs when
+ * it moves the batch in chunks of `chunk` points (two input/output slots plus
+ * the kernel workspace).
+ */
+bg_status bg_host_staging_size(const bg_plan* plan, int64_t chunk, size_t* bytes);
+
+/*
+ * bg_eval_host -- evaluate E points whose inputs and outputs live in HOST
+ * memory (the data-parallel evaluation of Sec. 3 with the host-device
+ * transfers included).  The batch moves in chunks of `chunk` points through
+ * two staging slots in the caller's device buffer `staging` (>=
+ * bg_host_staging_size bytes, 256-byte aligned): the copy of chunk c+1 to the
+ * device, the kernel on chunk c and the copy of chunk c-1 back to the host
+ * overlap on separate streams.  Asynchronous: the host buffers hold the
+ * results once `stream` reaches the call.  Host buffers should be page-locked
+ * (pageable memory works but the copies serialise).
+ *
+ *   momenta, eps  host arrays with the layouts of bg_eval
+ *   out, status   host arrays [E][H] and [E] (status is required here)
+ *   chunk         points per chunk, >= 1
+ * Returns BG_ERR_INVALID_ARG for device pointers in place of host buffers, a
+ * too small or misaligned staging buffer, or E < 0; BG_ERR_CUDA when a copy
+ * or launch cannot be enqueued.  Calls from several host threads are
+ * serialised while they enqueue.
+ */
+bg_status bg_eval_host(const bg_plan* plan, int64_t E, const void* momenta,
+                       const void* eps, void* out, uint8_t* status, int64_t chunk,
+                       void* staging, size_t staging_bytes, cudaStream_t stream);
+
+/*
  * bg_eval_noalloc -- the same evaluation as bg_eval, for callers that cannot
  * allocate device memory: a framework that owns the device-memory budget
  * through its own allocator, a latency-critical loop that cannot afford the

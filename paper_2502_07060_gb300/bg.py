@@ -31,7 +31,8 @@ ALTERNATING = 1
 
 # bg_plan_create / bg_eval / ... as declared in include/bg.h
 EXPORTED = ("bg_plan_create", "bg_plan_destroy", "bg_workspace_size", "bg_eval",
-            "bg_eval_noalloc", "bg_plan_describe", "bg_strerror", "bg_last_error", "bg_version")
+            "bg_eval_noalloc", "bg_host_staging_size", "bg_eval_host", "bg_plan_describe",
+            "bg_strerror", "bg_last_error", "bg_version")
 
 LIB_PATH = _build.LIB
 
@@ -54,6 +55,11 @@ def load_library(path=None):
     lib.bg_eval.restype = ctypes.c_int
     lib.bg_eval_noalloc.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, vp]
     lib.bg_eval_noalloc.restype = ctypes.c_int
+    lib.bg_host_staging_size.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
+    lib.bg_host_staging_size.restype = ctypes.c_int
+    lib.bg_eval_host.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.c_int64, vp,
+                                 ctypes.c_size_t, vp]
+    lib.bg_eval_host.restype = ctypes.c_int
     lib.bg_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.bg_plan_describe.restype = ctypes.c_int
     lib.bg_strerror.argtypes = [ctypes.c_int]
@@ -171,6 +177,35 @@ class Plan:
                             _ptr(workspace), ws_bytes, _stream_handle(stream)))
         return out, status
 
+
+    def staging_size(self, chunk):
+        b = ctypes.c_size_t()
+        _check(_lib.bg_host_staging_size(self._h, chunk, ctypes.byref(b)))
+        return b.value
+
+    def eval_host(self, momenta, eps, out=None, status=None, chunk=1 << 18, staging=None,
+                  stream=None):
+        """bg_eval_host: host (preferably pinned) input tensors in, host results
+        out; transfers and kernels of consecutive chunks overlap.  Returns
+        (out, status) host tensors, valid after the stream synchronises."""
+        E = momenta.shape[0]
+        if out is None:
+            shape = (E,) if self.n_assign == 1 else (E, self.n_assign)
+            out = torch.empty(shape, dtype=momenta.dtype, pin_memory=momenta.is_pinned())
+        if status is None:
+            status = torch.empty(E, dtype=torch.uint8, pin_memory=momenta.is_pinned())
+        for t in (momenta, eps, out, status):
+            if not t.is_contiguous() or t.is_cuda:
+                raise ValueError("eval_host takes contiguous host tensors")
+        chunk = max(1, min(chunk, E)) if E else 1
+        need = self.staging_size(chunk)
+        if staging is None:
+            if getattr(self, "_staging", None) is None or self._staging.numel() < need:
+                self._staging = torch.empty(need, dtype=torch.uint8, device="cuda")
+            staging = self._staging
+        _check(_lib.bg_eval_host(self._h, E, _ptr(momenta), _ptr(eps), _ptr(out), _ptr(status),
+                                 chunk, _ptr(staging), staging.numel(), _stream_handle(stream)))
+        return out, status
 
     def eval_noalloc(self, momenta, eps, out=None, status=None, stream=None):
         """bg_eval_noalloc: the same result as eval() without any device

@@ -164,8 +164,8 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
 
     // Kernel choice: the compact kernel (run-time n) by default; the unrolled
     // per-n kernel on request (BG_KERNEL=unrolled, F_p only, n <= 8).  Table
-    // placement: shared memory when two blocks fit on an SM, else global
-    // scratch (BG_TABLE=shared|global overrides).
+    // placement: shared memory for small tables, else global scratch
+    // (BG_TABLE=shared|global overrides).
     const char* kenv = getenv("BG_KERNEL");
     const bool want_unrolled = kenv && strcmp(kenv, "unrolled") == 0;
     const char* tenv = getenv("BG_TABLE");
@@ -186,8 +186,10 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
         if (tenv) {
             want_global = strcmp(tenv, "global") == 0;
         } else if (field == BG_FIELD_FP) {
+            // measured on GB300 (n = 5..12): shared wins while a block's table
+            // is at most ~40 KB (five or more blocks per SM), global beyond
             const size_t smem = (size_t)words * bgk::kBlockFpCompactSmem * elem;
-            want_global = smem > 110 * 1024;     // fewer than two blocks per SM
+            want_global = smem > 40 * 1024;
         }
         for (const auto& e : registry())
             if (e.compact && e.field == (int)field && e.D == Dk && e.DS == DSk &&

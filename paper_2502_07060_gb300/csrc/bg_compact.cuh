@@ -14,7 +14,8 @@
 //   prefix  A = [i, s]:   -2 P_A.J_[s+1,j] - SA([s+1,j])
 //   suffix  C = [t+1, j]: +2 P_C.J_[i,t]   - SA([i,t])
 //   inner   B = [s+1, t]:  2 J_[i,s].J_[t+1,j]
-//   plus the momentum part sum_s (J_A.J_B)(P_A - P_B),
+//   plus the momentum part sum_s (J_A.J_B)(P_A - P_B)
+//     = 2 sum_s (J_A.J_B) K_{s+1} - SA([i,j]) (K_i + K_{j+1}),
 // where SA(X) = sum over the splits X = Y|Z of J_Y.J_Z is accumulated while X
 // itself is built and stored next to its current.  Per range of length m this
 // costs m(m+1)/2 - 1 vector updates instead of 2(m-1) + 3 C(m-1,2).
@@ -253,7 +254,7 @@ bg_compact_kernel(const F f, const CompactArgs a) {
 #pragma unroll 1
                 for (int b = 0; b < m - 1; ++b) {
                     const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
-                    T pb[DS], sf[DS], Kt[D], PA[D], PB[D], dP[D];
+                    T pb[DS], sf[DS], Kt[D], PA[D], PB[D];
                     IO::template load<DS>(jvec(lenA, i), pb);
                     IO::template load<DS>(jvec(lenB, i + b + 1), sf);
                     IO::template load<D>(kvec(i + b + 1), Kt);
@@ -261,7 +262,6 @@ bg_compact_kernel(const F f, const CompactArgs a) {
                     for (int mu = 0; mu < D; ++mu) {
                         PA[mu] = f.tsub(Kt[mu], Ki[mu]);
                         PB[mu] = f.tsub(Kj[mu], Kt[mu]);
-                        dP[mu] = f.tsub(PA[mu], PB[mu]);
                     }
                     // three-gluon vertex of the split at s = i + b
                     const C adj = f.template dot<DS, METRIC>(pb, sf);
@@ -274,7 +274,9 @@ bg_compact_kernel(const F f, const CompactArgs a) {
                     if (lenB >= 2)
                         cpre = f.csub(cpre, f.t_to_c(Sr[(g.sbase(lenB) + i + b + 1) * BLOCK]));
                     f.template acc2<DS>(acc, csuf, sf, cpre, pb);
-                    f.template acc1<D>(acc, adj, dP);
+                    // momentum part: adj (P_A - P_B) = adj (2 K_{i+b+1} - K_i - K_j);
+                    // the K_i + K_j share is added once per range below
+                    f.template acc1<D>(acc, f.cdbl(adj), Kt);
                     // four-gluon vertex: prefix [i, i+a], inner [i+a+1, i+b], suffix sf
                     int q = 0;
 #pragma unroll 1
@@ -295,6 +297,12 @@ bg_compact_kernel(const F f, const CompactArgs a) {
                         const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
                         f.template acc1<DS>(acc, g0, in0);
                     }
+                }
+                {
+                    T KiKj[D];
+#pragma unroll
+                    for (int mu = 0; mu < D; ++mu) KiKj[mu] = f.tadd(Ki[mu], Kj[mu]);
+                    f.template acc1<D>(acc, f.cneg(sa), KiKj);     // - SA(i,j) (K_i + K_j)
                 }
                 if (m < N) {
                     const int sidx = g.sbase(m) + i;

@@ -287,3 +287,28 @@ def test_full_size_metric_workload_sampled():
     kc, ec = G.c64_batch(2026, E, 8, 6, 6, 0)
     outc, _, _ = run_c64(kc, ec, 0)
     check_c64(outc[sample], kc[sample], ec[sample], 0, max_widened=0.0)
+
+
+@pytest.mark.parametrize("field,pinned", [("fp", True), ("fp", False), ("c64", True)])
+def test_eval_host_pipeline_matches_device_eval(field, pinned):
+    """bg_eval_host (host buffers, chunked and double buffered) returns exactly
+    what bg_eval returns on device copies of the same inputs; chunk sizes
+    leave a ragged last chunk."""
+    import torch
+    bg = _bg()
+    n, d, E = 8, 6, 10007
+    if field == "fp":
+        k, e = G.fp_batch(71, E, n, d, d)
+        hk, he = torch.from_numpy(k.view(np.int32)), torch.from_numpy(e.view(np.int32))
+        plan = bg.Plan(n, d, d, bg.FIELD_FP, P)
+    else:
+        k, e = G.c64_batch(71, E, n, d, d)
+        hk, he = torch.from_numpy(k), torch.from_numpy(e)
+        plan = bg.Plan(n, d, d, bg.FIELD_C64, 0)
+    if pinned:
+        hk, he = hk.pin_memory(), he.pin_memory()
+    ref, rst = plan.eval(hk.cuda(), he.cuda())
+    for chunk in (4096, 3000, E):
+        out, st = plan.eval_host(hk, he, chunk=chunk)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref.cpu()) and torch.equal(st, rst.cpu())
