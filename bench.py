@@ -70,6 +70,37 @@ def kernel_mults(n, d, Ds):
     return tot
 
 
+KERNEL_SOURCES = ("paper_2502_07060_gb300/csrc/bg_compact.cuh", "paper_2502_07060_gb300/csrc/bg_field.cuh")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name):
+    """DRAM bytes per 2^22-point launch from the ncu summary profiles/<name>,
+    or None when the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", name)
+    vals = {}
+    try:
+        with open(path) as f:
+            for line in f:
+                if ":" in line and line.split(":")[0].strip() in (
+                        "kernel_source_sha256_16", "traffic_bytes_per_launch_2p22"):
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+    except OSError:
+        return None
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return float(vals["traffic_bytes_per_launch_2p22"])
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -359,6 +390,10 @@ def main():
     achieved = fp["value_per_rank"] * tally
     c64_flops = 6 * tally + 2 * 5348
     peak_fp64 = n_sm * 2 * 2 * sm_max * 1e6
+    kops = kernel_mults(N_LEG, D, DS)
+    traffic_fp = profiled_traffic("fp_compact_n8_d6.md")
+    traffic_c64 = profiled_traffic("c64_compact_n8_d6.md")
+    scale = E / float(1 << 22)
     line = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": fp["ms_per_step"],
@@ -366,19 +401,26 @@ def main():
         "data": "synthetic", "config": config,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_mulmod,
                      "unit": "field multiplications/s (F_p, literal tally)",
-                     "frac": achieved / peak_mulmod, "traffic": None,
-                     "ops_per_unit": tally, "kernel_ops_per_unit": kernel_mults(N_LEG, D, DS),
+                     "frac": achieved / peak_mulmod,
+                     "traffic": None if traffic_fp is None else traffic_fp * scale,
+                     "ops_per_unit": tally, "kernel_ops_per_unit": kops,
+                     "frac_kernel_ops": fp["value_per_rank"] * kops / peak_mulmod,
                      "peak_derivation": f"{n_sm} SMs x 64 IMAD/clk x {sm_max:.0f} MHz / 3 IMAD per "
-                                        f"Montgomery multiplication"},
-        "c64": None if c64 is None else {"value": world * c64["value_per_rank"], "unit": "amplitudes/s",
-                "ms_per_step": c64["ms_per_step"], "points_per_step": Ec, "steps": c64_steps,
-                "dtype": "f64",
-                "roofline": {"bound": "alu", "achieved": c64["value_per_rank"] * c64_flops,
-                             "peak": peak_fp64, "unit": "FP64 FLOP/s (literal tally)",
-                             "frac": c64["value_per_rank"] * c64_flops / peak_fp64,
-                             "peak_derivation": f"{n_sm} SMs x 2 DFMA/clk x 2 x {sm_max:.0f} MHz"},
-                "e2e_value": (world * Ec / (c64["e2e_ms_per_step"] / 1e3)) if e2e else None,
-                "clocks": c64["clocks"], "plan": c64["plan"]},
+                                        f"Montgomery multiplication (derived; measured IMAD rate 61-63/clk/SM)",
+                     "traffic_source": "profiles/fp_compact_n8_d6.md, ncu capture of 2^19 points "
+                                       "scaled by the point count"},
+        "c64": None if c64 is None else {
+            "value": world * c64["value_per_rank"], "unit": "amplitudes/s",
+            "ms_per_step": c64["ms_per_step"], "points_per_step": Ec, "steps": c64_steps,
+            "dtype": "f64",
+            "roofline": {"bound": "alu", "achieved": c64["value_per_rank"] * c64_flops,
+                         "peak": peak_fp64, "unit": "FP64 FLOP/s (literal tally)",
+                         "frac": c64["value_per_rank"] * c64_flops / peak_fp64,
+                         "frac_kernel_ops": c64["value_per_rank"] * kops * 8 / peak_fp64,
+                         "traffic": None if traffic_c64 is None else traffic_c64 * Ec / float(1 << 22),
+                         "peak_derivation": f"{n_sm} SMs x 2 DFMA/clk x 2 x {sm_max:.0f} MHz"},
+            "e2e_value": (world * Ec / (c64["e2e_ms_per_step"] / 1e3)) if e2e else None,
+            "clocks": c64["clocks"], "plan": c64["plan"]},
         "e2e": None if not e2e else {
             "value": world * E / (fp["e2e_ms_per_step"] / 1e3), "unit": "amplitudes/s",
             "h2d_bytes_per_step": fp["h2d_bytes"], "d2h_bytes_per_step": fp["d2h_bytes"]},
