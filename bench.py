@@ -306,6 +306,63 @@ def run_field(field, E, steps, warmup, rank, dist, device, seed, e2e=True):
     return res
 
 
+def mixed_workload(args, device):
+    """Uneven batch: 2^22 points spread evenly over n = 4..12, d = D_s in
+    {4, 6, 8} and both number types (54 groups).  Times (a) 54 plain
+    per-group bg_eval launches, (b) one graph launch of the batch with the
+    default configuration and (c) with the autotuned configuration."""
+    import torch
+    from paper_2502_07060_gb300 import bg
+    total = 1 << args.log2_points
+    specs = [(f, n, d) for f in ("fp", "c64") for n in range(4, 13) for d in (4, 6, 8)]
+    per = total // len(specs)
+    groups = []
+    for i, (f, n, d) in enumerate(specs):
+        if f == "fp":
+            k, e = G.fp_batch(3000 + i, per, n, d, d, P, 0)
+            kd = torch.from_numpy(k.view(np.int32)).to(device)
+            ed = torch.from_numpy(e.view(np.int32)).to(device)
+            plan = bg.Plan(n, d, d, bg.FIELD_FP, P, bg.MOSTLY_MINUS)
+        else:
+            k, e = G.c64_batch(3000 + i, per, n, d, d, 0)
+            kd = torch.from_numpy(k).to(device)
+            ed = torch.from_numpy(e).to(device)
+            plan = bg.Plan(n, d, d, bg.FIELD_C64, 0, bg.MOSTLY_MINUS)
+        del k, e
+        out = torch.empty(per, dtype=kd.dtype, device=device)
+        st = torch.empty(per, dtype=torch.uint8, device=device)
+        groups.append((plan, kd, ed, out, st))
+    stream = torch.cuda.current_stream(device)
+    wss = [plan.workspace(per, device) for plan, *_ in groups]
+
+    def plain():
+        for (plan, kd, ed, out, st), ws in zip(groups, wss):
+            plan.eval(kd, ed, out=out, status=st, workspace=ws, stream=stream)
+
+    steps = max(3, args.steps // 10)
+    ms_plain = time_steps(plain, steps, args.warmup, stream, None, device)
+    batch = bg.Batch(groups)
+    ms_batch = time_steps(lambda: batch.launch(stream), steps, args.warmup, stream, None, device)
+    desc_default = batch.describe()
+    del batch
+    best, _ = bg.Batch.autotune(groups, reps=1, stream=stream)
+    tuned = bg.Batch(groups, config=best)
+    ms_tuned = time_steps(lambda: tuned.launch(stream), steps, args.warmup, stream, None, device)
+    n_pts = per * len(specs)
+    return {"workload": "uneven batch: 54 groups (n = 4..12, d = D_s in {4, 6, 8}, F_p and C64), "
+                        f"{per} points each, {n_pts} points per step",
+            "plain_launches": {"ms_per_step": ms_plain / steps, "value": n_pts / (ms_plain / steps / 1e3),
+                               "launches_per_step": len(specs)},
+            "batch_default": {"ms_per_step": ms_batch / steps, "value": n_pts / (ms_batch / steps / 1e3),
+                              "describe": desc_default},
+            "batch_autotuned": {"ms_per_step": ms_tuned / steps, "value": n_pts / (ms_tuned / steps / 1e3),
+                                "config": {"tile_points": best.tile_points,
+                                           "fp_blocks_per_sm": best.fp_blocks_per_sm,
+                                           "c64_blocks_per_sm": best.c64_blocks_per_sm},
+                                "describe": tuned.describe()},
+            "unit": "amplitudes/s", "steps": steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,6 +374,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fields", default="fp,c64", help="comma list of fp, c64")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--workload", choices=["metric", "mixed"], default="metric",
+                    help="metric: n=8 d=6 headline line; mixed: uneven-batch comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -362,6 +421,10 @@ def main():
     import torch
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
+    if args.workload == "mixed":
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "mixed": mixed_workload(args, device)}))
+        return
     dist = init_dist(world, "nccl")
     fields = args.fields.split(",")
     e2e = not args.no_e2e

@@ -185,6 +185,62 @@ bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void* momenta,
                           const void* eps, void* out, uint8_t* status,
                           cudaStream_t stream);
 
+/*
+ * Uneven batches: groups of points with different n, d, D_s, metric and
+ * number type evaluated by ONE CUDA-graph launch (the data-parallel method of
+ * Sec. 3 over a mixed workload; Sec. 3.2 notes that the per-configuration
+ * launch overhead dominates small batches).  The groups are ordered by cost,
+ * cut into tiles and consumed by two persistent kernels (F_p and complex)
+ * that run as parallel branches of the graph.
+ */
+typedef struct {
+    const bg_plan* plan;      /* the group's configuration (n, d, D_s, field, p, ...) */
+    int64_t E;                /* points in the group (0: group skipped)           */
+    const void* momenta;      /* device buffers with the layouts of bg_eval       */
+    const void* eps;
+    void* out;
+    uint8_t* status;          /* may be NULL                                       */
+} bg_group;
+
+typedef struct {
+    int tile_points;          /* work items per tile; 0 = 1024                     */
+    int fp_blocks_per_sm;     /* residency cap of the F_p kernel; 0 = all that fit */
+    int c64_blocks_per_sm;    /* residency cap of the complex kernel; 0 = all      */
+} bg_batch_config;
+
+typedef struct bg_batch bg_batch;   /* opaque: tables in the workspace + a graph */
+
+/* bg_batch_workspace_size -- device bytes the batch needs (group and tile
+ * tables, tile counters, table scratch).  cfg == NULL: the largest size any
+ * bg_batch_autotune candidate needs. */
+bg_status bg_batch_workspace_size(const bg_group* groups, int n_groups,
+                                  const bg_batch_config* cfg, size_t* bytes);
+
+/* bg_batch_create -- order, tile, upload the tables into `workspace` (device,
+ * 256-byte aligned, owned by the batch until bg_batch_destroy) and capture the
+ * graph.  The groups' buffers are bound into the graph: each launch evaluates
+ * whatever they hold.  cfg may be NULL (defaults).  Synchronous. */
+bg_status bg_batch_create(const bg_group* groups, int n_groups, const bg_batch_config* cfg,
+                          void* workspace, size_t workspace_bytes, bg_batch** out);
+
+/* bg_batch_launch -- one graph launch on `stream` (asynchronous). */
+bg_status bg_batch_launch(const bg_batch* batch, cudaStream_t stream);
+
+/* bg_batch_describe -- one-line summary (groups, tiles, grids, workspace). */
+bg_status bg_batch_describe(const bg_batch* batch, char* buf, size_t len);
+
+/* bg_batch_destroy -- free the batch (not the workspace); NULL accepted. */
+bg_status bg_batch_destroy(bg_batch* batch);
+
+/* bg_batch_autotune -- time every candidate configuration (tile size x
+ * residency caps of the two kernels) on this batch, `reps` launches each on
+ * `stream`, and return the fastest in *best (and its time per launch in
+ * *best_ms if non-NULL).  Needs bg_batch_workspace_size(groups, n, NULL)
+ * bytes of workspace.  Synchronises the stream. */
+bg_status bg_batch_autotune(const bg_group* groups, int n_groups, void* workspace,
+                            size_t workspace_bytes, int reps, cudaStream_t stream,
+                            bg_batch_config* best, double* best_ms);
+
 /* bg_plan_describe -- NUL-terminated one-line description of the kernel the
  * plan launches (variant, block size, shared memory, workspace per thread)
  * written to buf[0..len); returns BG_ERR_INVALID_ARG when it does not fit. */

@@ -31,10 +31,23 @@ ALTERNATING = 1
 
 # bg_plan_create / bg_eval / ... as declared in include/bg.h
 EXPORTED = ("bg_plan_create", "bg_plan_destroy", "bg_workspace_size", "bg_eval",
-            "bg_eval_noalloc", "bg_host_staging_size", "bg_eval_host", "bg_plan_describe",
-            "bg_strerror", "bg_last_error", "bg_version")
+            "bg_eval_noalloc", "bg_host_staging_size", "bg_eval_host", "bg_batch_workspace_size",
+            "bg_batch_create", "bg_batch_launch", "bg_batch_describe", "bg_batch_destroy",
+            "bg_batch_autotune", "bg_plan_describe", "bg_strerror", "bg_last_error", "bg_version")
 
 LIB_PATH = _build.LIB
+
+
+class BgGroup(ctypes.Structure):
+    """bg_group of include/bg.h."""
+    _fields_ = [("plan", ctypes.c_void_p), ("E", ctypes.c_int64), ("momenta", ctypes.c_void_p),
+                ("eps", ctypes.c_void_p), ("out", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
+class BgBatchConfig(ctypes.Structure):
+    """bg_batch_config of include/bg.h."""
+    _fields_ = [("tile_points", ctypes.c_int), ("fp_blocks_per_sm", ctypes.c_int),
+                ("c64_blocks_per_sm", ctypes.c_int)]
 
 
 def load_library(path=None):
@@ -60,6 +73,21 @@ def load_library(path=None):
     lib.bg_eval_host.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.c_int64, vp,
                                  ctypes.c_size_t, vp]
     lib.bg_eval_host.restype = ctypes.c_int
+    gp = ctypes.POINTER(BgGroup)
+    cp = ctypes.POINTER(BgBatchConfig)
+    lib.bg_batch_workspace_size.argtypes = [gp, ctypes.c_int, cp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.bg_batch_workspace_size.restype = ctypes.c_int
+    lib.bg_batch_create.argtypes = [gp, ctypes.c_int, cp, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+    lib.bg_batch_create.restype = ctypes.c_int
+    lib.bg_batch_launch.argtypes = [vp, vp]
+    lib.bg_batch_launch.restype = ctypes.c_int
+    lib.bg_batch_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.bg_batch_describe.restype = ctypes.c_int
+    lib.bg_batch_destroy.argtypes = [vp]
+    lib.bg_batch_destroy.restype = ctypes.c_int
+    lib.bg_batch_autotune.argtypes = [gp, ctypes.c_int, vp, ctypes.c_size_t, ctypes.c_int, vp, cp,
+                                      ctypes.POINTER(ctypes.c_double)]
+    lib.bg_batch_autotune.restype = ctypes.c_int
     lib.bg_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.bg_plan_describe.restype = ctypes.c_int
     lib.bg_strerror.argtypes = [ctypes.c_int]
@@ -221,6 +249,66 @@ class Plan:
         _check(_lib.bg_eval_noalloc(self._h, E, _ptr(momenta), _ptr(eps), _ptr(out), _ptr(status),
                                     _stream_handle(stream)))
         return out, status
+
+
+class Batch:
+    """An uneven batch (bg_batch): groups = [(plan, momenta, eps, out, status)]
+    of device tensors, evaluated by one CUDA-graph launch."""
+
+    def __init__(self, groups, config=None, workspace=None):
+        self._keep = groups
+        arr = (BgGroup * len(groups))()
+        for i, (plan, k, e, out, st) in enumerate(groups):
+            arr[i] = BgGroup(plan.handle.value, k.shape[0], k.data_ptr(), e.data_ptr(), out.data_ptr(),
+                             st.data_ptr() if st is not None else 0)
+        self._arr = arr
+        self.config = config
+        cfgp = ctypes.byref(config) if config is not None else None
+        need = ctypes.c_size_t()
+        _check(_lib.bg_batch_workspace_size(arr, len(groups), cfgp, ctypes.byref(need)))
+        if workspace is None or workspace.numel() < need.value:
+            workspace = torch.empty(max(need.value, 256), dtype=torch.uint8, device="cuda")
+        self.workspace = workspace
+        h = ctypes.c_void_p()
+        _check(_lib.bg_batch_create(arr, len(groups), cfgp, _ptr(workspace), workspace.numel(),
+                                    ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(_lib.bg_batch_launch(self._h, _stream_handle(stream)))
+
+    def describe(self):
+        buf = ctypes.create_string_buffer(512)
+        _check(_lib.bg_batch_describe(self._h, buf, 512))
+        return buf.value.decode()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.bg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def autotune(groups, reps=2, stream=None):
+        """bg_batch_autotune over the library's candidate set; returns
+        (BgBatchConfig, ms per launch)."""
+        arr = (BgGroup * len(groups))()
+        for i, (plan, k, e, out, st) in enumerate(groups):
+            arr[i] = BgGroup(plan.handle.value, k.shape[0], k.data_ptr(), e.data_ptr(), out.data_ptr(),
+                             st.data_ptr() if st is not None else 0)
+        need = ctypes.c_size_t()
+        _check(_lib.bg_batch_workspace_size(arr, len(groups), None, ctypes.byref(need)))
+        ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device="cuda")
+        best = BgBatchConfig()
+        ms = ctypes.c_double()
+        _check(_lib.bg_batch_autotune(arr, len(groups), _ptr(ws), ws.numel(), reps,
+                                      _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms)))
+        return best, ms.value
 
 
 def strerror(status):

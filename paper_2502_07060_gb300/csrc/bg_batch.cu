@@ -1,0 +1,344 @@
+// bg_batch.cu -- uneven batches: many groups of points with different n, d,
+// D_s, metric and number type evaluated by one CUDA-graph launch.
+//
+// A batch is built once from its groups (each group: a plan and its device
+// buffers).  The host orders the groups by decreasing cost per point, cuts
+// them into tiles, stores the group and tile tables in the caller's workspace
+// and captures a graph: reset the tile counters, then the F_p and the complex
+// persistent kernels as two parallel branches (they use different pipes: the
+// integer multiply pipe and the FP64 pipe, so they can share SMs).  Each
+// branch's grid is one resident wave, optionally capped per SM; the caps and
+// the tile size are the knobs that bg_batch_autotune searches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bg_batch.cuh"
+#include "bg_internal.h"
+
+namespace {
+
+constexpr int kBlockFpBatch = 128;
+constexpr int kBlockC64Batch = 64;
+constexpr int kTuneTiles[] = {256, 1024, 4096};     // autotune candidates (points per tile)
+constexpr int kTuneFpCaps[] = {0, 4, 2};            // F_p blocks per SM (0 = all that fit)
+constexpr int kTuneC64Caps[] = {0, 3, 2, 1};        // C64 blocks per SM
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// relative cost of one point (field multiplications of the regrouped form)
+double point_cost(int n, int D, int DS, bool fp) {
+    const int N = n - 1;
+    double tot = 0;
+    for (int m = 2; m <= N; ++m) {
+        const double per = (m - 1) * (3.0 * DS + 3.0 * D) + (m - 1) * (m - 2) * DS;
+        tot += (N - m + 1) * per;
+    }
+    return fp ? tot : 8.0 * tot;      // FP64 pipe: far slower per multiplication
+}
+
+struct FieldPart {
+    std::vector<bgk::BatchGroup> groups;
+    std::vector<bgk::BatchTile> tiles;
+    int words = 0;                      // largest table, elements per thread
+    int blocks = 0;                     // grid
+    size_t off_groups = 0, off_tiles = 0, off_tables = 0;
+};
+
+struct Layout {
+    FieldPart part[2];                  // [0] = C64, [1] = F_p
+    size_t bytes = 0;
+};
+
+bg_status build_layout(const bg_group* groups, int n_groups, const bg_batch_config* cfg, int dev,
+                       Layout* L) {
+    if (!groups || n_groups < 1) return bgi::fail(BG_ERR_INVALID_ARG, "no groups");
+    const int tile = cfg && cfg->tile_points > 0 ? cfg->tile_points : 1024;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    struct Item { int idx; double cost; };
+    std::vector<Item> order;
+    for (int gi = 0; gi < n_groups; ++gi) {
+        const bg_group& g = groups[gi];
+        if (!g.plan) return bgi::fail(BG_ERR_INVALID_ARG, "group %d has no plan", gi);
+        if (g.E < 0) return bgi::fail(BG_ERR_INVALID_ARG, "group %d has E < 0", gi);
+        if (g.E == 0) continue;
+        if (!g.momenta || !g.eps || !g.out) return bgi::fail(BG_ERR_INVALID_ARG, "group %d: NULL buffer", gi);
+        const bg_plan* pl = g.plan;
+        if (g.E > (int64_t(1) << 40) / pl->H) return bgi::fail(BG_ERR_INVALID_ARG, "group %d too large", gi);
+        const int D = bgi::round_dim(pl->d), DS = bgi::round_dim(pl->Ds);
+        order.push_back({gi, point_cost(pl->n, D, DS, pl->field == BG_FIELD_FP) * pl->H});
+    }
+    std::stable_sort(order.begin(), order.end(), [](const Item& a, const Item& b) { return a.cost > b.cost; });
+    for (const Item& it : order) {
+        const bg_group& g = groups[it.idx];
+        const bg_plan* pl = g.plan;
+        FieldPart& fpart = L->part[pl->field == BG_FIELD_FP ? 1 : 0];
+        const int D = bgi::round_dim(pl->d), DS = bgi::round_dim(pl->Ds);
+        bgk::BatchGroup bgd{};
+        bgd.args.E = g.E;
+        bgd.args.H = pl->H;
+        bgd.args.S = pl->S;
+        bgd.args.n = pl->n;
+        bgd.args.d_in = pl->d;
+        bgd.args.ds_in = pl->Ds;
+        bgd.args.k = g.momenta;
+        bgd.args.eps = g.eps;
+        bgd.args.out = g.out;
+        bgd.args.status = g.status;
+        bgd.args.assign = pl->d_assign;
+        bgd.args.ws = nullptr;
+        bgd.variant = 2 * bgk::batch_pair_index(D, DS) + (int)pl->metric;
+        bgd.fp = pl->fpo;
+        const int gidx = (int)fpart.groups.size();
+        fpart.groups.push_back(bgd);
+        fpart.words = std::max(fpart.words, bgk::Geometry{pl->n - 1}.words(D, DS));
+        const int64_t items = g.E * pl->H;
+        for (int64_t first = 0; first < items; first += tile) {
+            bgk::BatchTile t;
+            t.group = gidx;
+            t.first = first;
+            t.count = (int)std::min<int64_t>(tile, items - first);
+            fpart.tiles.push_back(t);
+        }
+    }
+    // grids: one resident wave, capped per SM by the configuration
+    size_t off = 256;                    // [0, 256): the two tile counters
+    for (int f = 0; f < 2; ++f) {
+        FieldPart& P = L->part[f];
+        if (P.tiles.empty()) continue;
+        const void* func = f ? (const void*)&bgk::bg_batch_kernel<bgk::FpOps, kBlockFpBatch>
+                             : (const void*)&bgk::bg_batch_kernel<bgk::C64Ops, kBlockC64Batch>;
+        const int block = f ? kBlockFpBatch : kBlockC64Batch;
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, block, 0) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            return bgi::fail(BG_ERR_UNSUPPORTED, "batch kernel cannot be resident");
+        }
+        const int cap = cfg ? (f ? cfg->fp_blocks_per_sm : cfg->c64_blocks_per_sm) : 0;
+        if (cap > 0 && cap < occ) occ = cap;
+        P.blocks = std::min<int64_t>((int64_t)occ * sms, (int64_t)P.tiles.size());
+        const size_t elem = f ? 4 : 16;
+        P.off_groups = off;
+        off += up256(P.groups.size() * sizeof(bgk::BatchGroup));
+        P.off_tiles = off;
+        off += up256(P.tiles.size() * sizeof(bgk::BatchTile));
+        P.off_tables = off;
+        off += up256((size_t)P.blocks * block * P.words * elem);
+    }
+    L->bytes = off;
+    return BG_OK;
+}
+
+}  // namespace
+
+struct bg_batch {
+    int device = -1;
+    Layout L;
+    unsigned char* ws = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+bg_status bg_batch_workspace_size(const bg_group* groups, int n_groups, const bg_batch_config* cfg,
+                                  size_t* bytes) {
+    if (!bytes) return bgi::fail(BG_ERR_INVALID_ARG, "bytes is NULL");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return bgi::fail(BG_ERR_CUDA, "no current CUDA device");
+    }
+    if (cfg) {
+        Layout L;
+        bg_status st = build_layout(groups, n_groups, cfg, dev, &L);
+        if (st != BG_OK) return st;
+        *bytes = L.bytes;
+        return BG_OK;
+    }
+    // no configuration: the largest workspace any autotune candidate needs
+    size_t mx = 0;
+    for (int t : kTuneTiles) {
+        bg_batch_config c{t, 0, 0};
+        Layout L;
+        bg_status st = build_layout(groups, n_groups, &c, dev, &L);
+        if (st != BG_OK) return st;
+        mx = std::max(mx, L.bytes);
+    }
+    *bytes = mx;
+    return BG_OK;
+}
+
+bg_status bg_batch_create(const bg_group* groups, int n_groups, const bg_batch_config* cfg,
+                          void* workspace, size_t workspace_bytes, bg_batch** out) {
+    if (!out) return bgi::fail(BG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return bgi::fail(BG_ERR_CUDA, "no current CUDA device");
+    }
+    bg_batch* b = new (std::nothrow) bg_batch();
+    if (!b) return bgi::fail(BG_ERR_NOMEM, "host allocation failed");
+    b->device = dev;
+    bg_status st = build_layout(groups, n_groups, cfg, dev, &b->L);
+    if (st != BG_OK) { delete b; return st; }
+    if (!workspace || workspace_bytes < b->L.bytes || (uintptr_t)workspace % 256) {
+        const size_t need = b->L.bytes;
+        delete b;
+        return bgi::fail(BG_ERR_INVALID_ARG, "workspace of %zu B (256-byte aligned) needed", need);
+    }
+    if ((st = bgi::check_device_ptr(workspace, "workspace", dev)) != BG_OK) { delete b; return st; }
+    for (int gi = 0; gi < n_groups; ++gi) {
+        if (groups[gi].E == 0) continue;
+        const bg_plan* pl = groups[gi].plan;
+        if (pl->d_assign && pl->device != dev) { delete b; return bgi::fail(BG_ERR_CUDA, "group %d: plan on another device", gi); }
+        if ((st = bgi::check_device_ptr(groups[gi].momenta, "momenta", dev)) != BG_OK ||
+            (st = bgi::check_device_ptr(groups[gi].eps, "eps", dev)) != BG_OK ||
+            (st = bgi::check_device_ptr(groups[gi].out, "out", dev)) != BG_OK ||
+            (groups[gi].status && (st = bgi::check_device_ptr(groups[gi].status, "status", dev)) != BG_OK)) {
+            delete b;
+            return st;
+        }
+    }
+    b->ws = static_cast<unsigned char*>(workspace);
+    // group and tile tables -> workspace
+    for (int f = 0; f < 2; ++f) {
+        FieldPart& P = b->L.part[f];
+        if (P.tiles.empty()) continue;
+        if (cudaMemcpy(b->ws + P.off_groups, P.groups.data(), P.groups.size() * sizeof(bgk::BatchGroup),
+                       cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(b->ws + P.off_tiles, P.tiles.data(), P.tiles.size() * sizeof(bgk::BatchTile),
+                       cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return bgi::fail(BG_ERR_CUDA, "upload of the batch tables failed");
+        }
+    }
+    // capture: reset counters; F_p and C64 kernels on two parallel branches
+    cudaStream_t s0 = nullptr, s1 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaError_t err = cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking);
+    if (!err) err = cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking);
+    if (!err) err = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (!err) err = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (!err) err = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+    if (!err) err = cudaMemsetAsync(b->ws, 0, 256, s0);
+    if (!err) err = cudaEventRecord(fork, s0);
+    if (!err) err = cudaStreamWaitEvent(s1, fork, 0);
+    for (int f = 0; f < 2 && !err; ++f) {
+        FieldPart& P = b->L.part[f];
+        if (P.tiles.empty()) continue;
+        bgk::BatchArgs a;
+        a.groups = reinterpret_cast<const bgk::BatchGroup*>(b->ws + P.off_groups);
+        a.tiles = reinterpret_cast<const bgk::BatchTile*>(b->ws + P.off_tiles);
+        a.n_tiles = (int)P.tiles.size();
+        a.counter = reinterpret_cast<int*>(b->ws) + f;
+        a.tables = b->ws + P.off_tables;
+        a.words = P.words;
+        if (f) bgk::bg_batch_kernel<bgk::FpOps, kBlockFpBatch><<<P.blocks, kBlockFpBatch, 0, s0>>>(a);
+        else bgk::bg_batch_kernel<bgk::C64Ops, kBlockC64Batch><<<P.blocks, kBlockC64Batch, 0, s1>>>(a);
+        err = cudaGetLastError();
+    }
+    if (!err) err = cudaEventRecord(join, s1);
+    if (!err) err = cudaStreamWaitEvent(s0, join, 0);
+    cudaGraph_t graph = nullptr;
+    cudaError_t end = cudaStreamEndCapture(s0, &graph);
+    if (!err) err = end;
+    if (!err) err = cudaGraphInstantiate(&b->exec, graph, 0);
+    b->graph = graph;
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (s0) cudaStreamDestroy(s0);
+    if (s1) cudaStreamDestroy(s1);
+    if (err) {
+        cudaGetLastError();
+        bg_batch_destroy(b);
+        return bgi::fail(BG_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(err));
+    }
+    *out = b;
+    return BG_OK;
+}
+
+bg_status bg_batch_launch(const bg_batch* batch, cudaStream_t stream) {
+    if (!batch || !batch->exec) return bgi::fail(BG_ERR_INVALID_ARG, "batch is NULL");
+    cudaError_t err = cudaGraphLaunch(batch->exec, stream);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return bgi::fail(BG_ERR_CUDA, "graph launch failed: %s", cudaGetErrorString(err));
+    }
+    return BG_OK;
+}
+
+bg_status bg_batch_describe(const bg_batch* batch, char* buf, size_t len) {
+    if (!batch || !buf) return bgi::fail(BG_ERR_INVALID_ARG, "bad argument to bg_batch_describe");
+    const FieldPart& F = batch->L.part[1];
+    const FieldPart& C = batch->L.part[0];
+    int w = snprintf(buf, len,
+                     "fp: groups=%zu tiles=%zu blocks=%d words=%d; c64: groups=%zu tiles=%zu blocks=%d "
+                     "words=%d; workspace=%zu",
+                     F.groups.size(), F.tiles.size(), F.blocks, F.words, C.groups.size(), C.tiles.size(),
+                     C.blocks, C.words, batch->L.bytes);
+    if (w < 0 || (size_t)w >= len) return bgi::fail(BG_ERR_INVALID_ARG, "buffer too small");
+    return BG_OK;
+}
+
+bg_status bg_batch_destroy(bg_batch* batch) {
+    if (!batch) return BG_OK;
+    if (batch->exec) cudaGraphExecDestroy(batch->exec);
+    if (batch->graph) cudaGraphDestroy(batch->graph);
+    delete batch;
+    return BG_OK;
+}
+
+// Time every candidate configuration (tile size x residency caps) on the
+// caller's batch and return the fastest.  Each candidate: one warm-up launch
+// and `reps` timed launches of its graph on `stream`.
+bg_status bg_batch_autotune(const bg_group* groups, int n_groups, void* workspace, size_t workspace_bytes,
+                            int reps, cudaStream_t stream, bg_batch_config* best, double* best_ms) {
+    if (!best) return bgi::fail(BG_ERR_INVALID_ARG, "best is NULL");
+    if (reps < 1) reps = 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return bgi::fail(BG_ERR_CUDA, "event creation failed");
+    }
+    double best_t = -1.0;
+    bg_status result = BG_OK;
+    for (int t : kTuneTiles)
+        for (int fc : kTuneFpCaps)
+            for (int cc : kTuneC64Caps) {
+                bg_batch_config cfg{t, fc, cc};
+                bg_batch* b = nullptr;
+                bg_status st = bg_batch_create(groups, n_groups, &cfg, workspace, workspace_bytes, &b);
+                if (st != BG_OK) { result = st; continue; }
+                float ms = 0.f;
+                bool ok = bg_batch_launch(b, stream) == BG_OK && cudaEventRecord(e0, stream) == cudaSuccess;
+                for (int r = 0; r < reps && ok; ++r) ok = bg_batch_launch(b, stream) == BG_OK;
+                ok = ok && cudaEventRecord(e1, stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                     cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+                bg_batch_destroy(b);
+                if (!ok) {
+                    cudaGetLastError();
+                    result = bgi::fail(BG_ERR_CUDA, "timing a candidate failed");
+                    continue;
+                }
+                const double per = ms / reps;
+                if (best_t < 0 || per < best_t) {
+                    best_t = per;
+                    *best = cfg;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_t < 0) return result != BG_OK ? result : bgi::fail(BG_ERR_CUDA, "no candidate ran");
+    if (best_ms) *best_ms = best_t;
+    return BG_OK;
+}
+
+}  // extern "C"

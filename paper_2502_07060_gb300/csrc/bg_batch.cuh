@@ -1,0 +1,92 @@
+// bg_batch.cuh -- persistent kernel for a batch of uneven groups: points of
+// different n, d, D_s and metric (one number type per kernel) in one launch.
+//
+// The batch is cut into tiles of consecutive work items of one group.  Tiles
+// are ordered by decreasing cost per point (longest-processing-time first, so
+// the cheap tiles fill the tail) and handed out by one atomic counter: each
+// resident block takes the next tile, runs the recursion of bg_compact.cuh on
+// its items (the (D, D_s, metric) body the group needs), and repeats until the
+// queue is empty.  The tables of a block live in a global scratch region sized
+// for the largest group of the batch.  Blocks never wait for one another.
+#pragma once
+#include <cstdint>
+
+#include "bg_compact.cuh"
+
+namespace bgk {
+
+// (D, D_s) pairs compiled for the batch kernel, and the variant index
+// variant = 2 * pair + metric.
+constexpr int kBatchPairs = 6;
+__host__ __device__ constexpr int batch_pair_index(int D, int DS) {
+    return D == 4 ? (DS == 4 ? 0 : DS == 6 ? 1 : 2) : D == 6 ? (DS == 6 ? 3 : 4) : 5;
+}
+
+struct BatchGroup {
+    CompactArgs args;       // n, E, H, S, dims, device buffers (ws unused)
+    int variant;            // 2 * batch_pair_index(D, D_s) + metric
+    FpOps fp;               // Montgomery constants (F_p groups)
+};
+
+struct BatchTile {
+    int group;
+    int count;              // work items in the tile
+    int64_t first;          // first work item (point * H + assignment)
+};
+
+struct BatchArgs {
+    const BatchGroup* groups;
+    const BatchTile* tiles;
+    int n_tiles;
+    int* counter;           // next tile; zero before the launch
+    void* tables;           // per-block table regions
+    int words;              // table elements per thread (largest group)
+};
+
+template <class F>
+__device__ __forceinline__ F batch_field(const BatchGroup& g);
+template <>
+__device__ __forceinline__ FpOps batch_field<FpOps>(const BatchGroup& g) { return g.fp; }
+template <>
+__device__ __forceinline__ C64Ops batch_field<C64Ops>(const BatchGroup&) { return C64Ops{}; }
+
+template <class F, int BLOCK>
+__device__ __forceinline__ void batch_item(const F& f, const CompactArgs& a, int variant,
+                                           typename F::T* tab, int64_t u) {
+    switch (variant) {
+        case 0: bg_point<F, 4, 4, 0, BLOCK>(f, a, tab, u); break;
+        case 1: bg_point<F, 4, 4, 1, BLOCK>(f, a, tab, u); break;
+        case 2: bg_point<F, 4, 6, 0, BLOCK>(f, a, tab, u); break;
+        case 3: bg_point<F, 4, 6, 1, BLOCK>(f, a, tab, u); break;
+        case 4: bg_point<F, 4, 8, 0, BLOCK>(f, a, tab, u); break;
+        case 5: bg_point<F, 4, 8, 1, BLOCK>(f, a, tab, u); break;
+        case 6: bg_point<F, 6, 6, 0, BLOCK>(f, a, tab, u); break;
+        case 7: bg_point<F, 6, 6, 1, BLOCK>(f, a, tab, u); break;
+        case 8: bg_point<F, 6, 8, 0, BLOCK>(f, a, tab, u); break;
+        case 9: bg_point<F, 6, 8, 1, BLOCK>(f, a, tab, u); break;
+        case 10: bg_point<F, 8, 8, 0, BLOCK>(f, a, tab, u); break;
+        default: bg_point<F, 8, 8, 1, BLOCK>(f, a, tab, u); break;
+    }
+}
+
+template <class F, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) bg_batch_kernel(const BatchArgs a) {
+    using T = typename F::T;
+    __shared__ int s_tile;
+    T* tab = reinterpret_cast<T*>(a.tables) + static_cast<size_t>(blockIdx.x) * a.words * BLOCK;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int ti = s_tile;
+        __syncthreads();                       // every thread has read s_tile
+        if (ti >= a.n_tiles) break;
+        const BatchTile td = a.tiles[ti];
+        const BatchGroup& gd = a.groups[td.group];
+        const F f = batch_field<F>(gd);
+        const int variant = gd.variant;
+        for (int k = threadIdx.x; k < td.count; k += BLOCK)
+            batch_item<F, BLOCK>(f, gd.args, variant, tab, td.first + k);
+    }
+}
+
+}  // namespace bgk

@@ -119,9 +119,10 @@ struct TableIO {
     }
 };
 
-template <class F, int D, int DS, int METRIC, int BLOCK, bool GLOBAL_TABLE>
-__global__ void __launch_bounds__(BLOCK)
-bg_compact_kernel(const F f, const CompactArgs a) {
+// The whole recursion for work item u (point e = u / H, assignment h = u % H)
+// with the block's table at `tab` (shared or global memory).
+template <class F, int D, int DS, int METRIC, int BLOCK>
+__device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typename F::T* tab, int64_t u) {
     using T = typename F::T;
     using C = typename F::C;
     using Acc = typename F::A;
@@ -130,16 +131,7 @@ bg_compact_kernel(const F f, const CompactArgs a) {
     const int NLEG = a.n;
     const Geometry g{NLEG - 1};
     const int N = g.N;
-    const int W = g.words(D, DS);
     const int OFF_K = g.off_k(DS), OFF_SA = g.off_sa(D, DS), OFF_INV = g.off_inv(D, DS);
-
-    extern __shared__ __align__(16) unsigned char bg_smem[];
-    T* tab;                                   // this block's table
-    if constexpr (GLOBAL_TABLE) {
-        tab = reinterpret_cast<T*>(a.ws) + static_cast<size_t>(blockIdx.x) * W * BLOCK;
-    } else {
-        tab = reinterpret_cast<T*>(bg_smem);
-    }
     constexpr bool VEC = F::kIsFp;
     using IO = TableIO<T, VEC, BLOCK>;
     const int t = threadIdx.x;
@@ -149,176 +141,189 @@ bg_compact_kernel(const F f, const CompactArgs a) {
     T* Ir = tab + OFF_INV * BLOCK + t;                             // 1/P^2 per internal range
     auto jvec = [&](int len, int start) { return IO::template vec<DS>(Jr, g.jbase(len) + start); };
     auto kvec = [&](int i) { return IO::template vec<D>(Kr, i); };
-
     const io_t* kin = static_cast<const io_t*>(a.k);
     const io_t* ein = static_cast<const io_t*>(a.eps);
     io_t* out = static_cast<io_t*>(a.out);
+
+    int64_t e = u;
+    int h = 0;
+    if (a.H > 1) {
+        e = u / a.H;
+        h = static_cast<int>(u - e * a.H);
+    }
+    // a1: momenta -> prefix sums K_0 = 0, K_{l+1} = K_l + k_l (leg n unused:
+    // P_{1,n-1} = -k_n never enters); polarisations -> currents of length 1.
+    {
+        const io_t* kp = kin + e * NLEG * a.d_in;
+        T Kacc[D];
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) Kacc[mu] = f.zero();
+        IO::template store<D>(kvec(0), Kacc);
+#pragma unroll 1
+        for (int l = 0; l < N; ++l) {
+#pragma unroll
+            for (int mu = 0; mu < D; ++mu)
+                if (mu < a.d_in) Kacc[mu] = f.tadd(Kacc[mu], f.from_io(kp[l * a.d_in + mu]));
+            IO::template store<D>(kvec(l + 1), Kacc);
+        }
+    }
+    T eL[DS];
+#pragma unroll 1
+    for (int l = 0; l < NLEG; ++l) {
+        const int s = (a.assign != nullptr) ? a.assign[h * NLEG + l] : 0;
+        const io_t* ep = ein + ((e * NLEG + l) * a.S + s) * a.ds_in;
+        T v[DS];
+#pragma unroll
+        for (int mu = 0; mu < DS; ++mu) v[mu] = (mu < a.ds_in) ? f.from_io(ep[mu]) : f.zero();
+        if (l < N) {
+            IO::template store<DS>(jvec(1, l), v);     // current (1, l)
+        } else {
+#pragma unroll
+            for (int mu = 0; mu < DS; ++mu) eL[mu] = v[mu];
+        }
+    }
+    // a2: P^2 of every internal range (length 2..N-1), flat index sbase(m) + i
+    T* X = Sr;     // P^2 inputs of the inverse (reuses the SA slots)
+    T* Y = Ir;     // 1/P^2
+#pragma unroll 1
+    for (int m = 2; m < N; ++m) {
+#pragma unroll 1
+        for (int i = 0; i + m - 1 < N; ++i) {
+            T Ka[D], Kb[D], P[D];
+            IO::template load<D>(kvec(i), Ka);
+            IO::template load<D>(kvec(i + m), Kb);
+#pragma unroll
+            for (int mu = 0; mu < D; ++mu) P[mu] = f.tsub(Kb[mu], Ka[mu]);
+            X[(g.sbase(m) + i) * BLOCK] = f.inv_input(f.template dot<D, METRIC>(P, P));
+        }
+    }
+    // a3: all inverses.  F_p: Montgomery simultaneous inversion (prefix
+    // products, one Fermat inverse, backward sweep); C64: per range.
+    bool singular = false;
+    const int NS = g.ns();
+    if constexpr (F::kIsFp) {
+        T c = X[0];
+        Y[0] = c;
+#pragma unroll 1
+        for (int s = 1; s < NS; ++s) {
+            c = f.inv_mul(c, X[s * BLOCK]);
+            Y[s * BLOCK] = c;
+        }
+        singular = f.is_zero(c);
+        T r = f.inv_scalar(c);
+#pragma unroll 1
+        for (int s = NS - 1; s > 0; --s) {
+            const T x = X[s * BLOCK];
+            Y[s * BLOCK] = f.inv_store(f.inv_mul(Y[(s - 1) * BLOCK], r));
+            r = f.inv_mul(r, x);
+        }
+        Y[0] = f.inv_store(r);
+    } else {
+#pragma unroll 1
+        for (int s = 0; s < NS; ++s) {
+            const T x = X[s * BLOCK];
+            singular |= f.is_zero(x);
+            Y[s * BLOCK] = f.inv_scalar(x);
+        }
+    }
+
+    // a4: the recursion, by increasing length m
+    io_t result = f.zero_io();
+#pragma unroll 1
+    for (int m = 2; m <= N; ++m) {
+#pragma unroll 1
+        for (int i = 0; i + m - 1 < N; ++i) {
+            T Ki[D], Kj[D];
+            IO::template load<D>(kvec(i), Ki);
+            IO::template load<D>(kvec(i + m), Kj);
+            Acc acc[DS];
+            f.template acc_zero<DS>(acc);
+            C sa = f.czero();
+#pragma unroll 1
+            for (int b = 0; b < m - 1; ++b) {
+                const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
+                T pb[DS], sf[DS], Kt[D], PA[D], PB[D];
+                IO::template load<DS>(jvec(lenA, i), pb);
+                IO::template load<DS>(jvec(lenB, i + b + 1), sf);
+                IO::template load<D>(kvec(i + b + 1), Kt);
+#pragma unroll
+                for (int mu = 0; mu < D; ++mu) {
+                    PA[mu] = f.tsub(Kt[mu], Ki[mu]);
+                    PB[mu] = f.tsub(Kj[mu], Kt[mu]);
+                }
+                // three-gluon vertex of the split at s = i + b
+                const C adj = f.template dot<DS, METRIC>(pb, sf);
+                const C pa_jb = f.template dot<D, METRIC>(PA, sf);
+                const C pb_ja = f.template dot<D, METRIC>(PB, pb);
+                sa = f.cadd(sa, adj);
+                C csuf = f.cdbl(pb_ja);
+                if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(Sr[(g.sbase(lenA) + i) * BLOCK]));
+                C cpre = f.cneg(f.cdbl(pa_jb));
+                if (lenB >= 2)
+                    cpre = f.csub(cpre, f.t_to_c(Sr[(g.sbase(lenB) + i + b + 1) * BLOCK]));
+                f.template acc2<DS>(acc, csuf, sf, cpre, pb);
+                // momentum part: adj (P_A - P_B) = adj (2 K_{i+b+1} - K_i - K_j);
+                // the K_i + K_j share is added once per range below
+                f.template acc1<D>(acc, f.cdbl(adj), Kt);
+                // four-gluon vertex: prefix [i, i+a], inner [i+a+1, i+b], suffix sf
+                int q = 0;
+#pragma unroll 1
+                for (; q + 1 < b; q += 2) {
+                    T pa0[DS], pa1[DS], in0[DS], in1[DS];
+                    IO::template load<DS>(jvec(q + 1, i), pa0);
+                    IO::template load<DS>(jvec(q + 2, i), pa1);
+                    IO::template load<DS>(jvec(b - q, i + q + 1), in0);
+                    IO::template load<DS>(jvec(b - q - 1, i + q + 2), in1);
+                    const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
+                    const C g1 = f.cdbl(f.template dot<DS, METRIC>(pa1, sf));
+                    f.template acc2<DS>(acc, g0, in0, g1, in1);
+                }
+                if (q < b) {
+                    T pa0[DS], in0[DS];
+                    IO::template load<DS>(jvec(q + 1, i), pa0);
+                    IO::template load<DS>(jvec(b - q, i + q + 1), in0);
+                    const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
+                    f.template acc1<DS>(acc, g0, in0);
+                }
+            }
+            {
+                T KiKj[D];
+#pragma unroll
+                for (int mu = 0; mu < D; ++mu) KiKj[mu] = f.tadd(Ki[mu], Kj[mu]);
+                f.template acc1<D>(acc, f.cneg(sa), KiKj);     // - SA(i,j) (K_i + K_j)
+            }
+            if (m < N) {
+                const int sidx = g.sbase(m) + i;
+                T J[DS];
+                f.template finish<DS>(acc, Y[sidx * BLOCK], J);
+                IO::template store<DS>(jvec(m, i), J);
+                Sr[sidx * BLOCK] = f.c_to_t(sa);
+            } else {
+                // a5: contract the top bracket with the last polarisation
+                result = f.template amplitude<DS, METRIC>(acc, eL);
+            }
+        }
+    }
+    out[u] = singular ? f.zero_io() : result;
+    if (a.status != nullptr && h == 0) a.status[e] = singular ? 1 : 0;
+}
+
+template <class F, int D, int DS, int METRIC, int BLOCK, bool GLOBAL_TABLE>
+__global__ void __launch_bounds__(BLOCK)
+bg_compact_kernel(const F f, const CompactArgs a) {
+    using T = typename F::T;
+    extern __shared__ __align__(16) unsigned char bg_smem[];
+    T* tab;                                   // this block's table
+    if constexpr (GLOBAL_TABLE) {
+        const int W = Geometry{a.n - 1}.words(D, DS);
+        tab = reinterpret_cast<T*>(a.ws) + static_cast<size_t>(blockIdx.x) * W * BLOCK;
+    } else {
+        tab = reinterpret_cast<T*>(bg_smem);
+    }
     const int64_t total = a.E * a.H;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * BLOCK;
-
-    for (int64_t u = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; u < total; u += stride) {
-        int64_t e = u;
-        int h = 0;
-        if (a.H > 1) {
-            e = u / a.H;
-            h = static_cast<int>(u - e * a.H);
-        }
-        // a1: momenta -> prefix sums K_0 = 0, K_{l+1} = K_l + k_l (leg n unused:
-        // P_{1,n-1} = -k_n never enters); polarisations -> currents of length 1.
-        {
-            const io_t* kp = kin + e * NLEG * a.d_in;
-            T Kacc[D];
-#pragma unroll
-            for (int mu = 0; mu < D; ++mu) Kacc[mu] = f.zero();
-            IO::template store<D>(kvec(0), Kacc);
-#pragma unroll 1
-            for (int l = 0; l < N; ++l) {
-#pragma unroll
-                for (int mu = 0; mu < D; ++mu)
-                    if (mu < a.d_in) Kacc[mu] = f.tadd(Kacc[mu], f.from_io(kp[l * a.d_in + mu]));
-                IO::template store<D>(kvec(l + 1), Kacc);
-            }
-        }
-        T eL[DS];
-#pragma unroll 1
-        for (int l = 0; l < NLEG; ++l) {
-            const int s = (a.assign != nullptr) ? a.assign[h * NLEG + l] : 0;
-            const io_t* ep = ein + ((e * NLEG + l) * a.S + s) * a.ds_in;
-            T v[DS];
-#pragma unroll
-            for (int mu = 0; mu < DS; ++mu) v[mu] = (mu < a.ds_in) ? f.from_io(ep[mu]) : f.zero();
-            if (l < N) {
-                IO::template store<DS>(jvec(1, l), v);     // current (1, l)
-            } else {
-#pragma unroll
-                for (int mu = 0; mu < DS; ++mu) eL[mu] = v[mu];
-            }
-        }
-        // a2: P^2 of every internal range (length 2..N-1), flat index sbase(m) + i
-        T* X = Sr;     // P^2 inputs of the inverse (reuses the SA slots)
-        T* Y = Ir;     // 1/P^2
-#pragma unroll 1
-        for (int m = 2; m < N; ++m) {
-#pragma unroll 1
-            for (int i = 0; i + m - 1 < N; ++i) {
-                T Ka[D], Kb[D], P[D];
-                IO::template load<D>(kvec(i), Ka);
-                IO::template load<D>(kvec(i + m), Kb);
-#pragma unroll
-                for (int mu = 0; mu < D; ++mu) P[mu] = f.tsub(Kb[mu], Ka[mu]);
-                X[(g.sbase(m) + i) * BLOCK] = f.inv_input(f.template dot<D, METRIC>(P, P));
-            }
-        }
-        // a3: all inverses.  F_p: Montgomery simultaneous inversion (prefix
-        // products, one Fermat inverse, backward sweep); C64: per range.
-        bool singular = false;
-        const int NS = g.ns();
-        if constexpr (F::kIsFp) {
-            T c = X[0];
-            Y[0] = c;
-#pragma unroll 1
-            for (int s = 1; s < NS; ++s) {
-                c = f.inv_mul(c, X[s * BLOCK]);
-                Y[s * BLOCK] = c;
-            }
-            singular = f.is_zero(c);
-            T r = f.inv_scalar(c);
-#pragma unroll 1
-            for (int s = NS - 1; s > 0; --s) {
-                const T x = X[s * BLOCK];
-                Y[s * BLOCK] = f.inv_store(f.inv_mul(Y[(s - 1) * BLOCK], r));
-                r = f.inv_mul(r, x);
-            }
-            Y[0] = f.inv_store(r);
-        } else {
-#pragma unroll 1
-            for (int s = 0; s < NS; ++s) {
-                const T x = X[s * BLOCK];
-                singular |= f.is_zero(x);
-                Y[s * BLOCK] = f.inv_scalar(x);
-            }
-        }
-
-        // a4: the recursion, by increasing length m
-        io_t result = f.zero_io();
-#pragma unroll 1
-        for (int m = 2; m <= N; ++m) {
-#pragma unroll 1
-            for (int i = 0; i + m - 1 < N; ++i) {
-                T Ki[D], Kj[D];
-                IO::template load<D>(kvec(i), Ki);
-                IO::template load<D>(kvec(i + m), Kj);
-                Acc acc[DS];
-                f.template acc_zero<DS>(acc);
-                C sa = f.czero();
-#pragma unroll 1
-                for (int b = 0; b < m - 1; ++b) {
-                    const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
-                    T pb[DS], sf[DS], Kt[D], PA[D], PB[D];
-                    IO::template load<DS>(jvec(lenA, i), pb);
-                    IO::template load<DS>(jvec(lenB, i + b + 1), sf);
-                    IO::template load<D>(kvec(i + b + 1), Kt);
-#pragma unroll
-                    for (int mu = 0; mu < D; ++mu) {
-                        PA[mu] = f.tsub(Kt[mu], Ki[mu]);
-                        PB[mu] = f.tsub(Kj[mu], Kt[mu]);
-                    }
-                    // three-gluon vertex of the split at s = i + b
-                    const C adj = f.template dot<DS, METRIC>(pb, sf);
-                    const C pa_jb = f.template dot<D, METRIC>(PA, sf);
-                    const C pb_ja = f.template dot<D, METRIC>(PB, pb);
-                    sa = f.cadd(sa, adj);
-                    C csuf = f.cdbl(pb_ja);
-                    if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(Sr[(g.sbase(lenA) + i) * BLOCK]));
-                    C cpre = f.cneg(f.cdbl(pa_jb));
-                    if (lenB >= 2)
-                        cpre = f.csub(cpre, f.t_to_c(Sr[(g.sbase(lenB) + i + b + 1) * BLOCK]));
-                    f.template acc2<DS>(acc, csuf, sf, cpre, pb);
-                    // momentum part: adj (P_A - P_B) = adj (2 K_{i+b+1} - K_i - K_j);
-                    // the K_i + K_j share is added once per range below
-                    f.template acc1<D>(acc, f.cdbl(adj), Kt);
-                    // four-gluon vertex: prefix [i, i+a], inner [i+a+1, i+b], suffix sf
-                    int q = 0;
-#pragma unroll 1
-                    for (; q + 1 < b; q += 2) {
-                        T pa0[DS], pa1[DS], in0[DS], in1[DS];
-                        IO::template load<DS>(jvec(q + 1, i), pa0);
-                        IO::template load<DS>(jvec(q + 2, i), pa1);
-                        IO::template load<DS>(jvec(b - q, i + q + 1), in0);
-                        IO::template load<DS>(jvec(b - q - 1, i + q + 2), in1);
-                        const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
-                        const C g1 = f.cdbl(f.template dot<DS, METRIC>(pa1, sf));
-                        f.template acc2<DS>(acc, g0, in0, g1, in1);
-                    }
-                    if (q < b) {
-                        T pa0[DS], in0[DS];
-                        IO::template load<DS>(jvec(q + 1, i), pa0);
-                        IO::template load<DS>(jvec(b - q, i + q + 1), in0);
-                        const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
-                        f.template acc1<DS>(acc, g0, in0);
-                    }
-                }
-                {
-                    T KiKj[D];
-#pragma unroll
-                    for (int mu = 0; mu < D; ++mu) KiKj[mu] = f.tadd(Ki[mu], Kj[mu]);
-                    f.template acc1<D>(acc, f.cneg(sa), KiKj);     // - SA(i,j) (K_i + K_j)
-                }
-                if (m < N) {
-                    const int sidx = g.sbase(m) + i;
-                    T J[DS];
-                    f.template finish<DS>(acc, Y[sidx * BLOCK], J);
-                    IO::template store<DS>(jvec(m, i), J);
-                    Sr[sidx * BLOCK] = f.c_to_t(sa);
-                } else {
-                    // a5: contract the top bracket with the last polarisation
-                    result = f.template amplitude<DS, METRIC>(acc, eL);
-                }
-            }
-        }
-        out[u] = singular ? f.zero_io() : result;
-        if (a.status != nullptr && h == 0) a.status[e] = singular ? 1 : 0;
-    }
+    for (int64_t u = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; u < total; u += stride)
+        bg_point<F, D, DS, METRIC, BLOCK>(f, a, tab, u);
 }
 
 }  // namespace bgk
