@@ -363,6 +363,122 @@ def mixed_workload(args, device):
             "unit": "amplitudes/s", "steps": steps}
 
 
+def serve_workload(args, device):
+    """Poisson arrivals (mean rate --serve-rate per second) of requests with
+    log-uniform sizes 1..65536 points, n uniform in 4..12, d = D_s uniform in
+    {4, 6, 8}, field uniform; latency = completion - arrival.  Served by
+    (a) bg_server (continuous admission, 8 stream slots) and (b) plain
+    per-request evaluation, one request at a time (copy in, bg_eval, copy out,
+    synchronise), in arrival order."""
+    import queue
+    import threading
+
+    import torch
+    from paper_2502_07060_gb300 import bg
+    rng = np.random.default_rng(2026)
+    configs = [(f, n, d) for f in ("fp", "c64") for n in range(4, 13) for d in (4, 6, 8)]
+    pool_pts = 1 << 16
+    pools, plans = {}, {}
+    for i, (f, n, d) in enumerate(configs):
+        if f == "fp":
+            k, e = G.fp_batch(7000 + i, pool_pts, n, d, d, P, 0)
+            pools[(f, n, d)] = (torch.from_numpy(k.view(np.int32)).pin_memory(),
+                                torch.from_numpy(e.view(np.int32)).pin_memory())
+            plans[(f, n, d)] = bg.Plan(n, d, d, bg.FIELD_FP, P)
+        else:
+            k, e = G.c64_batch(7000 + i, pool_pts, n, d, d, 0)
+            pools[(f, n, d)] = (torch.from_numpy(k).pin_memory(), torch.from_numpy(e).pin_memory())
+            plans[(f, n, d)] = bg.Plan(n, d, d, bg.FIELD_C64, 0)
+    n_req = int(args.serve_rate * args.serve_seconds)
+    gaps = rng.exponential(1.0 / args.serve_rate, n_req)
+    arrivals = np.cumsum(gaps)
+    reqs = []
+    for i in range(n_req):
+        cfg = configs[rng.integers(len(configs))]
+        E = int(np.clip(np.exp(rng.uniform(0, np.log(65536))), 1, 65536))
+        off = int(rng.integers(0, pool_pts - E + 1))
+        hk, he = pools[cfg]
+        out = torch.empty(E, dtype=hk.dtype).pin_memory()
+        st = torch.empty(E, dtype=torch.uint8).pin_memory()
+        reqs.append((plans[cfg], hk[off:off + E], he[off:off + E], out, st, E))
+    total_pts = sum(r[5] for r in reqs)
+
+    def summarise(lat, t0, t_end):
+        lat = np.array(lat) * 1e3
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+                "throughput_points_per_s": total_pts / (t_end - t0),
+                "throughput_requests_per_s": n_req / (t_end - t0)}
+
+    # (a) server
+    srv = bg.Server(8 << 30, max_inflight=8)
+    done_at = [0.0] * n_req
+    tickets = queue.Queue()
+
+    def waiter():
+        while True:
+            item = tickets.get()
+            if item is None:
+                return
+            i, t = item
+            srv.wait(t)
+            done_at[i] = time.perf_counter()
+
+    waiters = [threading.Thread(target=waiter) for _ in range(16)]
+    for w in waiters:
+        w.start()
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        delay = t0 + arrivals[i] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.put((i, srv.submit(r[0], r[1], r[2], r[3], r[4])))
+    for _ in waiters:
+        tickets.put(None)
+    for w in waiters:
+        w.join()
+    t_end = max(done_at)
+    served = summarise([done_at[i] - (t0 + arrivals[i]) for i in range(n_req)], t0, t_end)
+    served["peak_arena_bytes"] = srv.stats()["peak_bytes"]
+    srv.close()
+
+    # (b) plain per-request launches, one at a time in arrival order
+    stream = torch.cuda.current_stream(device)
+    work = queue.Queue()
+    done_plain = [0.0] * n_req
+
+    def worker():
+        while True:
+            item = work.get()
+            if item is None:
+                return
+            i = item
+            plan, hk, he, out, st, E = reqs[i]
+            dk = hk.to(device, non_blocking=True)
+            de = he.to(device, non_blocking=True)
+            o, s_ = plan.eval(dk, de, stream=stream)
+            out.copy_(o, non_blocking=True)
+            st.copy_(s_, non_blocking=True)
+            torch.cuda.synchronize(device)
+            done_plain[i] = time.perf_counter()
+
+    wt = threading.Thread(target=worker)
+    wt.start()
+    t0 = time.perf_counter()
+    for i in range(n_req):
+        delay = t0 + arrivals[i] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        work.put(i)
+    work.put(None)
+    wt.join()
+    plain = summarise([done_plain[i] - (t0 + arrivals[i]) for i in range(n_req)], t0, max(done_plain))
+    return {"workload": f"Poisson arrivals at {args.serve_rate}/s for {args.serve_seconds} s, "
+                        f"{n_req} requests, sizes log-uniform 1..65536 (total {total_pts} points), "
+                        "n uniform 4..12, d = D_s uniform {4, 6, 8}, F_p or C64",
+            "server": served, "plain_per_request": plain}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,8 +490,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fields", default="fp,c64", help="comma list of fp, c64")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
-    ap.add_argument("--workload", choices=["metric", "mixed"], default="metric",
-                    help="metric: n=8 d=6 headline line; mixed: uneven-batch comparison")
+    ap.add_argument("--workload", choices=["metric", "mixed", "serve"], default="metric",
+                    help="metric: n=8 d=6 headline line; mixed: uneven-batch comparison; "
+                         "serve: p50/p99 latency of the request server")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -424,6 +543,10 @@ def main():
     if args.workload == "mixed":
         if rank == 0:
             print(json.dumps({"metric": METRIC, "mixed": mixed_workload(args, device)}))
+        return
+    if args.workload == "serve":
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "serve": serve_workload(args, device)}))
         return
     dist = init_dist(world, "nccl")
     fields = args.fields.split(",")

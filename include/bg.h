@@ -54,8 +54,8 @@ typedef enum {
     BG_ERR_UNSUPPORTED = 2,   /* valid request this build has no kernel for    */
     BG_ERR_NOMEM = 3,         /* host or device allocation failed (plan only)  */
     BG_ERR_CUDA = 4,          /* CUDA runtime error (launch, device mismatch)  */
-    BG_ERR_TIMEOUT = 5,       /* reserved for serving waits                    */
-    BG_ERR_BUSY = 6           /* reserved for serving admission                */
+    BG_ERR_TIMEOUT = 5,       /* serving: the wait's deadline passed           */
+    BG_ERR_BUSY = 6           /* serving: the server is shutting down          */
 } bg_status;
 
 typedef enum {
@@ -240,6 +240,45 @@ bg_status bg_batch_destroy(bg_batch* batch);
 bg_status bg_batch_autotune(const bg_group* groups, int n_groups, void* workspace,
                             size_t workspace_bytes, int reps, cudaStream_t stream,
                             bg_batch_config* best, double* best_ms);
+
+/*
+ * Serving: evaluation requests of mixed size and configuration, submitted
+ * from host threads (the request stream of a finite-field reconstruction or
+ * Monte Carlo consumer, Sec. 1) and run with continuous admission.
+ *
+ * bg_serve_create allocates one device arena of `budget_bytes` on the current
+ * device and starts a dispatcher thread with `max_inflight` stream slots
+ * (1..64).  A submitted request is admitted as soon as a slot and arena
+ * memory for its inputs, outputs and workspace are free -- while earlier
+ * requests are still running -- so the copies and kernels of concurrent
+ * requests overlap on the device.  Admission is first-come-first-served, but
+ * a request that does not fit may be overtaken by later ones until it has
+ * waited 50 ms.  Host buffers (momenta, eps, out, status as for bg_eval) must
+ * stay valid until bg_serve_wait returns; page-locked memory lets copies
+ * overlap.  Every result equals what bg_eval gives for the request alone.
+ */
+typedef struct bg_server bg_server;
+
+bg_status bg_serve_create(size_t budget_bytes, int max_inflight, bg_server** out);
+
+/* bg_serve_submit -- queue E >= 1 points of `plan`; returns a ticket.
+ * BG_ERR_INVALID_ARG when the request can never fit the budget; BG_ERR_BUSY
+ * after bg_serve_destroy has begun. */
+bg_status bg_serve_submit(bg_server* srv, const bg_plan* plan, int64_t E, const void* momenta,
+                          const void* eps, void* out, uint8_t* status, uint64_t* ticket);
+
+/* bg_serve_wait -- block until the ticket's results are in its host buffers
+ * (BG_OK, the ticket is then retired), or until timeout_ms elapsed
+ * (BG_ERR_TIMEOUT, the ticket stays valid); timeout_ms < 0 waits forever. */
+bg_status bg_serve_wait(bg_server* srv, uint64_t ticket, int64_t timeout_ms);
+
+/* bg_serve_stats -- counters (any pointer may be NULL). */
+bg_status bg_serve_stats(bg_server* srv, uint64_t* submitted, uint64_t* completed,
+                         uint64_t* pending, size_t* bytes_in_use, size_t* peak_bytes);
+
+/* bg_serve_destroy -- finish every queued and running request, then free the
+ * arena, streams and thread.  No call on `srv` may follow. */
+bg_status bg_serve_destroy(bg_server* srv);
 
 /* bg_plan_describe -- NUL-terminated one-line description of the kernel the
  * plan launches (variant, block size, shared memory, workspace per thread)

@@ -33,7 +33,9 @@ ALTERNATING = 1
 EXPORTED = ("bg_plan_create", "bg_plan_destroy", "bg_workspace_size", "bg_eval",
             "bg_eval_noalloc", "bg_host_staging_size", "bg_eval_host", "bg_batch_workspace_size",
             "bg_batch_create", "bg_batch_launch", "bg_batch_describe", "bg_batch_destroy",
-            "bg_batch_autotune", "bg_plan_describe", "bg_strerror", "bg_last_error", "bg_version")
+            "bg_batch_autotune", "bg_serve_create", "bg_serve_submit", "bg_serve_wait",
+            "bg_serve_stats", "bg_serve_destroy", "bg_plan_describe", "bg_strerror", "bg_last_error",
+            "bg_version")
 
 LIB_PATH = _build.LIB
 
@@ -88,6 +90,18 @@ def load_library(path=None):
     lib.bg_batch_autotune.argtypes = [gp, ctypes.c_int, vp, ctypes.c_size_t, ctypes.c_int, vp, cp,
                                       ctypes.POINTER(ctypes.c_double)]
     lib.bg_batch_autotune.restype = ctypes.c_int
+    lib.bg_serve_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.bg_serve_create.restype = ctypes.c_int
+    lib.bg_serve_submit.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.bg_serve_submit.restype = ctypes.c_int
+    lib.bg_serve_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int64]
+    lib.bg_serve_wait.restype = ctypes.c_int
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    szp = ctypes.POINTER(ctypes.c_size_t)
+    lib.bg_serve_stats.argtypes = [vp, u64p, u64p, u64p, szp, szp]
+    lib.bg_serve_stats.restype = ctypes.c_int
+    lib.bg_serve_destroy.argtypes = [vp]
+    lib.bg_serve_destroy.restype = ctypes.c_int
     lib.bg_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.bg_plan_describe.restype = ctypes.c_int
     lib.bg_strerror.argtypes = [ctypes.c_int]
@@ -309,6 +323,56 @@ class Batch:
         _check(_lib.bg_batch_autotune(arr, len(groups), _ptr(ws), ws.numel(), reps,
                                       _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms)))
         return best, ms.value
+
+
+class Server:
+    """bg_server: continuous admission of evaluation requests on host buffers.
+
+    submit() returns a ticket; wait(ticket, timeout_ms) returns True when the
+    results are in the request's host tensors, False on timeout.  The caller
+    keeps the request's tensors alive until its wait succeeds (the server
+    also keeps references until then)."""
+
+    def __init__(self, budget_bytes, max_inflight=8):
+        h = ctypes.c_void_p()
+        _check(_lib.bg_serve_create(budget_bytes, max_inflight, ctypes.byref(h)))
+        self._h = h
+        self._live = {}
+
+    def submit(self, plan, momenta, eps, out, status=None):
+        t = ctypes.c_uint64()
+        _check(_lib.bg_serve_submit(self._h, plan.handle, momenta.shape[0], _ptr(momenta), _ptr(eps),
+                                    _ptr(out), _ptr(status), ctypes.byref(t)))
+        self._live[t.value] = (plan, momenta, eps, out, status)
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        st = _lib.bg_serve_wait(self._h, ticket, timeout_ms)
+        if st == BG_ERR_TIMEOUT:
+            return False
+        self._live.pop(ticket, None)
+        _check(st)
+        return True
+
+    def stats(self):
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        d, e = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(_lib.bg_serve_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                   ctypes.byref(d), ctypes.byref(e)))
+        return {"submitted": a.value, "completed": b.value, "pending": c.value,
+                "bytes_in_use": d.value, "peak_bytes": e.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.bg_serve_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def strerror(status):

@@ -1,0 +1,368 @@
+// bg_serve.cu -- a request server for evaluation requests of mixed size and
+// configuration (the request stream of a reconstruction or Monte Carlo
+// consumer of these amplitudes).
+//
+// Design:
+//   * one device arena of `budget` bytes, allocated at bg_serve_create and
+//     sub-allocated first-fit (256-byte granules) for each admitted request:
+//     its inputs, outputs and kernel workspace;
+//   * a dispatcher thread admits pending requests while memory and a stream
+//     slot are free -- continuously, not in rounds: a request that arrives
+//     while others run is admitted as soon as a slot and memory free up, and
+//     its copies and kernel overlap with the work already on the device;
+//   * admission is first-come-first-served, except that a request that does
+//     not fit may be overtaken by later ones until it has waited kStarveMs,
+//     after which nothing overtakes it;
+//   * each admitted request runs on its own stream slot: host->device copies,
+//     one bg_eval launch, device->host copies, then a host function (run by
+//     the CUDA driver, no CUDA calls in it) that marks the slot finished;
+//   * bg_serve_wait blocks on a condition variable with a deadline and
+//     returns BG_ERR_TIMEOUT when the request is not done by then.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "bg_internal.h"
+
+namespace {
+
+constexpr size_t kGranule = 256;
+constexpr double kStarveMs = 50.0;
+
+using Clock = std::chrono::steady_clock;
+
+size_t up_granule(size_t x) { return (x + kGranule - 1) & ~(kGranule - 1); }
+
+// First-fit allocator over [0, size) with coalescing (host bookkeeping only).
+class Arena {
+public:
+    explicit Arena(size_t size) { free_[0] = size; }
+    bool alloc(size_t bytes, size_t* off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, start = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+
+private:
+    std::map<size_t, size_t> free_;
+    size_t used_ = 0;
+};
+
+enum class State { Pending, Running, Done, Failed };
+
+struct Request {
+    uint64_t id;
+    const bg_plan* plan;
+    int64_t E;
+    const void* k;
+    const void* eps;
+    void* out;
+    uint8_t* status;
+    size_t bytes_k, bytes_e, bytes_o, bytes_s, bytes_ws, total;
+    Clock::time_point submitted;
+    State state = State::Pending;
+    bg_status result = BG_OK;
+    size_t off = 0;
+    int slot = -1;
+};
+
+}  // namespace
+
+struct bg_server {
+    int device = -1;
+    size_t budget = 0;
+    unsigned char* arena_mem = nullptr;
+    Arena* arena = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<Request*> slot_req;          // request running on each slot (or null)
+    std::vector<int> slot_done;              // set by the host function
+    std::mutex mu;
+    std::condition_variable cv_work;         // dispatcher: new request or slot finished
+    std::condition_variable cv_done;         // waiters
+    std::deque<Request*> pending;
+    std::map<uint64_t, Request*> requests;   // all not yet collected
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread thread;
+    // statistics
+    uint64_t n_submitted = 0, n_completed = 0;
+    size_t peak_used = 0;
+};
+
+namespace {
+
+struct SlotDone {
+    bg_server* srv;
+    int slot;
+};
+
+void CUDART_CB slot_finished(void* arg) {
+    SlotDone* sd = static_cast<SlotDone*>(arg);
+    {
+        std::lock_guard<std::mutex> lk(sd->srv->mu);
+        sd->srv->slot_done[sd->slot] = 1;
+    }
+    sd->srv->cv_work.notify_one();
+    delete sd;
+}
+
+// Enqueue the copies, the kernel and the completion callback of r on its slot.
+bg_status launch_request(bg_server* s, Request* r) {
+    cudaStream_t st = s->streams[r->slot];
+    unsigned char* base = s->arena_mem + r->off;
+    unsigned char* dk = base;
+    unsigned char* de = dk + r->bytes_k;
+    unsigned char* dout = de + r->bytes_e;
+    uint8_t* dst = reinterpret_cast<uint8_t*>(dout + r->bytes_o);
+    unsigned char* ws = dout + r->bytes_o + r->bytes_s;
+    const size_t elem = r->plan->field == BG_FIELD_FP ? 4 : 16;
+    const size_t nk = (size_t)r->E * r->plan->n * r->plan->d * elem;
+    const size_t ne = (size_t)r->E * r->plan->n * r->plan->S * r->plan->Ds * elem;
+    const size_t no = (size_t)r->E * r->plan->H * elem;
+    cudaError_t err = cudaMemcpyAsync(dk, r->k, nk, cudaMemcpyHostToDevice, st);
+    if (!err) err = cudaMemcpyAsync(de, r->eps, ne, cudaMemcpyHostToDevice, st);
+    if (err) { cudaGetLastError(); return BG_ERR_CUDA; }
+    bg_status bs = bg_eval(r->plan, r->E, dk, de, dout, dst, r->bytes_ws ? ws : nullptr, r->bytes_ws, st);
+    if (bs != BG_OK) return bs;
+    err = cudaMemcpyAsync(r->out, dout, no, cudaMemcpyDeviceToHost, st);
+    if (!err && r->status) err = cudaMemcpyAsync(r->status, dst, (size_t)r->E, cudaMemcpyDeviceToHost, st);
+    SlotDone* sd = new (std::nothrow) SlotDone{s, r->slot};
+    if (!sd) return BG_ERR_NOMEM;
+    if (!err) err = cudaLaunchHostFunc(st, slot_finished, sd);
+    if (err) { delete sd; cudaGetLastError(); return BG_ERR_CUDA; }
+    return BG_OK;
+}
+
+void dispatcher(bg_server* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        // collect finished slots
+        bool progressed = false;
+        for (size_t i = 0; i < s->streams.size(); ++i) {
+            if (s->slot_req[i] && s->slot_done[i]) {
+                Request* r = s->slot_req[i];
+                s->arena->release(r->off, r->total);
+                r->state = State::Done;
+                s->slot_req[i] = nullptr;
+                s->slot_done[i] = 0;
+                ++s->n_completed;
+                progressed = true;
+            }
+        }
+        if (progressed) s->cv_done.notify_all();
+        // admit
+        const auto now = Clock::now();
+        bool blocked_head = false;
+        for (auto it = s->pending.begin(); it != s->pending.end();) {
+            int slot = -1;
+            for (size_t i = 0; i < s->slot_req.size(); ++i)
+                if (!s->slot_req[i]) { slot = (int)i; break; }
+            if (slot < 0) break;
+            Request* r = *it;
+            size_t off = 0;
+            if (!blocked_head && s->arena->alloc(r->total, &off)) {
+                r->off = off;
+                r->slot = slot;
+                r->state = State::Running;
+                s->slot_req[slot] = r;
+                s->slot_done[slot] = 0;
+                if (s->arena->used() > s->peak_used) s->peak_used = s->arena->used();
+                it = s->pending.erase(it);
+                bg_status st = launch_request(s, r);
+                if (st != BG_OK) {              // nothing of r was enqueued after the failure point
+                    cudaStreamSynchronize(s->streams[slot]);
+                    s->arena->release(r->off, r->total);
+                    s->slot_req[slot] = nullptr;
+                    r->state = State::Failed;
+                    r->result = st;
+                    s->cv_done.notify_all();
+                }
+                continue;
+            }
+            // does not fit: later requests may overtake unless this one starves
+            const double waited = std::chrono::duration<double, std::milli>(now - r->submitted).count();
+            if (waited > kStarveMs) blocked_head = true;
+            ++it;
+        }
+        if (s->stop && s->pending.empty()) {
+            bool busy = false;
+            for (auto* r : s->slot_req) busy |= (r != nullptr);
+            if (!busy) break;
+        }
+        s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+bg_status bg_serve_create(size_t budget_bytes, int max_inflight, bg_server** out) {
+    if (!out) return bgi::fail(BG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (budget_bytes < kGranule || max_inflight < 1 || max_inflight > 64)
+        return bgi::fail(BG_ERR_INVALID_ARG, "budget >= 256 B and 1 <= max_inflight <= 64 required");
+    bg_server* s = new (std::nothrow) bg_server();
+    if (!s) return bgi::fail(BG_ERR_NOMEM, "host allocation failed");
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return bgi::fail(BG_ERR_CUDA, "no current CUDA device");
+    }
+    s->budget = budget_bytes & ~(kGranule - 1);
+    if (cudaMalloc(&s->arena_mem, s->budget) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return bgi::fail(BG_ERR_NOMEM, "device arena of %zu B could not be allocated", budget_bytes);
+    }
+    s->arena = new Arena(s->budget);
+    s->streams.resize(max_inflight);
+    s->slot_req.assign(max_inflight, nullptr);
+    s->slot_done.assign(max_inflight, 0);
+    for (int i = 0; i < max_inflight; ++i) {
+        if (cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            for (int j = 0; j < i; ++j) cudaStreamDestroy(s->streams[j]);
+            cudaFree(s->arena_mem);
+            delete s->arena;
+            delete s;
+            return bgi::fail(BG_ERR_CUDA, "stream creation failed");
+        }
+    }
+    s->thread = std::thread(dispatcher, s);
+    *out = s;
+    return BG_OK;
+}
+
+bg_status bg_serve_submit(bg_server* srv, const bg_plan* plan, int64_t E, const void* momenta,
+                          const void* eps, void* out, uint8_t* status, uint64_t* ticket) {
+    if (!srv || !plan || !ticket) return bgi::fail(BG_ERR_INVALID_ARG, "server, plan and ticket are required");
+    if (E < 1 || !momenta || !eps || !out) return bgi::fail(BG_ERR_INVALID_ARG, "E >= 1 and host buffers required");
+    if (plan->d_assign && plan->device != srv->device)
+        return bgi::fail(BG_ERR_INVALID_ARG, "plan and server are on different devices");
+    Request* r = new (std::nothrow) Request();
+    if (!r) return bgi::fail(BG_ERR_NOMEM, "host allocation failed");
+    const size_t elem = plan->field == BG_FIELD_FP ? 4 : 16;
+    r->plan = plan;
+    r->E = E;
+    r->k = momenta;
+    r->eps = eps;
+    r->out = out;
+    r->status = status;
+    r->bytes_k = up_granule((size_t)E * plan->n * plan->d * elem);
+    r->bytes_e = up_granule((size_t)E * plan->n * plan->S * plan->Ds * elem);
+    r->bytes_o = up_granule((size_t)E * plan->H * elem);
+    r->bytes_s = up_granule((size_t)E);
+    size_t ws = 0;
+    bg_workspace_size(plan, E, &ws);
+    r->bytes_ws = up_granule(ws);
+    r->total = r->bytes_k + r->bytes_e + r->bytes_o + r->bytes_s + r->bytes_ws;
+    if (r->total > srv->budget) {
+        const size_t need = r->total;
+        delete r;
+        return bgi::fail(BG_ERR_INVALID_ARG, "request needs %zu B, above the server budget of %zu B", need,
+                         srv->budget);
+    }
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->stop) {
+            delete r;
+            return bgi::fail(BG_ERR_BUSY, "server is shutting down");
+        }
+        r->id = srv->next_id++;
+        r->submitted = Clock::now();
+        srv->pending.push_back(r);
+        srv->requests[r->id] = r;
+        ++srv->n_submitted;
+        *ticket = r->id;
+    }
+    srv->cv_work.notify_one();
+    return BG_OK;
+}
+
+bg_status bg_serve_wait(bg_server* srv, uint64_t ticket, int64_t timeout_ms) {
+    if (!srv) return bgi::fail(BG_ERR_INVALID_ARG, "server is NULL");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->requests.find(ticket);
+    if (it == srv->requests.end()) return bgi::fail(BG_ERR_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    Request* r = it->second;
+    auto finished = [r] { return r->state == State::Done || r->state == State::Failed; };
+    if (timeout_ms < 0) {
+        srv->cv_done.wait(lk, finished);
+    } else if (!srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), finished)) {
+        return bgi::fail(BG_ERR_TIMEOUT, "request %llu not finished after %lld ms", (unsigned long long)ticket,
+                         (long long)timeout_ms);
+    }
+    const bg_status result = r->state == State::Done ? BG_OK : r->result;
+    srv->requests.erase(it);
+    delete r;
+    if (result != BG_OK) return bgi::fail(result, "request failed");
+    return BG_OK;
+}
+
+bg_status bg_serve_stats(bg_server* srv, uint64_t* submitted, uint64_t* completed, uint64_t* pending,
+                         size_t* bytes_in_use, size_t* peak_bytes) {
+    if (!srv) return bgi::fail(BG_ERR_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (submitted) *submitted = srv->n_submitted;
+    if (completed) *completed = srv->n_completed;
+    if (pending) *pending = srv->pending.size();
+    if (bytes_in_use) *bytes_in_use = srv->arena->used();
+    if (peak_bytes) *peak_bytes = srv->peak_used;
+    return BG_OK;
+}
+
+bg_status bg_serve_destroy(bg_server* srv) {
+    if (!srv) return BG_OK;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv_work.notify_all();
+    if (srv->thread.joinable()) srv->thread.join();
+    for (cudaStream_t st : srv->streams) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    cudaFree(srv->arena_mem);
+    for (auto& kv : srv->requests) delete kv.second;
+    delete srv->arena;
+    delete srv;
+    return BG_OK;
+}
+
+}  // extern "C"

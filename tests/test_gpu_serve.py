@@ -1,0 +1,100 @@
+"""Serving: every request's result is the same alone and in the mix (bit-exact
+over F_p; identical complex results, since the same kernel runs), waits time
+out with an error instead of blocking, and admission respects the device
+memory budget."""
+
+import numpy as np
+import pytest
+
+from paper_2502_07060_gb300 import inputs as G
+
+pytestmark = pytest.mark.gpu
+
+P = G.P_DEFAULT
+
+
+def _request(bg, field, n, d, E, seed):
+    import torch
+    if field == "fp":
+        k, e = G.fp_batch(seed, E, n, d, d, P, 0, workers=1)
+        hk = torch.from_numpy(k.view(np.int32)).pin_memory()
+        he = torch.from_numpy(e.view(np.int32)).pin_memory()
+        plan = bg.Plan(n, d, d, bg.FIELD_FP, P)
+    else:
+        k, e = G.c64_batch(seed, E, n, d, d, 0, workers=1)
+        hk = torch.from_numpy(k).pin_memory()
+        he = torch.from_numpy(e).pin_memory()
+        plan = bg.Plan(n, d, d, bg.FIELD_C64, 0)
+    out = torch.empty(E, dtype=hk.dtype).pin_memory()
+    st = torch.empty(E, dtype=torch.uint8).pin_memory()
+    return plan, hk, he, out, st
+
+
+def _alone(plan, hk, he):
+    import torch
+    o, s = plan.eval(hk.cuda(), he.cuda())
+    torch.cuda.synchronize()
+    return o.cpu(), s.cpu()
+
+
+def test_results_alone_equal_results_in_the_mix():
+    import torch
+    from paper_2502_07060_gb300 import bg
+    rng = np.random.default_rng(3)
+    reqs = []
+    for i in range(40):
+        field = "fp" if i % 2 else "c64"
+        n = int(rng.integers(4, 13))
+        d = int(rng.choice([4, 6, 8]))
+        E = int(np.exp(rng.uniform(0, np.log(4000))))
+        reqs.append(_request(bg, field, n, d, max(E, 1), 500 + i))
+    refs = [_alone(p, k, e) for p, k, e, _, _ in reqs]
+    srv = bg.Server(256 << 20, max_inflight=6)
+    tickets = [srv.submit(p, k, e, o, s) for p, k, e, o, s in reqs]
+    for t in tickets[::-1]:                       # wait in reverse order
+        assert srv.wait(t, timeout_ms=60000)
+    for (p, _, _, o, s), (ro, rs) in zip(reqs, refs):
+        assert torch.equal(o, ro), p.describe()
+        assert torch.equal(s, rs)
+    st = srv.stats()
+    assert st["completed"] == 40 and st["pending"] == 0 and st["bytes_in_use"] == 0
+    assert st["peak_bytes"] <= 256 << 20
+    srv.close()
+
+
+def test_wait_times_out_then_completes():
+    from paper_2502_07060_gb300 import bg
+    big = [_request(bg, "c64", 12, 8, 65536, 900 + i) for i in range(2)]
+    srv = bg.Server(1 << 30, max_inflight=1)
+    t1 = srv.submit(*big[0])
+    t2 = srv.submit(*big[1])
+    assert srv.wait(t2, timeout_ms=0) is False          # still queued behind t1
+    with pytest.raises(bg.BGError) as ei:
+        bg._check(bg._lib.bg_serve_wait(srv._h, t2, 0))
+    assert ei.value.status == bg.BG_ERR_TIMEOUT
+    assert srv.wait(t1, timeout_ms=-1) and srv.wait(t2, timeout_ms=-1)
+    ref = _alone(*big[1][:3])
+    assert np.array_equal(big[1][3].numpy(), ref[0].numpy())
+    srv.close()
+
+
+def test_budget_admission():
+    import torch
+    from paper_2502_07060_gb300 import bg
+    reqs = [_request(bg, "fp", 8, 6, 20000, 700 + i) for i in range(5)]
+
+    def up(x):
+        return (x + 255) // 256 * 256
+    E = 20000
+    one = (up(E * 8 * 6 * 4) * 2 + up(E * 4) + up(E) + up(reqs[0][0].workspace_size(E)))
+    budget = int(one * 1.5)
+    srv = bg.Server(budget, max_inflight=4)                       # room for one request at a time
+    with pytest.raises(bg.BGError) as ei:                              # can never fit
+        srv.submit(*_request(bg, "fp", 8, 6, 200000, 1))
+    assert ei.value.status == bg.BG_ERR_INVALID_ARG
+    ts = [srv.submit(*r) for r in reqs]
+    assert all(srv.wait(t, timeout_ms=60000) for t in ts)
+    for p, k, e, o, s in reqs:
+        assert torch.equal(o, _alone(p, k, e)[0])
+    assert one <= srv.stats()["peak_bytes"] <= budget
+    srv.close()
