@@ -6,7 +6,9 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -105,6 +107,24 @@ bg_status check_device_ptr(const void* ptr, const char* what, int device) {
 }
 
 int round_dim(int x) { return x <= 4 ? 4 : (x <= 6 ? 6 : 8); }
+
+// The dynamic shared-memory limit is an attribute of the kernel function, not
+// of a plan: raise it to `bytes` on `device` if it is lower, never lower it
+// (plans sharing a kernel may need different sizes).
+bg_status ensure_smem_limit(const void* func, int device, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> limit;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = limit[{func, device}];
+    if (cur >= bytes) return BG_OK;
+    cudaError_t err = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BG_ERR_UNSUPPORTED, "shared memory %zu B: %s", bytes, cudaGetErrorString(err));
+    }
+    cur = bytes;
+    return BG_OK;
+}
 
 }  // namespace bgi
 
@@ -236,12 +256,10 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
     cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device);
     pl->smem_bytes = best->global_table ? 0 : (size_t)words * best->block * best->elem_bytes;
     if (pl->smem_bytes > 0) {
-        cudaError_t err = cudaFuncSetAttribute(best->func, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)pl->smem_bytes);
-        if (err != cudaSuccess) {
-            cudaGetLastError();
+        bg_status st = bgi::ensure_smem_limit(best->func, pl->device, pl->smem_bytes);
+        if (st != BG_OK) {
             delete pl;
-            return fail(BG_ERR_UNSUPPORTED, "shared memory %zu B: %s", pl->smem_bytes, cudaGetErrorString(err));
+            return st;
         }
     }
     int occ = 0;
@@ -341,12 +359,7 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const voi
         if ((st = check_device_ptr(workspace, "workspace", dev)) != BG_OK) return st;
     }
     if (dev != plan->device && plan->smem_bytes > 0) {
-        cudaError_t err = cudaFuncSetAttribute(e->func, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)plan->smem_bytes);
-        if (err != cudaSuccess) {
-            cudaGetLastError();
-            return fail(BG_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
-        }
+        if ((st = bgi::ensure_smem_limit(e->func, dev, plan->smem_bytes)) != BG_OK) return st;
     }
 
     const int64_t items = E * plan->H;

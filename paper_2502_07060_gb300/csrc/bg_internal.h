@@ -34,4 +34,5 @@ const std::vector<bgk::KernelEntry>& registry();
 bg_status fail(bg_status s, const char* fmt, ...);
 bg_status check_device_ptr(const void* ptr, const char* what, int device);
 int round_dim(int x);
+bg_status ensure_smem_limit(const void* func, int device, size_t bytes);
 }  // namespace bgi

@@ -312,3 +312,18 @@ def test_eval_host_pipeline_matches_device_eval(field, pinned):
         out, st = plan.eval_host(hk, he, chunk=chunk)
         torch.cuda.synchronize()
         assert torch.equal(out, ref.cpu()) and torch.equal(st, rst.cpu())
+
+
+def test_plans_sharing_a_kernel_keep_their_shared_memory():
+    """A later plan with a smaller shared-memory table on the same kernel must
+    not lower the limit an earlier plan relies on."""
+    bg = _bg()
+    with _env(BG_TABLE="shared"):
+        big = bg.Plan(7, 6, 6, bg.FIELD_FP, P)
+        small = bg.Plan(4, 6, 6, bg.FIELD_FP, P)
+    assert "table=shared" in big.describe() and "table=shared" in small.describe()
+    for plan, n in ((big, 7), (small, 4)):
+        k, eps = G.fp_batch(5 + n, 300, n, 6, 6, P, 0)
+        ref, _ = C.amp_fp(k, eps, P, 0)
+        out, _ = plan.eval(_dev_u32(k), _dev_u32(eps))
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), ref)
