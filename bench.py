@@ -183,12 +183,23 @@ def init_dist(world, backend):
 
 
 def max_over_ranks(x, dist, device):
+    """Largest value of x over the ranks (the step time of the slowest rank)."""
     if dist is None:
         return x
     import torch
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_seed(base, rank):
+    """Each rank evaluates its own independent batch (weak scaling)."""
+    return base + rank
+
+
+def job_value(points_per_rank, world, ms_max):
+    """Whole-job amplitudes/s: the points of all ranks over the slowest rank's time."""
+    return world * points_per_rank / (ms_max / 1e3)
 
 
 # --------------------------------------------------------------------------
@@ -552,20 +563,20 @@ def main():
     fields = args.fields.split(",")
     e2e = not args.no_e2e
     if fields == ["c64"]:
-        c64 = run_field("c64", Ec, args.steps, args.warmup, rank, dist, device, 2000 + rank, e2e)
+        c64 = run_field("c64", Ec, args.steps, args.warmup, rank, dist, device, rank_seed(2000, rank), e2e)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "c64_only": True, "value": world * c64["value_per_rank"],
                               "unit": "amplitudes/s", "ms_per_step": c64["ms_per_step"],
                               "plan": c64["plan"], "clocks": c64["clocks"]}))
         return
-    fp = run_field("fp", E, args.steps, args.warmup, rank, dist, device, 1000 + rank, e2e)
+    fp = run_field("fp", E, args.steps, args.warmup, rank, dist, device, rank_seed(1000, rank), e2e)
     if "c64" in fields:
         c64_steps = max(3, args.steps // 5)
-        c64 = run_field("c64", Ec, c64_steps, args.warmup, rank, dist, device, 2000 + rank, e2e)
+        c64 = run_field("c64", Ec, c64_steps, args.warmup, rank, dist, device, rank_seed(2000, rank), e2e)
     else:
         c64 = None
 
-    value = world * fp["value_per_rank"]
+    value = job_value(E, world, fp["ms_per_step"])
     tally, _ = literal_tally(N_LEG, D, DS)
     peaks = read_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0) or 2070.0
