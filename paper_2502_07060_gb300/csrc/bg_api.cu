@@ -270,10 +270,6 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
         delete pl;
         return fail(BG_ERR_UNSUPPORTED, "kernel cannot be resident (%s)", cudaGetErrorString(err));
     }
-    if (const char* cap = getenv("BG_BLOCKS_PER_SM")) {     // residency cap for experiments
-        const int c = atoi(cap);
-        if (c > 0 && c < occ) occ = c;
-    }
     pl->blocks_per_sm = occ;
     if (n_assign > 1) {
         size_t bytes = pl->assign.size();

@@ -268,6 +268,24 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
                 // four-gluon vertex: prefix [i, i+a], inner [i+a+1, i+b], suffix sf
                 int q = 0;
 #pragma unroll 1
+                for (; q + 3 < b; q += 4) {
+                    T pa0[DS], pa1[DS], pa2[DS], pa3[DS], in0[DS], in1[DS], in2[DS], in3[DS];
+                    IO::template load<DS>(jvec(q + 1, i), pa0);
+                    IO::template load<DS>(jvec(q + 2, i), pa1);
+                    IO::template load<DS>(jvec(q + 3, i), pa2);
+                    IO::template load<DS>(jvec(q + 4, i), pa3);
+                    IO::template load<DS>(jvec(b - q, i + q + 1), in0);
+                    IO::template load<DS>(jvec(b - q - 1, i + q + 2), in1);
+                    IO::template load<DS>(jvec(b - q - 2, i + q + 3), in2);
+                    IO::template load<DS>(jvec(b - q - 3, i + q + 4), in3);
+                    const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
+                    const C g1 = f.cdbl(f.template dot<DS, METRIC>(pa1, sf));
+                    const C g2 = f.cdbl(f.template dot<DS, METRIC>(pa2, sf));
+                    const C g3 = f.cdbl(f.template dot<DS, METRIC>(pa3, sf));
+                    f.template acc2<DS>(acc, g0, in0, g1, in1);
+                    f.template acc2<DS>(acc, g2, in2, g3, in3);
+                }
+#pragma unroll 1
                 for (; q + 1 < b; q += 2) {
                     T pa0[DS], pa1[DS], in0[DS], in1[DS];
                     IO::template load<DS>(jvec(q + 1, i), pa0);
@@ -309,8 +327,7 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
 }
 
 template <class F, int D, int DS, int METRIC, int BLOCK, bool GLOBAL_TABLE>
-__global__ void __launch_bounds__(BLOCK)
-bg_compact_kernel(const F f, const CompactArgs a) {
+__device__ __forceinline__ void compact_body(const F& f, const CompactArgs& a) {
     using T = typename F::T;
     extern __shared__ __align__(16) unsigned char bg_smem[];
     T* tab;                                   // this block's table
@@ -324,6 +341,12 @@ bg_compact_kernel(const F f, const CompactArgs a) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * BLOCK;
     for (int64_t u = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; u < total; u += stride)
         bg_point<F, D, DS, METRIC, BLOCK>(f, a, tab, u);
+}
+
+template <class F, int D, int DS, int METRIC, int BLOCK, bool GLOBAL_TABLE>
+__global__ void __launch_bounds__(BLOCK)
+bg_compact_kernel(const F f, const CompactArgs a) {
+    compact_body<F, D, DS, METRIC, BLOCK, GLOBAL_TABLE>(f, a);
 }
 
 }  // namespace bgk
