@@ -227,7 +227,9 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
         }
     }
 
-    // a4: the recursion, by increasing length m
+    // a4: the recursion, by increasing length m.  Slot indices of the
+    // sub-currents are advanced incrementally (count(L) = N - L + 1 slots per
+    // length L) instead of being recomputed from jbase() at every access.
     io_t result = f.zero_io();
 #pragma unroll 1
     for (int m = 2; m <= N; ++m) {
@@ -239,12 +241,15 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
             Acc acc[DS];
             f.template acc_zero<DS>(acc);
             C sa = f.czero();
+            int ps = i;                          // slot of the prefix [i, i+b]      (length b+1)
+            int ss = g.jbase(m - 1) + i + 1;     // slot of the suffix [i+b+1, j]    (length m-1-b)
+            int es = i - N;                      // first inner slot [i+1, i+b]: jbase(b) + i + 1
 #pragma unroll 1
             for (int b = 0; b < m - 1; ++b) {
                 const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
                 T pb[DS], sf[DS], Kt[D], PA[D], PB[D];
-                IO::template load<DS>(jvec(lenA, i), pb);
-                IO::template load<DS>(jvec(lenB, i + b + 1), sf);
+                IO::template load<DS>(IO::template vec<DS>(Jr, ps), pb);
+                IO::template load<DS>(IO::template vec<DS>(Jr, ss), sf);
                 IO::template load<D>(kvec(i + b + 1), Kt);
 #pragma unroll
                 for (int mu = 0; mu < D; ++mu) {
@@ -257,27 +262,33 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
                 const C pb_ja = f.template dot<D, METRIC>(PB, pb);
                 sa = f.cadd(sa, adj);
                 C csuf = f.cdbl(pb_ja);
-                if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(Sr[(g.sbase(lenA) + i) * BLOCK]));
+                if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(Sr[(ps - N) * BLOCK]));     // SA(prefix)
                 C cpre = f.cneg(f.cdbl(pa_jb));
-                if (lenB >= 2)
-                    cpre = f.csub(cpre, f.t_to_c(Sr[(g.sbase(lenB) + i + b + 1) * BLOCK]));
+                if (lenB >= 2) cpre = f.csub(cpre, f.t_to_c(Sr[(ss - N) * BLOCK]));     // SA(suffix)
                 f.template acc2<DS>(acc, csuf, sf, cpre, pb);
                 // momentum part: adj (P_A - P_B) = adj (2 K_{i+b+1} - K_i - K_j);
                 // the K_i + K_j share is added once per range below
                 f.template acc1<D>(acc, f.cdbl(adj), Kt);
-                // four-gluon vertex: prefix [i, i+a], inner [i+a+1, i+b], suffix sf
+                // four-gluon vertex: prefix [i, i+q], inner [i+q+1, i+b], suffix sf
+                int pq = i, dp = N;              // prefix slot, step to the next length
+                int iq = es, di = N - b + 1;     // inner slot (length b-q), step down
                 int q = 0;
 #pragma unroll 1
                 for (; q + 3 < b; q += 4) {
                     T pa0[DS], pa1[DS], pa2[DS], pa3[DS], in0[DS], in1[DS], in2[DS], in3[DS];
-                    IO::template load<DS>(jvec(q + 1, i), pa0);
-                    IO::template load<DS>(jvec(q + 2, i), pa1);
-                    IO::template load<DS>(jvec(q + 3, i), pa2);
-                    IO::template load<DS>(jvec(q + 4, i), pa3);
-                    IO::template load<DS>(jvec(b - q, i + q + 1), in0);
-                    IO::template load<DS>(jvec(b - q - 1, i + q + 2), in1);
-                    IO::template load<DS>(jvec(b - q - 2, i + q + 3), in2);
-                    IO::template load<DS>(jvec(b - q - 3, i + q + 4), in3);
+                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa0);
+                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in0);
+                    pq += dp; iq -= di;
+                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa1);
+                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in1);
+                    pq += dp - 1; iq -= di + 1;
+                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa2);
+                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in2);
+                    pq += dp - 2; iq -= di + 2;
+                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa3);
+                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in3);
+                    pq += dp - 3; iq -= di + 3;
+                    dp -= 4; di += 4;
                     const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
                     const C g1 = f.cdbl(f.template dot<DS, METRIC>(pa1, sf));
                     const C g2 = f.cdbl(f.template dot<DS, METRIC>(pa2, sf));
@@ -288,21 +299,27 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
 #pragma unroll 1
                 for (; q + 1 < b; q += 2) {
                     T pa0[DS], pa1[DS], in0[DS], in1[DS];
-                    IO::template load<DS>(jvec(q + 1, i), pa0);
-                    IO::template load<DS>(jvec(q + 2, i), pa1);
-                    IO::template load<DS>(jvec(b - q, i + q + 1), in0);
-                    IO::template load<DS>(jvec(b - q - 1, i + q + 2), in1);
+                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa0);
+                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in0);
+                    pq += dp; iq -= di;
+                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa1);
+                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in1);
+                    pq += dp - 1; iq -= di + 1;
+                    dp -= 2; di += 2;
                     const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
                     const C g1 = f.cdbl(f.template dot<DS, METRIC>(pa1, sf));
                     f.template acc2<DS>(acc, g0, in0, g1, in1);
                 }
                 if (q < b) {
                     T pa0[DS], in0[DS];
-                    IO::template load<DS>(jvec(q + 1, i), pa0);
-                    IO::template load<DS>(jvec(b - q, i + q + 1), in0);
+                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa0);
+                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in0);
                     const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
                     f.template acc1<DS>(acc, g0, in0);
                 }
+                ps += N - b;                     // prefix length b+1 -> b+2
+                ss -= N - lenB + 1;              // suffix length lenB -> lenB-1
+                es += N - b + 1;                 // inner slots ending at i+b+1
             }
             {
                 T KiKj[D];
