@@ -244,6 +244,11 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
             int ps = i;                          // slot of the prefix [i, i+b]      (length b+1)
             int ss = g.jbase(m - 1) + i + 1;     // slot of the suffix [i+b+1, j]    (length m-1-b)
             int es = i - N;                      // first inner slot [i+1, i+b]: jbase(b) + i + 1
+            // momentum terms 2 adj_b K_{i+b+1} of consecutive splits are
+            // accumulated in pairs (one reduction per pair)
+            C mom_c = f.czero();
+            T mom_v[D];
+            bool mom_pending = false;
 #pragma unroll 1
             for (int b = 0; b < m - 1; ++b) {
                 const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
@@ -268,7 +273,15 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
                 f.template acc2<DS>(acc, csuf, sf, cpre, pb);
                 // momentum part: adj (P_A - P_B) = adj (2 K_{i+b+1} - K_i - K_j);
                 // the K_i + K_j share is added once per range below
-                f.template acc1<D>(acc, f.cdbl(adj), Kt);
+                if (mom_pending) {
+                    f.template acc2<D>(acc, mom_c, mom_v, f.cdbl(adj), Kt);
+                    mom_pending = false;
+                } else {
+                    mom_c = f.cdbl(adj);
+#pragma unroll
+                    for (int mu = 0; mu < D; ++mu) mom_v[mu] = Kt[mu];
+                    mom_pending = true;
+                }
                 // four-gluon vertex: prefix [i, i+q], inner [i+q+1, i+b], suffix sf
                 int pq = i, dp = N;              // prefix slot, step to the next length
                 int iq = es, di = N - b + 1;     // inner slot (length b-q), step down
@@ -325,7 +338,8 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
                 T KiKj[D];
 #pragma unroll
                 for (int mu = 0; mu < D; ++mu) KiKj[mu] = f.tadd(Ki[mu], Kj[mu]);
-                f.template acc1<D>(acc, f.cneg(sa), KiKj);     // - SA(i,j) (K_i + K_j)
+                if (mom_pending) f.template acc2<D>(acc, mom_c, mom_v, f.cneg(sa), KiKj);
+                else f.template acc1<D>(acc, f.cneg(sa), KiKj);     // - SA(i,j) (K_i + K_j)
             }
             if (m < N) {
                 const int sidx = g.sbase(m) + i;
