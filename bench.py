@@ -70,6 +70,35 @@ def kernel_mults(n, d, Ds):
     return tot
 
 
+def kernel_fp64_ops(n, d, Ds, real_k):
+    """FP64-pipe instructions (FMA, add and multiply each count one) the
+    complex kernel issues per amplitude in its regrouped form, a model count
+    from the kernel's structure.  real_k: momenta real (two FMAs per momentum
+    component in P.J and in the momentum term instead of four)."""
+    N = n - 1
+    kc = 1 if real_k else 2                    # adds per momentum component
+    km = 2 if real_k else 4                    # FMAs per momentum-current component
+    tot = 0
+    for m in range(2, N + 1):
+        ranges = N - m + 1
+        per = (m - 1) * 2 * d * kc               # P_A, P_B
+        per += (m - 1) * 4 * Ds                  # adjacent dots
+        per += (m - 1) * 2 * d * km              # P_A.J_B and P_B.J_A
+        per += (m - 1) * (2 + 2 + 4 + 2)         # coefficient algebra (SA, doubling)
+        per += (m - 1) * 8 * Ds                  # prefix and suffix scalar-vector products
+        per += (m - 1) * d * km                  # momentum term
+        per += (m - 1) * (m - 2) // 2 * (8 * Ds + 2)   # gap dots and inner products
+        per += d * kc + d * km                   # K_i + K_j and -SA (K_i + K_j)
+        if m < N:
+            per += Ds * (2 if real_k else 4)     # J = R / P^2
+            per += d * kc + d * (1 if real_k else 4)   # P^2
+            per += 8 if real_k else 12           # reciprocal (Newton steps), complex scaling
+        tot += ranges * per
+    tot += 4 * Ds                                # final contraction
+    tot += N * d * kc                            # prefix sums of the momenta
+    return tot
+
+
 KERNEL_SOURCES = ("paper_2502_07060_gb300/csrc/bg_compact.cuh", "paper_2502_07060_gb300/csrc/bg_field.cuh")
 
 
@@ -263,14 +292,19 @@ def run_field(field, E, steps, warmup, rank, dist, device, seed, e2e=True):
         hk = torch.from_numpy(k.view(np.int32))
         he = torch.from_numpy(e.view(np.int32))
     else:
+        # physical points: real momenta (stored with zero imaginary part)
         k, e = G.c64_batch(seed, E, N_LEG, D, DS, 0)
-        plan = bg.Plan(N_LEG, D, DS, bg.FIELD_C64, 0, bg.MOSTLY_MINUS)
-        hk = torch.from_numpy(k)
+        if field == "c64":
+            plan = bg.Plan(N_LEG, D, DS, bg.FIELD_C64_REAL, 0, bg.MOSTLY_MINUS)
+            hk = torch.from_numpy(np.ascontiguousarray(k.real))
+        else:                                   # "c64c": the general complex-momentum plan
+            plan = bg.Plan(N_LEG, D, DS, bg.FIELD_C64, 0, bg.MOSTLY_MINUS)
+            hk = torch.from_numpy(k)
         he = torch.from_numpy(e)
     del k, e
     dk = hk.to(device)
     de = he.to(device)
-    out = torch.empty(E, dtype=dk.dtype, device=device)
+    out = torch.empty(E, dtype=de.dtype, device=device)
     st = torch.empty(E, dtype=torch.uint8, device=device)
     ws = plan.workspace(E, device)
     stream = torch.cuda.current_stream(device)
@@ -295,7 +329,7 @@ def run_field(field, E, steps, warmup, rank, dist, device, seed, e2e=True):
     # chunks whose copies overlap the kernels
     pk = hk.pin_memory()
     pe = he.pin_memory()
-    hout = torch.empty(E, dtype=dk.dtype).pin_memory()
+    hout = torch.empty(E, dtype=de.dtype).pin_memory()
     hst = torch.empty(E, dtype=torch.uint8).pin_memory()
     del dk, de, out, st, ws
     torch.cuda.empty_cache()
@@ -499,7 +533,9 @@ def main():
     ap.add_argument("--log2-points", type=int, default=22)
     ap.add_argument("--log2-points-c64", type=int, default=22)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fields", default="fp,c64", help="comma list of fp, c64")
+    ap.add_argument("--fields", default="fp,c64,c64c",
+                    help="comma list of fp, c64 (real momenta, the physical points), c64c (the same "
+                         "points through the complex-momentum plan)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--workload", choices=["metric", "mixed", "serve"], default="metric",
                     help="metric: n=8 d=6 headline line; mixed: uneven-batch comparison; "
@@ -570,11 +606,13 @@ def main():
                               "plan": c64["plan"], "clocks": c64["clocks"]}))
         return
     fp = run_field("fp", E, args.steps, args.warmup, rank, dist, device, rank_seed(1000, rank), e2e)
+    c64_steps = max(3, args.steps // 5)
+    c64 = c64c = None
     if "c64" in fields:
-        c64_steps = max(3, args.steps // 5)
         c64 = run_field("c64", Ec, c64_steps, args.warmup, rank, dist, device, rank_seed(2000, rank), e2e)
-    else:
-        c64 = None
+    if "c64c" in fields:
+        c64c = run_field("c64c", Ec, c64_steps, args.warmup, rank, dist, device, rank_seed(2000, rank),
+                         False)
 
     value = job_value(E, world, fp["ms_per_step"])
     tally, _ = literal_tally(N_LEG, D, DS)
@@ -587,6 +625,9 @@ def main():
     achieved = fp["value_per_rank"] * tally
     c64_flops = 6 * tally + 2 * 5348
     peak_fp64 = n_sm * 2 * 2 * sm_max * 1e6
+    peak_fp64_instr = n_sm * 2 * sm_max * 1e6
+    ops_c64 = kernel_fp64_ops(N_LEG, D, DS, True)
+    ops_c64c = kernel_fp64_ops(N_LEG, D, DS, False)
     kops = kernel_mults(N_LEG, D, DS)
     traffic_fp = profiled_traffic("fp_compact_n8_d6.md")
     traffic_c64 = profiled_traffic("c64_compact_n8_d6.md")
@@ -610,14 +651,23 @@ def main():
             "value": world * c64["value_per_rank"], "unit": "amplitudes/s",
             "ms_per_step": c64["ms_per_step"], "points_per_step": Ec, "steps": c64_steps,
             "dtype": "f64",
+            "momenta": "real (physical points; BG_FIELD_C64_REAL plan)",
             "roofline": {"bound": "alu", "achieved": c64["value_per_rank"] * c64_flops,
-                         "peak": peak_fp64, "unit": "FP64 FLOP/s (literal tally)",
+                         "peak": peak_fp64, "unit": "FP64 FLOP/s (literal tally of complex operations)",
                          "frac": c64["value_per_rank"] * c64_flops / peak_fp64,
-                         "frac_kernel_ops": c64["value_per_rank"] * kops * 8 / peak_fp64,
+                         "kernel_fp64_instr_per_unit": ops_c64,
+                         "frac_kernel_ops": c64["value_per_rank"] * ops_c64 / peak_fp64_instr,
                          "traffic": None if traffic_c64 is None else traffic_c64 * Ec / float(1 << 22),
-                         "peak_derivation": f"{n_sm} SMs x 2 DFMA/clk x 2 x {sm_max:.0f} MHz"},
+                         "peak_derivation": f"{n_sm} SMs x 2 DFMA/clk x 2 x {sm_max:.0f} MHz "
+                                            f"(kernel ops: FP64 instructions at 2/clk/SM)"},
             "e2e_value": (world * Ec / (c64["e2e_ms_per_step"] / 1e3)) if e2e else None,
             "clocks": c64["clocks"], "plan": c64["plan"]},
+        "c64_complex_momenta": None if c64c is None else {
+            "value": world * c64c["value_per_rank"], "unit": "amplitudes/s",
+            "ms_per_step": c64c["ms_per_step"], "points_per_step": Ec, "steps": c64_steps,
+            "kernel_fp64_instr_per_unit": ops_c64c,
+            "frac_kernel_ops": c64c["value_per_rank"] * ops_c64c / peak_fp64_instr,
+            "clocks": c64c["clocks"], "plan": c64c["plan"]},
         "e2e": None if not e2e else {
             "value": world * E / (fp["e2e_ms_per_step"] / 1e3), "unit": "amplitudes/s",
             "h2d_bytes_per_step": fp["h2d_bytes"], "d2h_bytes_per_step": fp["d2h_bytes"]},

@@ -60,7 +60,13 @@ typedef enum {
 
 typedef enum {
     BG_FIELD_C64 = 0,         /* complex FP64 (Sec. 3, double precision)        */
-    BG_FIELD_FP = 1           /* prime field F_p, odd prime p < 2^31 (Sec. 3)  */
+    BG_FIELD_FP = 1,          /* prime field F_p, odd prime p < 2^31 (Sec. 3)  */
+    BG_FIELD_C64_REAL = 2     /* complex FP64 with REAL momenta: the physical
+                                 phase-space points of Sec. 3.  Momenta are
+                                 double [E][n][d]; polarisations and amplitudes
+                                 are double2 as for BG_FIELD_C64.  Same values
+                                 as BG_FIELD_C64 on momenta with zero imaginary
+                                 part, with fewer FP64 operations.             */
 } bg_field;
 
 typedef enum {
@@ -79,9 +85,10 @@ typedef struct bg_plan bg_plan;   /* opaque; immutable after creation; may be
  *   n        number of gluons, 4 <= n <= 12
  *   d        momentum dimension, 4 <= d <= 8 (Sec. 2.3)
  *   D_s      polarisation dimension, d <= D_s <= 8 (zero-padding embedding)
- *   field    BG_FIELD_FP or BG_FIELD_C64
+ *   field    BG_FIELD_FP, BG_FIELD_C64 or BG_FIELD_C64_REAL
  *   p        the prime for BG_FIELD_FP (odd prime, 3 <= p < 2^31, checked by
- *            a deterministic Miller-Rabin test); must be 0 for BG_FIELD_C64
+ *            a deterministic Miller-Rabin test); must be 0 for the complex
+ *            fields
  *   metric   BG_METRIC_*
  *   n_states S >= 1: states supplied per leg (eps layout [E][n][S][D_s])
  *   n_assign H >= 1: state assignments evaluated per point (out [E][H]);
@@ -111,9 +118,11 @@ bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes);
  * the results are valid once the stream reaches the call).
  *
  *   E          number of phase-space points, E >= 0 (E == 0: no launch)
- *   momenta    device [E][n][d]: uint32 residues (FP) or double2 (C64)
- *   eps        device [E][n][S][D_s], same element type (S = n_states)
- *   out        device [E][H]: uint32 in [0,p) (FP) or double2 (C64)
+ *   momenta    device [E][n][d]: uint32 residues (FP), double2 (C64) or
+ *              double (C64_REAL)
+ *   eps        device [E][n][S][D_s]: uint32 (FP) or double2 (complex
+ *              fields) (S = n_states)
+ *   out        device [E][H]: uint32 in [0,p) (FP) or double2 (complex)
  *   status     device [E] uint8 or NULL: 0 ok, 1 singular propagator
  *   workspace  device buffer of >= bg_workspace_size(plan, E) bytes, 256-byte
  *              aligned, or NULL when that size is 0; concurrent calls need

@@ -26,6 +26,7 @@ BG_ERR_BUSY = 6
 
 FIELD_C64 = 0
 FIELD_FP = 1
+FIELD_C64_REAL = 2        # complex values, real momenta (float64 [E][n][d])
 MOSTLY_MINUS = 0
 ALTERNATING = 1
 
@@ -196,17 +197,31 @@ class Plan:
 
     @property
     def io_dtype(self):
+        """dtype of polarisations and amplitudes."""
         return torch.int32 if self.field == FIELD_FP else torch.complex128
+
+    @property
+    def momentum_dtype(self):
+        """dtype of the momenta (float64 for FIELD_C64_REAL)."""
+        return torch.float64 if self.field == FIELD_C64_REAL else self.io_dtype
+
+    def _check_types(self, momenta, eps, out):
+        want_k = torch.empty((), dtype=self.momentum_dtype).element_size()
+        want_v = torch.empty((), dtype=self.io_dtype).element_size()
+        if momenta.element_size() != want_k or eps.element_size() != want_v or out.element_size() != want_v:
+            raise TypeError(f"element sizes: momenta {momenta.element_size()} (want {want_k}), "
+                            f"eps {eps.element_size()} and out {out.element_size()} (want {want_v})")
 
     def eval(self, momenta, eps, out=None, status=None, workspace=None, stream=None):
         """Amplitudes of E points.  momenta [E][n][d] and eps [E][n][(S)][D_s]
-        as device tensors (int32/uint32 residues for F_p, complex128 for C64).
+        as device tensors (int32/uint32 residues for F_p, complex128 for C64;
+        momenta float64 for C64_REAL).
         Returns (out [E] or [E][H], status [E] uint8)."""
         E = momenta.shape[0]
         dev = momenta.device
         if out is None:
             shape = (E,) if self.n_assign == 1 else (E, self.n_assign)
-            out = torch.empty(shape, dtype=momenta.dtype, device=dev)
+            out = torch.empty(shape, dtype=eps.dtype, device=dev)
         if status is None:
             status = torch.empty(E, dtype=torch.uint8, device=dev)
         for t in (momenta, eps, out, status):
@@ -215,6 +230,7 @@ class Plan:
         if workspace is None:
             workspace = self.workspace(E, dev)
         ws_bytes = workspace.numel() if workspace is not None else 0
+        self._check_types(momenta, eps, out)
         _check(_lib.bg_eval(self._h, E, _ptr(momenta), _ptr(eps), _ptr(out), _ptr(status),
                             _ptr(workspace), ws_bytes, _stream_handle(stream)))
         return out, status
@@ -233,7 +249,7 @@ class Plan:
         E = momenta.shape[0]
         if out is None:
             shape = (E,) if self.n_assign == 1 else (E, self.n_assign)
-            out = torch.empty(shape, dtype=momenta.dtype, pin_memory=momenta.is_pinned())
+            out = torch.empty(shape, dtype=eps.dtype, pin_memory=momenta.is_pinned())
         if status is None:
             status = torch.empty(E, dtype=torch.uint8, pin_memory=momenta.is_pinned())
         for t in (momenta, eps, out, status):
@@ -245,6 +261,7 @@ class Plan:
             if getattr(self, "_staging", None) is None or self._staging.numel() < need:
                 self._staging = torch.empty(need, dtype=torch.uint8, device="cuda")
             staging = self._staging
+        self._check_types(momenta, eps, out)
         _check(_lib.bg_eval_host(self._h, E, _ptr(momenta), _ptr(eps), _ptr(out), _ptr(status),
                                  chunk, _ptr(staging), staging.numel(), _stream_handle(stream)))
         return out, status
@@ -257,9 +274,10 @@ class Plan:
         dev = momenta.device
         if out is None:
             shape = (E,) if self.n_assign == 1 else (E, self.n_assign)
-            out = torch.empty(shape, dtype=momenta.dtype, device=dev)
+            out = torch.empty(shape, dtype=eps.dtype, device=dev)
         if status is None:
             status = torch.empty(E, dtype=torch.uint8, device=dev)
+        self._check_types(momenta, eps, out)
         _check(_lib.bg_eval_noalloc(self._h, E, _ptr(momenta), _ptr(eps), _ptr(out), _ptr(status),
                                     _stream_handle(stream)))
         return out, status
@@ -273,6 +291,7 @@ class Batch:
         self._keep = groups
         arr = (BgGroup * len(groups))()
         for i, (plan, k, e, out, st) in enumerate(groups):
+            plan._check_types(k, e, out)
             arr[i] = BgGroup(plan.handle.value, k.shape[0], k.data_ptr(), e.data_ptr(), out.data_ptr(),
                              st.data_ptr() if st is not None else 0)
         self._arr = arr
@@ -313,6 +332,7 @@ class Batch:
         (BgBatchConfig, ms per launch)."""
         arr = (BgGroup * len(groups))()
         for i, (plan, k, e, out, st) in enumerate(groups):
+            plan._check_types(k, e, out)
             arr[i] = BgGroup(plan.handle.value, k.shape[0], k.data_ptr(), e.data_ptr(), out.data_ptr(),
                              st.data_ptr() if st is not None else 0)
         need = ctypes.c_size_t()
@@ -340,6 +360,7 @@ class Server:
         self._live = {}
 
     def submit(self, plan, momenta, eps, out, status=None):
+        plan._check_types(momenta, eps, out)
         t = ctypes.c_uint64()
         _check(_lib.bg_serve_submit(self._h, plan.handle, momenta.shape[0], _ptr(momenta), _ptr(eps),
                                     _ptr(out), _ptr(status), ctypes.byref(t)))

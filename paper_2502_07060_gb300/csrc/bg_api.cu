@@ -21,6 +21,8 @@ BG_REG(fp, 5) BG_REG(fp, 6) BG_REG(fp, 7) BG_REG(fp, 8)
 BG_REGC(fp, 4, 4) BG_REGC(fp, 4, 6) BG_REGC(fp, 4, 8) BG_REGC(fp, 6, 6) BG_REGC(fp, 6, 8) BG_REGC(fp, 8, 8)
 BG_REGC(c64, 4, 4) BG_REGC(c64, 4, 6) BG_REGC(c64, 4, 8) BG_REGC(c64, 6, 6) BG_REGC(c64, 6, 8)
 BG_REGC(c64, 8, 8)
+BG_REGC(c64r, 4, 4) BG_REGC(c64r, 4, 6) BG_REGC(c64r, 4, 8) BG_REGC(c64r, 6, 6) BG_REGC(c64r, 6, 8)
+BG_REGC(c64r, 8, 8)
 #undef BG_REGC
 
 namespace {
@@ -49,6 +51,8 @@ const std::vector<bgk::KernelEntry>& registry() {
         BG_ADDC(fp, 4, 4) BG_ADDC(fp, 4, 6) BG_ADDC(fp, 4, 8) BG_ADDC(fp, 6, 6) BG_ADDC(fp, 6, 8)
         BG_ADDC(fp, 8, 8) BG_ADDC(c64, 4, 4) BG_ADDC(c64, 4, 6) BG_ADDC(c64, 4, 8) BG_ADDC(c64, 6, 6)
         BG_ADDC(c64, 6, 8) BG_ADDC(c64, 8, 8)
+        BG_ADDC(c64r, 4, 4) BG_ADDC(c64r, 4, 6) BG_ADDC(c64r, 4, 8) BG_ADDC(c64r, 6, 6)
+        BG_ADDC(c64r, 6, 8) BG_ADDC(c64r, 8, 8)
 #undef BG_ADDC
 #undef BG_ADD
     });
@@ -134,6 +138,10 @@ using bgi::registry;
 using bgi::round_dim;
 using bgi::is_prime_u32;
 using bgi::mulmod64;
+using bgi::value_bytes;
+using bgi::momentum_bytes;
+using bgi::compact_params;
+using bgi::field_name;
 
 extern "C" {
 
@@ -162,7 +170,7 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
     if (n < 4 || n > 12) return fail(BG_ERR_INVALID_ARG, "n = %d outside [4, 12]", n);
     if (d < 4 || d > 8) return fail(BG_ERR_INVALID_ARG, "d = %d outside [4, 8]", d);
     if (D_s < d || D_s > 8) return fail(BG_ERR_INVALID_ARG, "D_s = %d outside [d, 8]", D_s);
-    if (field != BG_FIELD_FP && field != BG_FIELD_C64)
+    if (field != BG_FIELD_FP && field != BG_FIELD_C64 && field != BG_FIELD_C64_REAL)
         return fail(BG_ERR_INVALID_ARG, "unknown field %d", (int)field);
     if (metric != BG_METRIC_MOSTLY_MINUS && metric != BG_METRIC_ALTERNATING)
         return fail(BG_ERR_INVALID_ARG, "unknown metric %d", (int)metric);
@@ -201,7 +209,7 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
     } else {
         const bgk::Geometry geo{n - 1};
         words = geo.words(Dk, DSk);
-        const size_t elem = field == BG_FIELD_FP ? 4 : 16;
+        const size_t elem = value_bytes(field);
         bool want_global = true;
         if (tenv) {
             want_global = strcmp(tenv, "global") == 0;
@@ -215,7 +223,7 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
             if (e.compact && e.field == (int)field && e.D == Dk && e.DS == DSk &&
                 e.metric == (int)metric && e.global_table == want_global)
                 best = &e;
-        if (!best)      // C64 has only the global placement
+        if (!best)      // the complex fields have only the global placement
             for (const auto& e : registry())
                 if (e.compact && e.field == (int)field && e.D == Dk && e.DS == DSk &&
                     e.metric == (int)metric)
@@ -316,7 +324,7 @@ bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
     int w = snprintf(buf, len,
                      "field=%s n=%d d=%d D_s=%d kernel=%s kernel_D=%d kernel_D_s=%d metric=%s "
                      "table=%s block=%d blocks_per_sm=%d smem=%zu words_per_thread=%d elem_bytes=%d",
-                     plan->field == BG_FIELD_FP ? "fp" : "c64", plan->n, plan->d, plan->Ds,
+                     field_name(plan->field), plan->n, plan->d, plan->Ds,
                      e->compact ? "compact" : "unrolled", e->D, e->DS,
                      plan->metric == BG_METRIC_MOSTLY_MINUS ? "mostly_minus" : "alternating",
                      e->global_table ? "global" : "shared", e->block, plan->blocks_per_sm,
@@ -333,9 +341,10 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const voi
     if (E == 0) return BG_OK;
     if (!momenta || !eps || !out) return fail(BG_ERR_INVALID_ARG, "momenta, eps and out must be non-NULL");
     if (E > (int64_t(1) << 40) / plan->H) return fail(BG_ERR_INVALID_ARG, "E too large");
-    const size_t elem = plan->field == BG_FIELD_FP ? 4 : 16;
-    if (((uintptr_t)momenta | (uintptr_t)eps | (uintptr_t)out) % elem)
-        return fail(BG_ERR_INVALID_ARG, "momenta, eps and out must be aligned to %zu bytes", elem);
+    const size_t elem = value_bytes(plan->field), kelem = momentum_bytes(plan->field);
+    if (((uintptr_t)eps | (uintptr_t)out) % elem || (uintptr_t)momenta % kelem)
+        return fail(BG_ERR_INVALID_ARG, "momenta, eps and out must be aligned to their element sizes "
+                    "(%zu, %zu, %zu bytes)", kelem, elem, elem);
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -372,8 +381,7 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const voi
         a.d_in = plan->d; a.ds_in = plan->Ds;
         a.k = momenta; a.eps = eps; a.out = out; a.status = status;
         a.assign = plan->d_assign; a.ws = workspace;
-        const void* fparams = plan->field == BG_FIELD_FP ? (const void*)&plan->fpo : (const void*)&plan->c64o;
-        e->launch(fparams, &a, dim3((unsigned)blocks), plan->smem_bytes, stream);
+        e->launch(compact_params(plan), &a, dim3((unsigned)blocks), plan->smem_bytes, stream);
     } else {
         bgk::LaunchArgs a;
         a.E = E; a.H = plan->H; a.S = plan->S;

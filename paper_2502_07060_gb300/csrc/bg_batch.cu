@@ -30,15 +30,18 @@ constexpr int kTuneC64Caps[] = {0, 3, 2, 1};        // C64 blocks per SM
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// relative cost of one point (field multiplications of the regrouped form)
-double point_cost(int n, int D, int DS, bool fp) {
+// relative cost of one point (field multiplications of the regrouped form;
+// complex points weighted by their FP64 FMAs, the FP64 pipe being far slower
+// per operation than the integer multiply pipe)
+double point_cost(int n, int D, int DS, bg_field field) {
     const int N = n - 1;
     double tot = 0;
+    const double kw = field == BG_FIELD_C64_REAL ? 0.5 : 1.0;    // momentum terms
     for (int m = 2; m <= N; ++m) {
-        const double per = (m - 1) * (3.0 * DS + 3.0 * D) + (m - 1) * (m - 2) * DS;
+        const double per = (m - 1) * (3.0 * DS + 3.0 * kw * D) + (m - 1) * (m - 2) * DS;
         tot += (N - m + 1) * per;
     }
-    return fp ? tot : 8.0 * tot;      // FP64 pipe: far slower per multiplication
+    return field == BG_FIELD_FP ? tot : 8.0 * tot;
 }
 
 struct FieldPart {
@@ -50,7 +53,7 @@ struct FieldPart {
 };
 
 struct Layout {
-    FieldPart part[2];                  // [0] = C64, [1] = F_p
+    FieldPart part[2];                  // [0] = complex (C64, C64_REAL), [1] = F_p
     size_t bytes = 0;
 };
 
@@ -71,7 +74,7 @@ bg_status build_layout(const bg_group* groups, int n_groups, const bg_batch_conf
         const bg_plan* pl = g.plan;
         if (g.E > (int64_t(1) << 40) / pl->H) return bgi::fail(BG_ERR_INVALID_ARG, "group %d too large", gi);
         const int D = bgi::round_dim(pl->d), DS = bgi::round_dim(pl->Ds);
-        order.push_back({gi, point_cost(pl->n, D, DS, pl->field == BG_FIELD_FP) * pl->H});
+        order.push_back({gi, point_cost(pl->n, D, DS, pl->field) * pl->H});
     }
     std::stable_sort(order.begin(), order.end(), [](const Item& a, const Item& b) { return a.cost > b.cost; });
     for (const Item& it : order) {
@@ -92,7 +95,8 @@ bg_status build_layout(const bg_group* groups, int n_groups, const bg_batch_conf
         bgd.args.status = g.status;
         bgd.args.assign = pl->d_assign;
         bgd.args.ws = nullptr;
-        bgd.variant = 2 * bgk::batch_pair_index(D, DS) + (int)pl->metric;
+        bgd.variant = 2 * bgk::batch_pair_index(D, DS) + (int)pl->metric +
+                      (pl->field == BG_FIELD_C64_REAL ? bgk::kBatchVariants : 0);
         bgd.fp = pl->fpo;
         const int gidx = (int)fpart.groups.size();
         fpart.groups.push_back(bgd);

@@ -16,15 +16,17 @@
 namespace bgk {
 
 // (D, D_s) pairs compiled for the batch kernel, and the variant index
-// variant = 2 * pair + metric.
+// variant = 2 * pair + metric, plus kBatchVariants for complex groups with
+// real momenta (run by the complex kernel).
 constexpr int kBatchPairs = 6;
+constexpr int kBatchVariants = 2 * kBatchPairs;
 __host__ __device__ constexpr int batch_pair_index(int D, int DS) {
     return D == 4 ? (DS == 4 ? 0 : DS == 6 ? 1 : 2) : D == 6 ? (DS == 6 ? 3 : 4) : 5;
 }
 
 struct BatchGroup {
     CompactArgs args;       // n, E, H, S, dims, device buffers (ws unused)
-    int variant;            // 2 * batch_pair_index(D, D_s) + metric
+    int variant;            // 2 * batch_pair_index(D, D_s) + metric (+ kBatchVariants)
     FpOps fp;               // Montgomery constants (F_p groups)
 };
 
@@ -51,7 +53,7 @@ template <>
 __device__ __forceinline__ C64Ops batch_field<C64Ops>(const BatchGroup&) { return C64Ops{}; }
 
 template <class F, int BLOCK>
-__device__ __forceinline__ void batch_item(const F& f, const CompactArgs& a, int variant,
+__device__ __forceinline__ void batch_dims(const F& f, const CompactArgs& a, int variant,
                                            typename F::T* tab, int64_t u) {
     switch (variant) {
         case 0: bg_point<F, 4, 4, 0, BLOCK>(f, a, tab, u); break;
@@ -67,6 +69,18 @@ __device__ __forceinline__ void batch_item(const F& f, const CompactArgs& a, int
         case 10: bg_point<F, 8, 8, 0, BLOCK>(f, a, tab, u); break;
         default: bg_point<F, 8, 8, 1, BLOCK>(f, a, tab, u); break;
     }
+}
+
+template <class F, int BLOCK>
+__device__ __forceinline__ void batch_item(const F& f, const CompactArgs& a, int variant,
+                                           typename F::T* tab, int64_t u) {
+    if constexpr (!F::kIsFp) {
+        if (variant >= kBatchVariants) {         // same table element type (double2)
+            batch_dims<C64ROps, BLOCK>(C64ROps{}, a, variant - kBatchVariants, tab, u);
+            return;
+        }
+    }
+    batch_dims<F, BLOCK>(f, a, variant, tab, u);
 }
 
 template <class F, int BLOCK>

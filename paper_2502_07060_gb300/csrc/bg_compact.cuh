@@ -127,6 +127,8 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
     using C = typename F::C;
     using Acc = typename F::A;
     using io_t = typename F::io_t;
+    using TK = typename F::TK;               // momentum component (may be real)
+    using kio_t = typename F::kio_t;
 
     const int NLEG = a.n;
     const Geometry g{NLEG - 1};
@@ -134,14 +136,15 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
     const int OFF_K = g.off_k(DS), OFF_SA = g.off_sa(D, DS), OFF_INV = g.off_inv(D, DS);
     constexpr bool VEC = F::kIsFp;
     using IO = TableIO<T, VEC, BLOCK>;
+    using KIO = TableIO<TK, VEC, BLOCK>;
     const int t = threadIdx.x;
     T* Jr = tab + (VEC ? t * DS : t);                              // currents
-    T* Kr = tab + OFF_K * BLOCK + (VEC ? t * D : t);               // prefix sums
+    TK* Kr = reinterpret_cast<TK*>(tab + OFF_K * BLOCK) + (VEC ? t * D : t);   // prefix sums
     T* Sr = tab + OFF_SA * BLOCK + t;                              // SA per internal range
     T* Ir = tab + OFF_INV * BLOCK + t;                             // 1/P^2 per internal range
     auto jvec = [&](int len, int start) { return IO::template vec<DS>(Jr, g.jbase(len) + start); };
-    auto kvec = [&](int i) { return IO::template vec<D>(Kr, i); };
-    const io_t* kin = static_cast<const io_t*>(a.k);
+    auto kvec = [&](int i) { return KIO::template vec<D>(Kr, i); };
+    const kio_t* kin = static_cast<const kio_t*>(a.k);
     const io_t* ein = static_cast<const io_t*>(a.eps);
     io_t* out = static_cast<io_t*>(a.out);
 
@@ -154,17 +157,17 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
     // a1: momenta -> prefix sums K_0 = 0, K_{l+1} = K_l + k_l (leg n unused:
     // P_{1,n-1} = -k_n never enters); polarisations -> currents of length 1.
     {
-        const io_t* kp = kin + e * NLEG * a.d_in;
-        T Kacc[D];
+        const kio_t* kp = kin + e * NLEG * a.d_in;
+        TK Kacc[D];
 #pragma unroll
-        for (int mu = 0; mu < D; ++mu) Kacc[mu] = f.zero();
-        IO::template store<D>(kvec(0), Kacc);
+        for (int mu = 0; mu < D; ++mu) Kacc[mu] = f.kzero();
+        KIO::template store<D>(kvec(0), Kacc);
 #pragma unroll 1
         for (int l = 0; l < N; ++l) {
 #pragma unroll
             for (int mu = 0; mu < D; ++mu)
-                if (mu < a.d_in) Kacc[mu] = f.tadd(Kacc[mu], f.from_io(kp[l * a.d_in + mu]));
-            IO::template store<D>(kvec(l + 1), Kacc);
+                if (mu < a.d_in) Kacc[mu] = f.kadd(Kacc[mu], f.kfrom_io(kp[l * a.d_in + mu]));
+            KIO::template store<D>(kvec(l + 1), Kacc);
         }
     }
     T eL[DS];
@@ -189,12 +192,12 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
     for (int m = 2; m < N; ++m) {
 #pragma unroll 1
         for (int i = 0; i + m - 1 < N; ++i) {
-            T Ka[D], Kb[D], P[D];
-            IO::template load<D>(kvec(i), Ka);
-            IO::template load<D>(kvec(i + m), Kb);
+            TK Ka[D], Kb[D], P[D];
+            KIO::template load<D>(kvec(i), Ka);
+            KIO::template load<D>(kvec(i + m), Kb);
 #pragma unroll
-            for (int mu = 0; mu < D; ++mu) P[mu] = f.tsub(Kb[mu], Ka[mu]);
-            X[(g.sbase(m) + i) * BLOCK] = f.inv_input(f.template dot<D, METRIC>(P, P));
+            for (int mu = 0; mu < D; ++mu) P[mu] = f.ksub(Kb[mu], Ka[mu]);
+            X[(g.sbase(m) + i) * BLOCK] = f.inv_input(f.template kkdot<D, METRIC>(P, P));
         }
     }
     // a3: all inverses.  F_p: Montgomery simultaneous inversion (prefix
@@ -235,9 +238,9 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
     for (int m = 2; m <= N; ++m) {
 #pragma unroll 1
         for (int i = 0; i + m - 1 < N; ++i) {
-            T Ki[D], Kj[D];
-            IO::template load<D>(kvec(i), Ki);
-            IO::template load<D>(kvec(i + m), Kj);
+            TK Ki[D], Kj[D];
+            KIO::template load<D>(kvec(i), Ki);
+            KIO::template load<D>(kvec(i + m), Kj);
             Acc acc[DS];
             f.template acc_zero<DS>(acc);
             C sa = f.czero();
@@ -247,24 +250,25 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
             // momentum terms 2 adj_b K_{i+b+1} of consecutive splits are
             // accumulated in pairs (one reduction per pair)
             C mom_c = f.czero();
-            T mom_v[D];
+            TK mom_v[D];
             bool mom_pending = false;
 #pragma unroll 1
             for (int b = 0; b < m - 1; ++b) {
                 const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
-                T pb[DS], sf[DS], Kt[D], PA[D], PB[D];
+                T pb[DS], sf[DS];
+                TK Kt[D], PA[D], PB[D];
                 IO::template load<DS>(IO::template vec<DS>(Jr, ps), pb);
                 IO::template load<DS>(IO::template vec<DS>(Jr, ss), sf);
-                IO::template load<D>(kvec(i + b + 1), Kt);
+                KIO::template load<D>(kvec(i + b + 1), Kt);
 #pragma unroll
                 for (int mu = 0; mu < D; ++mu) {
-                    PA[mu] = f.tsub(Kt[mu], Ki[mu]);
-                    PB[mu] = f.tsub(Kj[mu], Kt[mu]);
+                    PA[mu] = f.ksub(Kt[mu], Ki[mu]);
+                    PB[mu] = f.ksub(Kj[mu], Kt[mu]);
                 }
                 // three-gluon vertex of the split at s = i + b
                 const C adj = f.template dot<DS, METRIC>(pb, sf);
-                const C pa_jb = f.template dot<D, METRIC>(PA, sf);
-                const C pb_ja = f.template dot<D, METRIC>(PB, pb);
+                const C pa_jb = f.template kdot<D, METRIC>(PA, sf);
+                const C pb_ja = f.template kdot<D, METRIC>(PB, pb);
                 sa = f.cadd(sa, adj);
                 C csuf = f.cdbl(pb_ja);
                 if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(Sr[(ps - N) * BLOCK]));     // SA(prefix)
@@ -274,7 +278,7 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
                 // momentum part: adj (P_A - P_B) = adj (2 K_{i+b+1} - K_i - K_j);
                 // the K_i + K_j share is added once per range below
                 if (mom_pending) {
-                    f.template acc2<D>(acc, mom_c, mom_v, f.cdbl(adj), Kt);
+                    f.template kacc2<D>(acc, mom_c, mom_v, f.cdbl(adj), Kt);
                     mom_pending = false;
                 } else {
                     mom_c = f.cdbl(adj);
@@ -286,8 +290,10 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
                 int pq = i, dp = N;              // prefix slot, step to the next length
                 int iq = es, di = N - b + 1;     // inner slot (length b-q), step down
                 int q = 0;
+                // F_p: four gaps per iteration (independent loads and dots in
+                // flight); C64 is bound by the FP64 pipe and takes pairs only
 #pragma unroll 1
-                for (; q + 3 < b; q += 4) {
+                for (; F::kIsFp && q + 3 < b; q += 4) {
                     T pa0[DS], pa1[DS], pa2[DS], pa3[DS], in0[DS], in1[DS], in2[DS], in3[DS];
                     IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa0);
                     IO::template load<DS>(IO::template vec<DS>(Jr, iq), in0);
@@ -335,11 +341,11 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
                 es += N - b + 1;                 // inner slots ending at i+b+1
             }
             {
-                T KiKj[D];
+                TK KiKj[D];
 #pragma unroll
-                for (int mu = 0; mu < D; ++mu) KiKj[mu] = f.tadd(Ki[mu], Kj[mu]);
-                if (mom_pending) f.template acc2<D>(acc, mom_c, mom_v, f.cneg(sa), KiKj);
-                else f.template acc1<D>(acc, f.cneg(sa), KiKj);     // - SA(i,j) (K_i + K_j)
+                for (int mu = 0; mu < D; ++mu) KiKj[mu] = f.kadd(Ki[mu], Kj[mu]);
+                if (mom_pending) f.template kacc2<D>(acc, mom_c, mom_v, f.cneg(sa), KiKj);
+                else f.template kacc1<D>(acc, f.cneg(sa), KiKj);     // - SA(i,j) (K_i + K_j)
             }
             if (m < N) {
                 const int sidx = g.sbase(m) + i;

@@ -1,3 +1,3 @@
 // Compact kernel instances: field c64, D = 4, D_s = 4 (both metrics).
 #include "bg_instances.cuh"
-BG_DEFINE_COMPACT(4, 4, false, c64)
+BG_DEFINE_COMPACT(4, 4, C64Ops, c64)

@@ -1,3 +1,3 @@
 // Compact kernel instances: field c64, D = 6, D_s = 6 (both metrics).
 #include "bg_instances.cuh"
-BG_DEFINE_COMPACT(6, 6, false, c64)
+BG_DEFINE_COMPACT(6, 6, C64Ops, c64)

@@ -1,3 +1,3 @@
 // Compact kernel instances: field c64, D = 8, D_s = 8 (both metrics).
 #include "bg_instances.cuh"
-BG_DEFINE_COMPACT(8, 8, false, c64)
+BG_DEFINE_COMPACT(8, 8, C64Ops, c64)

@@ -1,0 +1,3 @@
+// Compact kernel instances: field c64 with real momenta, D = 6, D_s = 8 (both metrics).
+#include "bg_instances.cuh"
+BG_DEFINE_COMPACT(6, 8, C64ROps, c64r)

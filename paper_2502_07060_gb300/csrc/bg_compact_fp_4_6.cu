@@ -1,3 +1,3 @@
 // Compact kernel instances: field fp, D = 4, D_s = 6 (both metrics).
 #include "bg_instances.cuh"
-BG_DEFINE_COMPACT(4, 6, true, fp)
+BG_DEFINE_COMPACT(4, 6, FpOps, fp)

@@ -1,3 +1,3 @@
 // Compact kernel instances: field fp, D = 8, D_s = 8 (both metrics).
 #include "bg_instances.cuh"
-BG_DEFINE_COMPACT(8, 8, true, fp)
+BG_DEFINE_COMPACT(8, 8, FpOps, fp)

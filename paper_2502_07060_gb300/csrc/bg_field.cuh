@@ -45,7 +45,10 @@ struct FpOps {
     using C = uint32_t;
     using A = uint64_t;
     using io_t = uint32_t;
+    using TK = uint32_t;            // momentum component
+    using kio_t = uint32_t;         // momentum input element
     static constexpr bool kIsFp = true;
+    static constexpr int kField = 1;
 
     uint32_t p, pinv, r2, r3, one, pm2;   // r2 = R^2, r3 = R^3, one = R (mod p)
 
@@ -139,6 +142,22 @@ struct FpOps {
         return r;
     }
     __device__ __forceinline__ T inv_store(T inv1) const { return mmul(inv1, r3); }   // level 3
+
+    // momentum operations: momenta are field elements like the currents
+    __device__ __forceinline__ TK kzero() const { return 0u; }
+    __device__ __forceinline__ TK kfrom_io(kio_t x) const { return from_io(x); }
+    __device__ __forceinline__ TK kadd(TK a, TK b) const { return tadd(a, b); }
+    __device__ __forceinline__ TK ksub(TK a, TK b) const { return tsub(a, b); }
+    template <int D, int METRIC>
+    __device__ __forceinline__ C kdot(const TK* a, const T* b) const { return dot<D, METRIC>(a, b); }
+    template <int D, int METRIC>
+    __device__ __forceinline__ C kkdot(const TK* a, const TK* b) const { return dot<D, METRIC>(a, b); }
+    template <int K>
+    __device__ __forceinline__ void kacc1(A* acc, C c, const TK* v) const { acc1<K>(acc, c, v); }
+    template <int K>
+    __device__ __forceinline__ void kacc2(A* acc, C c1, const TK* v1, C c2, const TK* v2) const {
+        acc2<K>(acc, c1, v1, c2, v2);
+    }
     __device__ __forceinline__ bool is_zero(T x) const { return x == 0u; }
     __device__ __forceinline__ io_t zero_io() const { return 0u; }
 };
@@ -148,7 +167,10 @@ struct C64Ops {
     using C = double2;
     using A = double2;
     using io_t = double2;
+    using TK = double2;
+    using kio_t = double2;
     static constexpr bool kIsFp = false;
+    static constexpr int kField = 0;
 
     __device__ __forceinline__ T zero() const { return make_double2(0.0, 0.0); }
     __device__ __forceinline__ T from_io(io_t x) const { return x; }
@@ -223,6 +245,78 @@ struct C64Ops {
     __device__ __forceinline__ T inv_store(T v) const { return v; }
     __device__ __forceinline__ bool is_zero(T z) const { return z.x == 0.0 && z.y == 0.0; }
     __device__ __forceinline__ io_t zero_io() const { return make_double2(0.0, 0.0); }
+
+    // complex momenta
+    __device__ __forceinline__ TK kzero() const { return zero(); }
+    __device__ __forceinline__ TK kfrom_io(kio_t x) const { return x; }
+    __device__ __forceinline__ TK kadd(TK a, TK b) const { return tadd(a, b); }
+    __device__ __forceinline__ TK ksub(TK a, TK b) const { return tsub(a, b); }
+    template <int D, int METRIC>
+    __device__ __forceinline__ C kdot(const TK* a, const T* b) const { return dot<D, METRIC>(a, b); }
+    template <int D, int METRIC>
+    __device__ __forceinline__ C kkdot(const TK* a, const TK* b) const { return dot<D, METRIC>(a, b); }
+    template <int K>
+    __device__ __forceinline__ void kacc1(A* acc, C c, const TK* v) const { acc1<K>(acc, c, v); }
+    template <int K>
+    __device__ __forceinline__ void kacc2(A* acc, C c1, const TK* v1, C c2, const TK* v2) const {
+        acc2<K>(acc, c1, v1, c2, v2);
+    }
+};
+
+// Complex FP64 with real momenta (physical phase-space points, Sec. 3): the
+// currents and polarisations stay complex, momenta are real doubles.  A
+// momentum-current contraction is then two FMAs per component (real times
+// complex) instead of four, P^2 is real and so is its inverse, and the
+// momentum term of the three-gluon vertex accumulates with two FMAs per
+// component.
+struct C64ROps : C64Ops {
+    using TK = double;
+    using kio_t = double;
+    static constexpr int kField = 2;
+
+    __device__ __forceinline__ TK kzero() const { return 0.0; }
+    __device__ __forceinline__ TK kfrom_io(kio_t x) const { return x; }
+    __device__ __forceinline__ TK kadd(TK a, TK b) const { return a + b; }
+    __device__ __forceinline__ TK ksub(TK a, TK b) const { return a - b; }
+    template <int D, int METRIC>
+    __device__ __forceinline__ C kdot(const TK* a, const T* b) const {
+        double re = 0.0, im = 0.0;
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) {
+            const double s = msign<METRIC>(mu) > 0 ? a[mu] : -a[mu];
+            re = fma(s, b[mu].x, re);
+            im = fma(s, b[mu].y, im);
+        }
+        return make_double2(re, im);
+    }
+    template <int D, int METRIC>
+    __device__ __forceinline__ C kkdot(const TK* a, const TK* b) const {
+        double re = 0.0;
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) re = fma(msign<METRIC>(mu) > 0 ? a[mu] : -a[mu], b[mu], re);
+        return make_double2(re, 0.0);
+    }
+    template <int K>
+    __device__ __forceinline__ void kacc1(A* acc, C c, const TK* v) const {
+#pragma unroll
+        for (int mu = 0; mu < K; ++mu) {
+            acc[mu].x = fma(c.x, v[mu], acc[mu].x);
+            acc[mu].y = fma(c.y, v[mu], acc[mu].y);
+        }
+    }
+    template <int K>
+    __device__ __forceinline__ void kacc2(A* acc, C c1, const TK* v1, C c2, const TK* v2) const {
+        kacc1<K>(acc, c1, v1);
+        kacc1<K>(acc, c2, v2);
+    }
+    // P^2 is real: its inverse is the correctly rounded reciprocal, and the
+    // current is R scaled by it
+    __device__ __forceinline__ T inv_scalar(T z) const { return make_double2(__drcp_rn(z.x), 0.0); }
+    template <int K>
+    __device__ __forceinline__ void finish(const A* acc, T inv, T* out) const {
+#pragma unroll
+        for (int mu = 0; mu < K; ++mu) out[mu] = make_double2(acc[mu].x * inv.x, acc[mu].y * inv.x);
+    }
 };
 
 }  // namespace bgk

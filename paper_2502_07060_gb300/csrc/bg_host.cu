@@ -60,9 +60,9 @@ struct Slot {
 };
 
 Slot slot_sizes(const bg_plan* pl, int64_t chunk) {
-    const size_t elem = pl->field == BG_FIELD_FP ? 4 : 16;
+    const size_t elem = bgi::value_bytes(pl->field);
     Slot s;
-    s.k = up256((size_t)chunk * pl->n * pl->d * elem);
+    s.k = up256((size_t)chunk * pl->n * pl->d * bgi::momentum_bytes(pl->field));
     s.eps = up256((size_t)chunk * pl->n * pl->S * pl->Ds * elem);
     s.out = up256((size_t)chunk * pl->H * elem);
     s.status = up256((size_t)chunk);
@@ -112,8 +112,8 @@ extern "C" bg_status bg_eval_host(const bg_plan* plan, int64_t E, const void* mo
     unsigned char* slot_base[2] = {base, base + sz.total()};
     void* ws = base + 2 * sz.total();
     size_t ws_bytes = staging_bytes - 2 * sz.total();
-    const size_t elem = plan->field == BG_FIELD_FP ? 4 : 16;
-    const size_t k_pt = (size_t)plan->n * plan->d * elem;
+    const size_t elem = bgi::value_bytes(plan->field);
+    const size_t k_pt = (size_t)plan->n * plan->d * bgi::momentum_bytes(plan->field);
     const size_t e_pt = (size_t)plan->n * plan->S * plan->Ds * elem;
     const size_t o_pt = (size_t)plan->H * elem;
 

@@ -16,7 +16,7 @@
 namespace bgk {
 
 struct KernelEntry {
-    int field;          // 0 = C64, 1 = F_p (bg_field)
+    int field;          // bg_field: 0 = C64, 1 = F_p, 2 = C64 with real momenta
     int n;              // gluons; 0 for the compact kernel (any n)
     int D, DS, metric;
     bool global_table;  // table in global scratch (true) or shared memory
@@ -63,7 +63,7 @@ void launch_compact(const void* fp, const void* args, dim3 grid, size_t smem, cu
 template <class F, int D, int DS, int M, int B, bool G>
 KernelEntry make_compact() {
     KernelEntry e;
-    e.field = F::kIsFp ? 1 : 0;
+    e.field = F::kField;
     e.n = 0;
     e.D = D;
     e.DS = DS;
@@ -103,25 +103,26 @@ void register_unrolled(std::vector<KernelEntry>& v) {
 }
 
 // Compact kernels: every (D, D_s) pair with D <= D_s in {4, 6, 8}, both
-// metrics; F_p with shared or global table, C64 with global table.
+// metrics; F_p with shared or global table, the complex fields (complex or
+// real momenta) with global table.
 constexpr int kBlockFpCompactSmem = 64;
 constexpr int kBlockFpCompactGlobal = 128;
 constexpr int kBlockC64Compact = 64;
 
-template <int D, int DS, int M, bool FP>
+template <class F, int D, int DS, int M>
 void add_compact_dims(std::vector<KernelEntry>& v) {
-    if constexpr (FP) {
-        v.push_back(make_compact<FpOps, D, DS, M, kBlockFpCompactSmem, false>());
-        v.push_back(make_compact<FpOps, D, DS, M, kBlockFpCompactGlobal, true>());
+    if constexpr (F::kIsFp) {
+        v.push_back(make_compact<F, D, DS, M, kBlockFpCompactSmem, false>());
+        v.push_back(make_compact<F, D, DS, M, kBlockFpCompactGlobal, true>());
     } else {
-        v.push_back(make_compact<C64Ops, D, DS, M, kBlockC64Compact, true>());
+        v.push_back(make_compact<F, D, DS, M, kBlockC64Compact, true>());
     }
 }
 
-template <int D, int DS, bool FP>
+template <class F, int D, int DS>
 void register_compact(std::vector<KernelEntry>& v) {
-    add_compact_dims<D, DS, 0, FP>(v);
-    add_compact_dims<D, DS, 1, FP>(v);
+    add_compact_dims<F, D, DS, 0>(v);
+    add_compact_dims<F, D, DS, 1>(v);
 }
 
 }  // namespace bgk
@@ -131,7 +132,7 @@ void register_compact(std::vector<KernelEntry>& v) {
         bgk::register_unrolled<NLEG>(v);                                      \
     }
 
-#define BG_DEFINE_COMPACT(D, DS, FP, TAG)                                     \
+#define BG_DEFINE_COMPACT(D, DS, OPS, TAG)                                    \
     void bg_register_compact_##TAG##_##D##_##DS(std::vector<bgk::KernelEntry>& v) { \
-        bgk::register_compact<D, DS, FP>(v);                                  \
+        bgk::register_compact<bgk::OPS, D, DS>(v);                            \
     }

@@ -24,6 +24,7 @@ struct bg_plan {
     bgk::FieldC64 c64{};
     bgk::FpOps fpo{};                 // compact kernels
     bgk::C64Ops c64o{};
+    bgk::C64ROps c64ro{};
     int sm_count = 0;
     int blocks_per_sm = 0;
     size_t smem_bytes = 0;            // dynamic shared memory per block
@@ -35,4 +36,19 @@ bg_status fail(bg_status s, const char* fmt, ...);
 bg_status check_device_ptr(const void* ptr, const char* what, int device);
 int round_dim(int x);
 bg_status ensure_smem_limit(const void* func, int device, size_t bytes);
+
+// bytes of one polarisation / amplitude element (uint32 residue or double2)
+inline size_t value_bytes(bg_field f) { return f == BG_FIELD_FP ? 4 : 16; }
+// bytes of one momentum component (uint32, double2, or double for real momenta)
+inline size_t momentum_bytes(bg_field f) {
+    return f == BG_FIELD_FP ? 4 : f == BG_FIELD_C64_REAL ? 8 : 16;
+}
+// field constants passed to the compact kernel of the plan's field
+inline const void* compact_params(const bg_plan* pl) {
+    return pl->field == BG_FIELD_FP ? (const void*)&pl->fpo
+         : pl->field == BG_FIELD_C64_REAL ? (const void*)&pl->c64ro : (const void*)&pl->c64o;
+}
+inline const char* field_name(bg_field f) {
+    return f == BG_FIELD_FP ? "fp" : f == BG_FIELD_C64_REAL ? "c64_real" : "c64";
+}
 }  // namespace bgi

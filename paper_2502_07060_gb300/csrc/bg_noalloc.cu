@@ -66,9 +66,10 @@ extern "C" bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void*
         return bgi::fail(BG_ERR_INVALID_ARG, "momenta, eps and out must be non-NULL");
     if (E > (int64_t(1) << 40) / plan->H)
         return bgi::fail(BG_ERR_INVALID_ARG, "E * n_assign exceeds the maximum of 2^40 work items");
-    const size_t elem = plan->field == BG_FIELD_FP ? 4 : 16;
-    if (((uintptr_t)momenta | (uintptr_t)eps | (uintptr_t)out) % elem)
-        return bgi::fail(BG_ERR_INVALID_ARG, "momenta, eps and out must be aligned to %zu bytes", elem);
+    const size_t elem = bgi::value_bytes(plan->field), kelem = bgi::momentum_bytes(plan->field);
+    if (((uintptr_t)eps | (uintptr_t)out) % elem || (uintptr_t)momenta % kelem)
+        return bgi::fail(BG_ERR_INVALID_ARG, "momenta, eps and out must be aligned to their element sizes "
+                         "(%zu, %zu, %zu bytes)", kelem, elem, elem);
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -118,8 +119,7 @@ extern "C" bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void*
     a.d_in = plan->d; a.ds_in = plan->Ds;
     a.k = momenta; a.eps = eps; a.out = out; a.status = status;
     a.assign = plan->d_assign; a.ws = scratch;
-    const void* fparams = plan->field == BG_FIELD_FP ? (const void*)&plan->fpo : (const void*)&plan->c64o;
-    e->launch(fparams, &a, dim3((unsigned)blocks), 0, stream);
+    e->launch(bgi::compact_params(plan), &a, dim3((unsigned)blocks), 0, stream);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return bgi::fail(BG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(err));
     return BG_OK;

@@ -148,8 +148,8 @@ bg_status launch_request(bg_server* s, Request* r) {
     unsigned char* dout = de + r->bytes_e;
     uint8_t* dst = reinterpret_cast<uint8_t*>(dout + r->bytes_o);
     unsigned char* ws = dout + r->bytes_o + r->bytes_s;
-    const size_t elem = r->plan->field == BG_FIELD_FP ? 4 : 16;
-    const size_t nk = (size_t)r->E * r->plan->n * r->plan->d * elem;
+    const size_t elem = bgi::value_bytes(r->plan->field);
+    const size_t nk = (size_t)r->E * r->plan->n * r->plan->d * bgi::momentum_bytes(r->plan->field);
     const size_t ne = (size_t)r->E * r->plan->n * r->plan->S * r->plan->Ds * elem;
     const size_t no = (size_t)r->E * r->plan->H * elem;
     cudaError_t err = cudaMemcpyAsync(dk, r->k, nk, cudaMemcpyHostToDevice, st);
@@ -276,14 +276,14 @@ bg_status bg_serve_submit(bg_server* srv, const bg_plan* plan, int64_t E, const 
         return bgi::fail(BG_ERR_INVALID_ARG, "plan and server are on different devices");
     Request* r = new (std::nothrow) Request();
     if (!r) return bgi::fail(BG_ERR_NOMEM, "host allocation failed");
-    const size_t elem = plan->field == BG_FIELD_FP ? 4 : 16;
+    const size_t elem = bgi::value_bytes(plan->field);
     r->plan = plan;
     r->E = E;
     r->k = momenta;
     r->eps = eps;
     r->out = out;
     r->status = status;
-    r->bytes_k = up_granule((size_t)E * plan->n * plan->d * elem);
+    r->bytes_k = up_granule((size_t)E * plan->n * plan->d * bgi::momentum_bytes(plan->field));
     r->bytes_e = up_granule((size_t)E * plan->n * plan->S * plan->Ds * elem);
     r->bytes_o = up_granule((size_t)E * plan->H * elem);
     r->bytes_s = up_granule((size_t)E);

@@ -23,18 +23,23 @@ def _group(bg, field, n, d, Ds, metric, E, seed, S=1, assign=None):
         plan = bg.Plan(n, d, Ds, bg.FIELD_FP, p, metric, S, assign)
     else:
         k, e = G.c64_batch(seed, E, n, d, Ds, metric, S=S, workers=1)
-        kd = torch.from_numpy(k).cuda()
+        if field == "c64r":                       # real momenta
+            kd = torch.from_numpy(np.ascontiguousarray(k.real)).cuda()
+        else:
+            kd = torch.from_numpy(k).cuda()
         ed = torch.from_numpy(e).cuda()
-        plan = bg.Plan(n, d, Ds, bg.FIELD_C64, 0, metric, S, assign)
+        fid = bg.FIELD_C64_REAL if field == "c64r" else bg.FIELD_C64
+        plan = bg.Plan(n, d, Ds, fid, 0, metric, S, assign)
     H = plan.n_assign
-    out = torch.empty((E,) if H == 1 else (E, H), dtype=kd.dtype, device="cuda")
+    out = torch.empty((E,) if H == 1 else (E, H), dtype=ed.dtype, device="cuda")
     st = torch.empty(E, dtype=torch.uint8, device="cuda")
     return plan, kd, ed, out, st
 
 
 SPECS = [("fp", 4, 4, 4, 0, 3000), ("fp", 8, 6, 6, 0, 5000), ("fp", 12, 8, 8, 1, 700),
          ("fp", 7, 5, 7, 1, 1234), ("c64", 5, 4, 4, 0, 999), ("c64", 8, 6, 6, 1, 1500),
-         ("c64", 11, 8, 8, 0, 300), ("fp", 6, 4, 6, 0, 0), ("c64", 9, 6, 8, 0, 400)]
+         ("c64", 11, 8, 8, 0, 300), ("fp", 6, 4, 6, 0, 0), ("c64", 9, 6, 8, 0, 400),
+         ("c64r", 8, 6, 6, 0, 1300), ("c64r", 12, 4, 8, 1, 250)]
 
 
 def test_batch_matches_per_group_eval():
@@ -44,6 +49,7 @@ def test_batch_matches_per_group_eval():
     assign = np.array([[(h >> l) & 1 for l in range(6)] for h in range(64)], dtype=np.uint8)
     groups.append(_group(bg, "fp", 6, 4, 4, 1, 200, 99, S=2, assign=assign))
     groups.append(_group(bg, "c64", 6, 4, 4, 0, 150, 98, S=2, assign=assign))
+    groups.append(_group(bg, "c64r", 6, 4, 4, 1, 120, 97, S=2, assign=assign))
     refs = []
     for plan, k, e, _, _ in groups:
         if k.shape[0] == 0:

@@ -22,10 +22,13 @@ def _request(bg, field, n, d, E, seed):
         plan = bg.Plan(n, d, d, bg.FIELD_FP, P)
     else:
         k, e = G.c64_batch(seed, E, n, d, d, 0, workers=1)
-        hk = torch.from_numpy(k).pin_memory()
+        if field == "c64r":                       # real momenta
+            hk = torch.from_numpy(np.ascontiguousarray(k.real)).pin_memory()
+        else:
+            hk = torch.from_numpy(k).pin_memory()
         he = torch.from_numpy(e).pin_memory()
-        plan = bg.Plan(n, d, d, bg.FIELD_C64, 0)
-    out = torch.empty(E, dtype=hk.dtype).pin_memory()
+        plan = bg.Plan(n, d, d, bg.FIELD_C64_REAL if field == "c64r" else bg.FIELD_C64, 0)
+    out = torch.empty(E, dtype=he.dtype).pin_memory()
     st = torch.empty(E, dtype=torch.uint8).pin_memory()
     return plan, hk, he, out, st
 
@@ -43,7 +46,7 @@ def test_results_alone_equal_results_in_the_mix():
     rng = np.random.default_rng(3)
     reqs = []
     for i in range(40):
-        field = "fp" if i % 2 else "c64"
+        field = "fp" if i % 2 else ("c64r" if i % 4 == 2 else "c64")
         n = int(rng.integers(4, 13))
         d = int(rng.choice([4, 6, 8]))
         E = int(np.exp(rng.uniform(0, np.log(4000))))

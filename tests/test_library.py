@@ -58,7 +58,8 @@ def _create(lib, n=8, d=6, Ds=6, field=1, p=2147483629, metric=0, S=1, H=1, assi
 @pytest.mark.parametrize("kw", [
     dict(n=3), dict(n=13), dict(d=3), dict(d=9), dict(Ds=5), dict(Ds=9),
     dict(p=2147483647 * 2 + 1), dict(p=2147483649), dict(p=4), dict(p=2147483627),  # not prime
-    dict(field=2), dict(metric=2), dict(field=0, p=7), dict(S=0), dict(H=0), dict(H=2),
+    dict(field=3), dict(field=-1), dict(metric=2), dict(field=0, p=7), dict(field=2, p=7), dict(S=0),
+    dict(H=0), dict(H=2),
 ])
 def test_plan_rejects_bad_arguments_on_host(lib, kw):
     assert _create(lib, **kw) == 1          # BG_ERR_INVALID_ARG before any CUDA call
