@@ -630,7 +630,7 @@ def main():
     ops_c64c = kernel_fp64_ops(N_LEG, D, DS, False)
     kops = kernel_mults(N_LEG, D, DS)
     traffic_fp = profiled_traffic("fp_compact_n8_d6.md")
-    traffic_c64 = profiled_traffic("c64_compact_n8_d6.md")
+    traffic_c64 = profiled_traffic("c64_real_compact_n8_d6.md")
     scale = E / float(1 << 22)
     line = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
