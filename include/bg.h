@@ -93,8 +93,13 @@ typedef struct bg_plan bg_plan;   /* opaque; immutable after creation; may be
  *   n_states S >= 1: states supplied per leg (eps layout [E][n][S][D_s])
  *   n_assign H >= 1: state assignments evaluated per point (out [E][H]);
  *            H * n <= 2^20
- *   assign   host array [H][n] of state indices < S, copied by the call; may
- *            be NULL only when H == 1 (then every leg uses state 0)
+ *   assign   host array [H][n] of state indices < S, copied by the call; or
+ *            NULL with H == 1 (every leg uses state 0); or NULL with
+ *            H == S^n, S >= 2: every assignment, leg l taking state
+ *            (h / S^l) mod S in output column h.  That form evaluates all
+ *            assignments of a point in one recursion whose sub-currents are
+ *            shared between the assignments that agree on their legs (one
+ *            warp per point); bg_eval_noalloc and bg_batch_* reject it.
  *   out      receives the plan
  */
 bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p,

@@ -142,12 +142,19 @@ class Plan:
     """One (n, d, D_s, field, p, metric, states) configuration (bg_plan)."""
 
     def __init__(self, n, d, Ds, field, p=0, metric=MOSTLY_MINUS, n_states=1, assign=None):
+        """assign: None (every leg takes state 0), an [H][n] table of state
+        indices, or "all": every one of the n_states^n assignments, output
+        index h = sum_l s_l n_states^l, evaluated with shared sub-currents."""
         self.n, self.d, self.Ds = n, d, Ds
         self.field, self.p, self.metric = field, p, metric
         self.n_states = n_states
         buf = None
         H = 1
-        if assign is not None:
+        if isinstance(assign, str):
+            if assign != "all":
+                raise ValueError('assign must be None, a table or "all"')
+            H = n_states ** n
+        elif assign is not None:
             import numpy as np
             a = np.ascontiguousarray(assign, dtype=np.uint8)
             if a.ndim != 2 or a.shape[1] != n:

@@ -24,6 +24,10 @@ BG_REGC(c64, 8, 8)
 BG_REGC(c64r, 4, 4) BG_REGC(c64r, 4, 6) BG_REGC(c64r, 4, 8) BG_REGC(c64r, 6, 6) BG_REGC(c64r, 6, 8)
 BG_REGC(c64r, 8, 8)
 #undef BG_REGC
+#define BG_REGS(TAG, D) void bg_register_states_##TAG##_##D(std::vector<bgk::StatesEntry>&);
+BG_REGS(fp, 4) BG_REGS(fp, 6) BG_REGS(fp, 8) BG_REGS(c64, 4) BG_REGS(c64, 6) BG_REGS(c64, 8)
+BG_REGS(c64r, 4) BG_REGS(c64r, 6) BG_REGS(c64r, 8)
+#undef BG_REGS
 
 namespace {
 thread_local std::string g_last_error;
@@ -55,6 +59,17 @@ const std::vector<bgk::KernelEntry>& registry() {
         BG_ADDC(c64r, 6, 8) BG_ADDC(c64r, 8, 8)
 #undef BG_ADDC
 #undef BG_ADD
+    });
+    return v;
+}
+
+const std::vector<bgk::StatesEntry>& states_registry() {
+    static std::vector<bgk::StatesEntry> v;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        bg_register_states_fp_4(v); bg_register_states_fp_6(v); bg_register_states_fp_8(v);
+        bg_register_states_c64_4(v); bg_register_states_c64_6(v); bg_register_states_c64_8(v);
+        bg_register_states_c64r_4(v); bg_register_states_c64r_6(v); bg_register_states_c64r_8(v);
     });
     return v;
 }
@@ -143,6 +158,44 @@ using bgi::momentum_bytes;
 using bgi::compact_params;
 using bgi::field_name;
 
+namespace {
+
+// Table bytes of one block of the states kernel above which the table moves
+// to global scratch: at most this much shared memory keeps four or more
+// blocks (16 warps) resident per SM.
+constexpr size_t kStatesSmemMax = 56 * 1024;
+
+// States-kernel choice, table placement and occupancy of an all-assignment plan.
+bg_status setup_states(bg_plan* pl, const char* tenv) {
+    const int D = round_dim(pl->d), DS = round_dim(pl->Ds);
+    for (const auto& e : bgi::states_registry())
+        if (e.field == (int)pl->field && e.D == D && e.DS == DS && e.metric == (int)pl->metric)
+            pl->sentry = &e;
+    if (!pl->sentry) return fail(BG_ERR_UNSUPPORTED, "no all-assignment kernel for this plan");
+    pl->sgeo = bgk::make_states_geometry(pl->n, pl->S, D, DS, pl->sentry->elem_bytes, pl->sentry->elem_k_bytes);
+    pl->all_states = true;
+    const size_t smem = (size_t)bgk::kStatesWarps * pl->sgeo.words * pl->sentry->elem_bytes;
+    bool global = smem > kStatesSmemMax;
+    if (tenv) global = strcmp(tenv, "global") == 0 || smem > 227 * 1024;
+    pl->states_global = global;
+    pl->smem_bytes = global ? 0 : smem;
+    if (pl->smem_bytes > 0) {
+        bg_status st = bgi::ensure_smem_limit(pl->sentry->func, pl->device, pl->smem_bytes);
+        if (st != BG_OK) return st;
+    }
+    int occ = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pl->sentry->func,
+                                                                    32 * bgk::kStatesWarps, pl->smem_bytes);
+    if (err != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return fail(BG_ERR_UNSUPPORTED, "all-assignment kernel cannot be resident (%s)", cudaGetErrorString(err));
+    }
+    pl->blocks_per_sm = occ;
+    return BG_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* bg_strerror(bg_status s) {
@@ -183,7 +236,16 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
     if (n_states < 1 || n_states > 255) return fail(BG_ERR_INVALID_ARG, "n_states = %d", n_states);
     if (n_assign < 1 || (int64_t)n_assign * n > (1 << 20))
         return fail(BG_ERR_INVALID_ARG, "n_assign = %d", n_assign);
-    if (n_assign > 1 && !assign) return fail(BG_ERR_INVALID_ARG, "assign is NULL with n_assign > 1");
+    // assign == NULL with H > 1: all S^n assignments (H must equal S^n),
+    // evaluated with sub-currents shared between assignments
+    bool all_states = false;
+    if (n_assign > 1 && !assign) {
+        int64_t h = 1;
+        for (int l = 0; l < n && h <= n_assign; ++l) h *= n_states;
+        if (n_states < 2 || h != n_assign)
+            return fail(BG_ERR_INVALID_ARG, "assign is NULL with n_assign = %d != n_states^n", n_assign);
+        all_states = true;
+    }
     if (assign) {
         for (int64_t i = 0; i < (int64_t)n_assign * n; ++i)
             if (assign[i] >= n_states)
@@ -279,7 +341,14 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
         return fail(BG_ERR_UNSUPPORTED, "kernel cannot be resident (%s)", cudaGetErrorString(err));
     }
     pl->blocks_per_sm = occ;
-    if (n_assign > 1) {
+    if (all_states) {
+        bg_status st = setup_states(pl, tenv);
+        if (st != BG_OK) {
+            delete pl;
+            return st;
+        }
+    }
+    if (n_assign > 1 && !all_states) {
         size_t bytes = pl->assign.size();
         if (cudaMalloc(&pl->d_assign, bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -309,7 +378,15 @@ static int64_t resident_blocks(const bg_plan* pl) { return (int64_t)pl->blocks_p
 bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes) {
     if (!plan || !bytes || E < 0) return fail(BG_ERR_INVALID_ARG, "bad argument to bg_workspace_size");
     *bytes = 0;
-    if (!plan->entry->global_table || E == 0) return BG_OK;
+    if (E == 0) return BG_OK;
+    if (plan->all_states) {
+        if (!plan->states_global) return BG_OK;
+        int64_t blocks = (E + bgk::kStatesWarps - 1) / bgk::kStatesWarps;
+        if (blocks > resident_blocks(plan)) blocks = resident_blocks(plan);
+        *bytes = (size_t)blocks * bgk::kStatesWarps * plan->sgeo.words * plan->sentry->elem_bytes;
+        return BG_OK;
+    }
+    if (!plan->entry->global_table) return BG_OK;
     const int64_t items = E * plan->H;
     const int B = plan->entry->block;
     int64_t blocks = (items + B - 1) / B;
@@ -321,6 +398,18 @@ bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes) {
 bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
     if (!plan || !buf) return fail(BG_ERR_INVALID_ARG, "bad argument to bg_plan_describe");
     const auto* e = plan->entry;
+    if (plan->all_states) {
+        int w = snprintf(buf, len,
+                         "field=%s n=%d d=%d D_s=%d kernel=states kernel_D=%d kernel_D_s=%d metric=%s "
+                         "table=%s states=%d assignments=%d warps_per_block=%d blocks_per_sm=%d smem=%zu "
+                         "words_per_point=%d elem_bytes=%d",
+                         field_name(plan->field), plan->n, plan->d, plan->Ds, plan->sentry->D,
+                         plan->sentry->DS, plan->metric == BG_METRIC_MOSTLY_MINUS ? "mostly_minus" : "alternating",
+                         plan->states_global ? "global" : "shared", plan->S, plan->H, bgk::kStatesWarps,
+                         plan->blocks_per_sm, plan->smem_bytes, plan->sgeo.words, plan->sentry->elem_bytes);
+        if (w < 0 || (size_t)w >= len) return fail(BG_ERR_INVALID_ARG, "buffer too small");
+        return BG_OK;
+    }
     int w = snprintf(buf, len,
                      "field=%s n=%d d=%d D_s=%d kernel=%s kernel_D=%d kernel_D_s=%d metric=%s "
                      "table=%s block=%d blocks_per_sm=%d smem=%zu words_per_thread=%d elem_bytes=%d",
@@ -367,10 +456,26 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const voi
         if ((uintptr_t)workspace % 256) return fail(BG_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
         if ((st = check_device_ptr(workspace, "workspace", dev)) != BG_OK) return st;
     }
-    if (dev != plan->device && plan->smem_bytes > 0) {
+    if (!plan->all_states && dev != plan->device && plan->smem_bytes > 0) {
         if ((st = bgi::ensure_smem_limit(e->func, dev, plan->smem_bytes)) != BG_OK) return st;
     }
 
+    if (plan->all_states) {
+        if (dev != plan->device && plan->smem_bytes > 0) {
+            if ((st = bgi::ensure_smem_limit(plan->sentry->func, dev, plan->smem_bytes)) != BG_OK) return st;
+        }
+        int64_t blocks = (E + bgk::kStatesWarps - 1) / bgk::kStatesWarps;
+        if (blocks > resident_blocks(plan)) blocks = resident_blocks(plan);
+        bgk::StatesArgs a;
+        a.E = E; a.n = plan->n; a.d_in = plan->d; a.ds_in = plan->Ds;
+        a.k = momenta; a.eps = eps; a.out = out; a.status = status;
+        a.ws = plan->states_global ? workspace : nullptr;
+        plan->sentry->launch(compact_params(plan), a, plan->sgeo, dim3((unsigned)blocks), plan->smem_bytes,
+                             stream);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return fail(BG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(err));
+        return BG_OK;
+    }
     const int64_t items = E * plan->H;
     int64_t blocks = (items + e->block - 1) / e->block;
     const int64_t cap = e->global_table ? resident_blocks(plan) : resident_blocks(plan) * 256;

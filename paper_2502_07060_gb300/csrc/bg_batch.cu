@@ -72,6 +72,8 @@ bg_status build_layout(const bg_group* groups, int n_groups, const bg_batch_conf
         if (g.E == 0) continue;
         if (!g.momenta || !g.eps || !g.out) return bgi::fail(BG_ERR_INVALID_ARG, "group %d: NULL buffer", gi);
         const bg_plan* pl = g.plan;
+        if (pl->all_states)
+            return bgi::fail(BG_ERR_UNSUPPORTED, "group %d: all-assignment plans are evaluated by bg_eval", gi);
         if (g.E > (int64_t(1) << 40) / pl->H) return bgi::fail(BG_ERR_INVALID_ARG, "group %d too large", gi);
         const int D = bgi::round_dim(pl->d), DS = bgi::round_dim(pl->Ds);
         order.push_back({gi, point_cost(pl->n, D, DS, pl->field) * pl->H});

@@ -8,6 +8,7 @@
 
 #include "../../include/bg.h"
 #include "bg_instances.cuh"
+#include "bg_states.cuh"
 
 struct bg_plan {
     int n, d, Ds;
@@ -28,10 +29,16 @@ struct bg_plan {
     int sm_count = 0;
     int blocks_per_sm = 0;
     size_t smem_bytes = 0;            // dynamic shared memory per block
+    // all S^n assignments with sub-current reuse (assign == NULL, H == S^n > 1)
+    bool all_states = false;
+    const bgk::StatesEntry* sentry = nullptr;
+    bgk::StatesGeometry sgeo{};
+    bool states_global = false;       // states table in global scratch
 };
 
 namespace bgi {
 const std::vector<bgk::KernelEntry>& registry();
+const std::vector<bgk::StatesEntry>& states_registry();
 bg_status fail(bg_status s, const char* fmt, ...);
 bg_status check_device_ptr(const void* ptr, const char* what, int device);
 int round_dim(int x);

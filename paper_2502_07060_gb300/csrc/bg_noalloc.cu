@@ -64,6 +64,8 @@ extern "C" bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void*
     if (E == 0) return BG_OK;
     if (!momenta || !eps || !out)
         return bgi::fail(BG_ERR_INVALID_ARG, "momenta, eps and out must be non-NULL");
+    if (plan->all_states)
+        return bgi::fail(BG_ERR_UNSUPPORTED, "all-assignment plans (assign == NULL, H = S^n) are not supported here");
     if (E > (int64_t(1) << 40) / plan->H)
         return bgi::fail(BG_ERR_INVALID_ARG, "E * n_assign exceeds the maximum of 2^40 work items");
     const size_t elem = bgi::value_bytes(plan->field), kelem = bgi::momentum_bytes(plan->field);
