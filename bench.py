@@ -408,6 +408,53 @@ def mixed_workload(args, device):
             "unit": "amplitudes/s", "steps": steps}
 
 
+def helicity_workload(args, device):
+    """All 2^n helicity assignments (n = 6..10, d = D_s = 4, two states per
+    leg): F_p at p = 2^31 - 1 in the alternating metric and complex FP64 on
+    physical points (real momenta).  Times the all-assignment plan (shared
+    sub-currents) against the same assignments as an explicit table (one full
+    recursion per assignment)."""
+    import torch
+    from paper_2502_07060_gb300 import bg
+    res = []
+    steps = 3
+    for field in ("fp", "c64"):
+        for n in range(6, 11):
+            H = 1 << n
+            E = 1 << (args.log2_points_helicity if field == "fp" else args.log2_points_helicity - 3)
+            table = np.array([[(h >> l) & 1 for l in range(n)] for h in range(H)], dtype=np.uint8)
+            if field == "fp":
+                k, e = G.fp_batch(4000 + n, E, n, 4, 4, G.P_MERSENNE, 1, S=2)
+                kd = torch.from_numpy(k.view(np.int32)).to(device)
+                ed = torch.from_numpy(e.view(np.int32)).to(device)
+                mk = lambda a: bg.Plan(n, 4, 4, bg.FIELD_FP, G.P_MERSENNE, bg.ALTERNATING, 2, a)
+            else:
+                k, e = G.c64_batch(4000 + n, E, n, 4, 4, 0, S=2)
+                kd = torch.from_numpy(np.ascontiguousarray(k.real)).to(device)
+                ed = torch.from_numpy(e).to(device)
+                mk = lambda a: bg.Plan(n, 4, 4, bg.FIELD_C64_REAL, 0, bg.MOSTLY_MINUS, 2, a)
+            del k, e
+            out = torch.empty((E, H), dtype=ed.dtype, device=device)
+            st = torch.empty(E, dtype=torch.uint8, device=device)
+            stream = torch.cuda.current_stream(device)
+            row = {"field": field, "n": n, "points": E, "assignments": H}
+            for mode, a in (("shared_currents", "all"), ("per_assignment", table)):
+                plan = mk(a)
+                ws = plan.workspace(E, device)
+                ms = time_steps(lambda: plan.eval(kd, ed, out=out, status=st, workspace=ws, stream=stream),
+                                steps, args.warmup, stream, None, device)
+                row[mode] = {"ms_per_step": ms / steps, "value": E * H / (ms / steps / 1e3),
+                             "plan": plan.describe()}
+                del plan, ws
+            row["speedup"] = row["shared_currents"]["value"] / row["per_assignment"]["value"]
+            res.append(row)
+            del kd, ed, out, st
+            torch.cuda.empty_cache()
+    return {"workload": "all 2^n helicity assignments, n = 6..10, d = D_s = 4, S = 2 states per leg; "
+                        "F_p p = 2^31-1 (alternating metric) and complex FP64 with real momenta",
+            "unit": "amplitudes/s", "steps": steps, "rows": res}
+
+
 def serve_workload(args, device):
     """Poisson arrivals (mean rate --serve-rate per second) of requests with
     log-uniform sizes 1..65536 points, n uniform in 4..12, d = D_s uniform in
@@ -537,9 +584,12 @@ def main():
                     help="comma list of fp, c64 (real momenta, the physical points), c64c (the same "
                          "points through the complex-momentum plan)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
-    ap.add_argument("--workload", choices=["metric", "mixed", "serve"], default="metric",
+    ap.add_argument("--workload", choices=["metric", "mixed", "serve", "helicity"], default="metric",
                     help="metric: n=8 d=6 headline line; mixed: uneven-batch comparison; "
-                         "serve: p50/p99 latency of the request server")
+                         "serve: p50/p99 latency of the request server; helicity: all 2^n "
+                         "helicities with shared sub-currents against one recursion per assignment")
+    ap.add_argument("--log2-points-helicity", type=int, default=18,
+                    help="F_p points per n of the helicity workload (complex: 8x fewer)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args()
@@ -590,6 +640,10 @@ def main():
     if args.workload == "mixed":
         if rank == 0:
             print(json.dumps({"metric": METRIC, "mixed": mixed_workload(args, device)}))
+        return
+    if args.workload == "helicity":
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "helicity": helicity_workload(args, device)}))
         return
     if args.workload == "serve":
         if rank == 0:

@@ -106,6 +106,23 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p,
                          bg_metric metric, int n_states, int n_assign,
                          const uint8_t* assign, bg_plan** out);
 
+/*
+ * bg_plan_create_product -- a plan over every assignment of a product of
+ * per-leg state sets: leg l takes states 0 .. states_per_leg[l]-1 (of the
+ * n_states slots per leg in eps).  H = prod states_per_leg; output column
+ * h = sum_l s_l * prod_{l' < l} states_per_leg[l'] (leg 0 fastest).  All
+ * assignments of a point are evaluated in one recursion whose sub-currents
+ * are shared between the assignments that agree on their legs (Sec. 2.2
+ * memoisation carried across assignments): the helicity sums of Sec. 2.3
+ * (all legs two states) and the cut trees of Sec. 2.1 (only the internal
+ * legs with several states; see bg_cut_trace).  1 <= states_per_leg[l] <=
+ * n_states <= 255, H * n <= 2^20.  Other arguments and errors as
+ * bg_plan_create; bg_eval_noalloc and bg_batch_* reject such plans.
+ */
+bg_status bg_plan_create_product(int n, int d, int D_s, bg_field field, uint32_t p,
+                                 bg_metric metric, int n_states,
+                                 const uint8_t* states_per_leg, bg_plan** out);
+
 /* bg_plan_destroy -- free a plan (NULL is accepted).  No kernel of this plan
  * may still be running. */
 bg_status bg_plan_destroy(bg_plan* plan);
@@ -293,6 +310,22 @@ bg_status bg_serve_stats(bg_server* srv, uint64_t* submitted, uint64_t* complete
 /* bg_serve_destroy -- finish every queued and running request, then free the
  * arena, streams and thread.  No call on `srv` may follow. */
 bg_status bg_serve_destroy(bg_server* srv);
+
+/*
+ * bg_cut_trace -- state sum over a ring of k tree amplitudes (the leading pole
+ * of a one-loop cut, Sec. 2.1): for every point e,
+ *     out[e] = sum_{s_1..s_k} prod_{i=1..k} M_i[e][s_{i+1}][s_i],  s_{k+1} = s_1,
+ * i.e. trace(M_k ... M_2 M_1).  M is a HOST array of k device pointers, each
+ * [E][S][S] (row = outgoing internal state, column = incoming), uint32
+ * residues in [0, p) for BG_FIELD_FP or double2 for the complex fields: the
+ * output of a product plan whose only legs with S states are leg 0 (the
+ * incoming internal leg, with the dual "tilde" states of Sec. 2.3) and leg
+ * n-1 (the outgoing one), the others one state.  out: device [E], same
+ * element type.  1 <= k <= 16, 1 <= S <= 8, p < 2^31 for F_p (ignored
+ * otherwise).  Asynchronous on `stream`; errors as bg_eval.
+ */
+bg_status bg_cut_trace(bg_field field, uint32_t p, int64_t E, int k, int S,
+                       const void* const* M, void* out, cudaStream_t stream);
 
 /* bg_plan_describe -- NUL-terminated one-line description of the kernel the
  * plan launches (variant, block size, shared memory, workspace per thread)

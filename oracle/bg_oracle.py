@@ -48,7 +48,11 @@ The code is generic over the number type: ``fractions.Fraction``, Python
 ``complex``, ``mpmath.mpc`` and the prime field ``GF(p)`` below all work,
 because only +, -, *, / and == are used.
 
-Pins (tests/test_oracle_pins.py) relate this module to facts the paper and
+``cut_state_sum`` is the sum over internal states of a ring of tree
+amplitudes that a one-loop cut needs (Sec. 2.1), literal over all state
+tuples.
+
+Pins (tests/test_oracle_pins.py, tests/test_oracle_cut.py) relate this module to facts the paper and
 mathematics fix: the tensor-form brute-force diagram sum, the Ward identity,
 cyclic and reflection symmetry, U(1) decoupling, current conservation,
 dimensional embedding, Lorentz invariance, Parke-Taylor (Sec. 3.1),
@@ -421,3 +425,25 @@ def bruteforce_diagrams(k, eps, metric, i_unit):
         for mu in range(Ds):
             M = M + en[mu] * b[mu]
     return M, count
+
+
+def cut_state_sum(mats):
+    """State sum over a ring of tree amplitudes (the leading pole of a
+    one-loop cut, Sec. 2.1): with k trees joined in a ring by k internal legs,
+    tree i given as its amplitudes M_i[s_out][s_in] for the states of its
+    outgoing and incoming internal legs,
+
+        sum over s_1..s_k of  prod_i M_i[s_{i+1}][s_i],    s_{k+1} = s_1,
+
+    evaluated literally, term by term over all S^k state tuples.  ``mats`` is
+    a list of k square nested lists (or arrays) of one number type."""
+    k = len(mats)
+    S = len(mats[0])
+    total = None
+    for states in itertools.product(range(S), repeat=k):
+        term = None
+        for i in range(k):
+            v = mats[i][states[(i + 1) % k]][states[i]]
+            term = v if term is None else term * v
+        total = term if total is None else total + term
+    return total

@@ -31,7 +31,7 @@ MOSTLY_MINUS = 0
 ALTERNATING = 1
 
 # bg_plan_create / bg_eval / ... as declared in include/bg.h
-EXPORTED = ("bg_plan_create", "bg_plan_destroy", "bg_workspace_size", "bg_eval",
+EXPORTED = ("bg_plan_create", "bg_plan_create_product", "bg_cut_trace", "bg_plan_destroy", "bg_workspace_size", "bg_eval",
             "bg_eval_noalloc", "bg_host_staging_size", "bg_eval_host", "bg_batch_workspace_size",
             "bg_batch_create", "bg_batch_launch", "bg_batch_describe", "bg_batch_destroy",
             "bg_batch_autotune", "bg_serve_create", "bg_serve_submit", "bg_serve_wait",
@@ -63,6 +63,13 @@ def load_library(path=None):
                                    ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(vp)]
     lib.bg_plan_create.restype = ctypes.c_int
+    lib.bg_plan_create_product.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(vp)]
+    lib.bg_plan_create_product.restype = ctypes.c_int
+    lib.bg_cut_trace.argtypes = [ctypes.c_int, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(vp), vp, vp]
+    lib.bg_cut_trace.restype = ctypes.c_int
     lib.bg_plan_destroy.argtypes = [vp]
     lib.bg_plan_destroy.restype = ctypes.c_int
     lib.bg_workspace_size.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
@@ -141,13 +148,30 @@ def _stream_handle(stream):
 class Plan:
     """One (n, d, D_s, field, p, metric, states) configuration (bg_plan)."""
 
-    def __init__(self, n, d, Ds, field, p=0, metric=MOSTLY_MINUS, n_states=1, assign=None):
+    def __init__(self, n, d, Ds, field, p=0, metric=MOSTLY_MINUS, n_states=1, assign=None,
+                 states_per_leg=None):
         """assign: None (every leg takes state 0), an [H][n] table of state
         indices, or "all": every one of the n_states^n assignments, output
-        index h = sum_l s_l n_states^l, evaluated with shared sub-currents."""
+        index h = sum_l s_l n_states^l, evaluated with shared sub-currents.
+        states_per_leg (instead of assign): the product plan of
+        bg_plan_create_product (leg l takes states 0..states_per_leg[l]-1)."""
         self.n, self.d, self.Ds = n, d, Ds
         self.field, self.p, self.metric = field, p, metric
         self.n_states = n_states
+        self._ws = None
+        if states_per_leg is not None:
+            import numpy as np
+            r = np.ascontiguousarray(states_per_leg, dtype=np.uint8)
+            if r.shape != (n,):
+                raise ValueError("states_per_leg must have n entries")
+            self._radix = r
+            self.n_assign = int(np.prod(r.astype(np.int64)))
+            h = ctypes.c_void_p()
+            _check(_lib.bg_plan_create_product(n, d, Ds, field, p, metric, n_states,
+                                               r.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                               ctypes.byref(h)))
+            self._h = h
+            return
         buf = None
         H = 1
         if isinstance(assign, str):
@@ -401,6 +425,23 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def cut_trace(field, matrices, out=None, p=0, stream=None):
+    """bg_cut_trace: out[e] = trace(M_k ... M_1) for device tensors
+    matrices[i] of shape [E][S][S] or [E][S*S] (row = outgoing state)."""
+    import torch
+    k = len(matrices)
+    E = matrices[0].shape[0]
+    S = int(round((matrices[0][0].numel()) ** 0.5)) if E else 1
+    for m in matrices:
+        if not m.is_contiguous() or m.shape[0] != E or m[0].numel() != S * S:
+            raise ValueError("matrices must be contiguous [E][S][S] tensors")
+    if out is None:
+        out = torch.empty(E, dtype=matrices[0].dtype, device=matrices[0].device)
+    ptrs = (ctypes.c_void_p * k)(*[m.data_ptr() for m in matrices])
+    _check(_lib.bg_cut_trace(field, p, E, k, S, ptrs, _ptr(out), _stream_handle(stream)))
+    return out
 
 
 def strerror(status):

@@ -165,16 +165,21 @@ namespace {
 // blocks (16 warps) resident per SM.
 constexpr size_t kStatesSmemMax = 56 * 1024;
 
-// States-kernel choice, table placement and occupancy of an all-assignment plan.
-bg_status setup_states(bg_plan* pl, const char* tenv) {
+// States-kernel choice, table placement and occupancy of a plan over the
+// product of per-leg state sets (radix[l] states on leg l).
+bg_status setup_states(bg_plan* pl, const int* radix, const char* tenv) {
     const int D = round_dim(pl->d), DS = round_dim(pl->Ds);
+    bool uniform = true;
+    for (int l = 1; l < pl->n; ++l) uniform &= radix[l] == radix[0];
     for (const auto& e : bgi::states_registry())
-        if (e.field == (int)pl->field && e.D == D && e.DS == DS && e.metric == (int)pl->metric)
+        if (e.field == (int)pl->field && e.D == D && e.DS == DS && e.metric == (int)pl->metric &&
+            e.uniform == uniform)
             pl->sentry = &e;
     if (!pl->sentry) return fail(BG_ERR_UNSUPPORTED, "no all-assignment kernel for this plan");
-    pl->sgeo = bgk::make_states_geometry(pl->n, pl->S, D, DS, pl->sentry->elem_bytes, pl->sentry->elem_k_bytes);
+    pl->sgeo = bgk::make_states_geometry(pl->n, pl->S, radix, D, DS, pl->sentry->elem_bytes,
+                                         pl->sentry->elem_k_bytes);
     pl->all_states = true;
-    const size_t smem = (size_t)bgk::kStatesWarps * pl->sgeo.words * pl->sentry->elem_bytes;
+    const size_t smem = (size_t)bgk::kStatesWarps * pl->sgeo.P * pl->sgeo.words * pl->sentry->elem_bytes;
     bool global = smem > kStatesSmemMax;
     if (tenv) global = strcmp(tenv, "global") == 0 || smem > 227 * 1024;
     pl->states_global = global;
@@ -215,8 +220,13 @@ const char* bg_last_error(void) { return g_last_error.c_str(); }
 
 int bg_version(void) { return BG_VERSION; }
 
-bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_metric metric,
-                         int n_states, int n_assign, const uint8_t* assign, bg_plan** out) {
+}  // extern "C"
+
+// Plan creation; product_radix (or NULL) gives the states per leg of a
+// product plan (all assignments of the product of per-leg state sets).
+static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, bg_metric metric,
+                             int n_states, int n_assign, const uint8_t* assign, const uint8_t* product_radix,
+                             bg_plan** out) {
     g_last_error.clear();
     if (!out) return fail(BG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -238,8 +248,8 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
         return fail(BG_ERR_INVALID_ARG, "n_assign = %d", n_assign);
     // assign == NULL with H > 1: all S^n assignments (H must equal S^n),
     // evaluated with sub-currents shared between assignments
-    bool all_states = false;
-    if (n_assign > 1 && !assign) {
+    bool all_states = product_radix != nullptr;
+    if (n_assign > 1 && !assign && !product_radix) {
         int64_t h = 1;
         for (int l = 0; l < n && h <= n_assign; ++l) h *= n_states;
         if (n_states < 2 || h != n_assign)
@@ -254,8 +264,9 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
 
     // Kernel choice: the compact kernel (run-time n) by default; the unrolled
     // per-n kernel on request (BG_KERNEL=unrolled, F_p only, n <= 8).  Table
-    // placement: shared memory for small tables, else global scratch
-    // (BG_TABLE=shared|global overrides).
+    // placement: shared memory for small tables, else global scratch, or split
+    // (currents global, the rest on chip) (BG_TABLE=shared|global|split
+    // overrides).
     const char* kenv = getenv("BG_KERNEL");
     const bool want_unrolled = kenv && strcmp(kenv, "unrolled") == 0;
     const char* tenv = getenv("BG_TABLE");
@@ -272,19 +283,23 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
         const bgk::Geometry geo{n - 1};
         words = geo.words(Dk, DSk);
         const size_t elem = value_bytes(field);
-        bool want_global = true;
+        int want = bgk::kPlaceGlobal;
         if (tenv) {
-            want_global = strcmp(tenv, "global") == 0;
+            want = strcmp(tenv, "shared") == 0 ? bgk::kPlaceShared
+                 : strcmp(tenv, "split") == 0 ? bgk::kPlaceSplit : bgk::kPlaceGlobal;
         } else if (field == BG_FIELD_FP) {
             // measured on GB300 (n = 5..12): shared wins while a block's table
             // is at most ~40 KB (five or more blocks per SM), global beyond
             const size_t smem = (size_t)words * bgk::kBlockFpCompactSmem * elem;
-            want_global = smem > 40 * 1024;
+            want = smem > 40 * 1024 ? bgk::kPlaceGlobal : bgk::kPlaceShared;
         }
-        for (const auto& e : registry())
+        for (const auto& e : registry()) {
+            const int place = e.split ? bgk::kPlaceSplit : e.global_table ? bgk::kPlaceGlobal : bgk::kPlaceShared;
             if (e.compact && e.field == (int)field && e.D == Dk && e.DS == DSk &&
-                e.metric == (int)metric && e.global_table == want_global)
+                e.metric == (int)metric && place == want)
                 best = &e;
+        }
+        if (best && best->split) words = geo.cur_words(DSk);
         if (!best)      // the complex fields have only the global placement
             for (const auto& e : registry())
                 if (e.compact && e.field == (int)field && e.D == Dk && e.DS == DSk &&
@@ -324,7 +339,9 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
         return fail(BG_ERR_CUDA, "no CUDA device");
     }
     cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device);
-    pl->smem_bytes = best->global_table ? 0 : (size_t)words * best->block * best->elem_bytes;
+    pl->smem_bytes = best->split ? (size_t)bgk::Geometry{n - 1}.aux_words(round_dim(d), round_dim(D_s)) *
+                                       best->block * best->elem_bytes
+                   : best->global_table ? 0 : (size_t)words * best->block * best->elem_bytes;
     if (pl->smem_bytes > 0) {
         bg_status st = bgi::ensure_smem_limit(best->func, pl->device, pl->smem_bytes);
         if (st != BG_OK) {
@@ -342,7 +359,9 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
     }
     pl->blocks_per_sm = occ;
     if (all_states) {
-        bg_status st = setup_states(pl, tenv);
+        int radix[bgk::kStatesMaxLegs];
+        for (int l = 0; l < n; ++l) radix[l] = product_radix ? product_radix[l] : n_states;
+        bg_status st = setup_states(pl, radix, tenv);
         if (st != BG_OK) {
             delete pl;
             return st;
@@ -366,6 +385,31 @@ bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_m
     return BG_OK;
 }
 
+extern "C" {
+
+bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_metric metric,
+                         int n_states, int n_assign, const uint8_t* assign, bg_plan** out) {
+    return create_plan(n, d, D_s, field, p, metric, n_states, n_assign, assign, nullptr, out);
+}
+
+bg_status bg_plan_create_product(int n, int d, int D_s, bg_field field, uint32_t p, bg_metric metric,
+                                 int n_states, const uint8_t* states_per_leg, bg_plan** out) {
+    g_last_error.clear();
+    if (!out) return fail(BG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!states_per_leg) return fail(BG_ERR_INVALID_ARG, "states_per_leg is NULL");
+    if (n < 4 || n > 12) return fail(BG_ERR_INVALID_ARG, "n = %d outside [4, 12]", n);
+    if (n_states < 1 || n_states > 255) return fail(BG_ERR_INVALID_ARG, "n_states = %d", n_states);
+    int64_t h = 1;
+    for (int l = 0; l < n; ++l) {
+        if (states_per_leg[l] < 1 || states_per_leg[l] > n_states)
+            return fail(BG_ERR_INVALID_ARG, "states_per_leg[%d] = %d outside [1, n_states]", l, states_per_leg[l]);
+        h *= states_per_leg[l];
+        if (h * n > (1 << 20)) return fail(BG_ERR_INVALID_ARG, "product of states_per_leg too large");
+    }
+    return create_plan(n, d, D_s, field, p, metric, n_states, (int)h, nullptr, states_per_leg, out);
+}
+
 bg_status bg_plan_destroy(bg_plan* plan) {
     if (!plan) return BG_OK;
     if (plan->d_assign) cudaFree(plan->d_assign);
@@ -381,9 +425,10 @@ bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes) {
     if (E == 0) return BG_OK;
     if (plan->all_states) {
         if (!plan->states_global) return BG_OK;
-        int64_t blocks = (E + bgk::kStatesWarps - 1) / bgk::kStatesWarps;
+        const int64_t per_block = (int64_t)bgk::kStatesWarps * plan->sgeo.P;
+        int64_t blocks = (E + per_block - 1) / per_block;
         if (blocks > resident_blocks(plan)) blocks = resident_blocks(plan);
-        *bytes = (size_t)blocks * bgk::kStatesWarps * plan->sgeo.words * plan->sentry->elem_bytes;
+        *bytes = (size_t)blocks * per_block * plan->sgeo.words * plan->sentry->elem_bytes;
         return BG_OK;
     }
     if (!plan->entry->global_table) return BG_OK;
@@ -401,12 +446,12 @@ bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
     if (plan->all_states) {
         int w = snprintf(buf, len,
                          "field=%s n=%d d=%d D_s=%d kernel=states kernel_D=%d kernel_D_s=%d metric=%s "
-                         "table=%s states=%d assignments=%d warps_per_block=%d blocks_per_sm=%d smem=%zu "
-                         "words_per_point=%d elem_bytes=%d",
+                         "table=%s states=%d assignments=%d warps_per_block=%d points_per_warp=%d "
+                         "blocks_per_sm=%d smem=%zu words_per_point=%d elem_bytes=%d",
                          field_name(plan->field), plan->n, plan->d, plan->Ds, plan->sentry->D,
                          plan->sentry->DS, plan->metric == BG_METRIC_MOSTLY_MINUS ? "mostly_minus" : "alternating",
                          plan->states_global ? "global" : "shared", plan->S, plan->H, bgk::kStatesWarps,
-                         plan->blocks_per_sm, plan->smem_bytes, plan->sgeo.words, plan->sentry->elem_bytes);
+                         plan->sgeo.P, plan->blocks_per_sm, plan->smem_bytes, plan->sgeo.words, plan->sentry->elem_bytes);
         if (w < 0 || (size_t)w >= len) return fail(BG_ERR_INVALID_ARG, "buffer too small");
         return BG_OK;
     }
@@ -416,7 +461,7 @@ bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
                      field_name(plan->field), plan->n, plan->d, plan->Ds,
                      e->compact ? "compact" : "unrolled", e->D, e->DS,
                      plan->metric == BG_METRIC_MOSTLY_MINUS ? "mostly_minus" : "alternating",
-                     e->global_table ? "global" : "shared", e->block, plan->blocks_per_sm,
+                     e->split ? "split" : e->global_table ? "global" : "shared", e->block, plan->blocks_per_sm,
                      plan->smem_bytes, plan->words, e->elem_bytes);
     if (w < 0 || (size_t)w >= len) return fail(BG_ERR_INVALID_ARG, "buffer too small");
     return BG_OK;
@@ -464,7 +509,8 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const voi
         if (dev != plan->device && plan->smem_bytes > 0) {
             if ((st = bgi::ensure_smem_limit(plan->sentry->func, dev, plan->smem_bytes)) != BG_OK) return st;
         }
-        int64_t blocks = (E + bgk::kStatesWarps - 1) / bgk::kStatesWarps;
+        const int64_t per_block = (int64_t)bgk::kStatesWarps * plan->sgeo.P;
+        int64_t blocks = (E + per_block - 1) / per_block;
         if (blocks > resident_blocks(plan)) blocks = resident_blocks(plan);
         bgk::StatesArgs a;
         a.E = E; a.n = plan->n; a.d_in = plan->d; a.ds_in = plan->Ds;

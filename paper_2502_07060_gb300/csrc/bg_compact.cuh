@@ -64,7 +64,15 @@ struct Geometry {
     __host__ __device__ int off_sa(int D, int DS) const { return off_k(DS) + up4((N + 1) * D); }
     __host__ __device__ int off_inv(int D, int DS) const { return off_sa(D, DS) + ns(); }
     __host__ __device__ int words(int D, int DS) const { return off_inv(D, DS) + ns(); }
+    // split placement: currents in global scratch, the rest (K, SA, 1/P^2) on chip
+    __host__ __device__ int cur_words(int DS) const { return off_k(DS); }
+    __host__ __device__ int aux_words(int D, int DS) const { return words(D, DS) - off_k(DS); }
 };
+
+// Table placements of the compact kernel.
+constexpr int kPlaceShared = 0;     // whole table in shared memory
+constexpr int kPlaceGlobal = 1;     // whole table in global scratch (L2 resident)
+constexpr int kPlaceSplit = 2;      // currents in global scratch, K / SA / 1/P^2 in shared memory
 
 // Vector access to the table.  VEC (F_p): a thread's K-component vector is
 // contiguous ([slot][thread][K]); it is read with 16- or 8-byte accesses, and
@@ -120,9 +128,11 @@ struct TableIO {
 };
 
 // The whole recursion for work item u (point e = u / H, assignment h = u % H)
-// with the block's table at `tab` (shared or global memory).
+// with the block's currents at `tab` and its prefix sums, SA and 1/P^2 at
+// `aux` (shared or global memory).
 template <class F, int D, int DS, int METRIC, int BLOCK>
-__device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typename F::T* tab, int64_t u) {
+__device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typename F::T* tab,
+                                         typename F::T* aux, int64_t u) {
     using T = typename F::T;
     using C = typename F::C;
     using Acc = typename F::A;
@@ -139,9 +149,9 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
     using KIO = TableIO<TK, VEC, BLOCK>;
     const int t = threadIdx.x;
     T* Jr = tab + (VEC ? t * DS : t);                              // currents
-    TK* Kr = reinterpret_cast<TK*>(tab + OFF_K * BLOCK) + (VEC ? t * D : t);   // prefix sums
-    T* Sr = tab + OFF_SA * BLOCK + t;                              // SA per internal range
-    T* Ir = tab + OFF_INV * BLOCK + t;                             // 1/P^2 per internal range
+    TK* Kr = reinterpret_cast<TK*>(aux) + (VEC ? t * D : t);      // prefix sums
+    T* Sr = aux + (OFF_SA - OFF_K) * BLOCK + t;                    // SA per internal range
+    T* Ir = aux + (OFF_INV - OFF_K) * BLOCK + t;                   // 1/P^2 per internal range
     auto jvec = [&](int len, int start) { return IO::template vec<DS>(Jr, g.jbase(len) + start); };
     auto kvec = [&](int i) { return KIO::template vec<D>(Kr, i); };
     const kio_t* kin = static_cast<const kio_t*>(a.k);
@@ -363,27 +373,39 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
     if (a.status != nullptr && h == 0) a.status[e] = singular ? 1 : 0;
 }
 
-template <class F, int D, int DS, int METRIC, int BLOCK, bool GLOBAL_TABLE>
+// bg_point with the whole table at `tab` (one region, as in the batch kernel).
+template <class F, int D, int DS, int METRIC, int BLOCK>
+__device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typename F::T* tab, int64_t u) {
+    bg_point<F, D, DS, METRIC, BLOCK>(f, a, tab, tab + Geometry{a.n - 1}.off_k(DS) * BLOCK, u);
+}
+
+template <class F, int D, int DS, int METRIC, int BLOCK, int PLACE>
 __device__ __forceinline__ void compact_body(const F& f, const CompactArgs& a) {
     using T = typename F::T;
     extern __shared__ __align__(16) unsigned char bg_smem[];
-    T* tab;                                   // this block's table
-    if constexpr (GLOBAL_TABLE) {
-        const int W = Geometry{a.n - 1}.words(D, DS);
-        tab = reinterpret_cast<T*>(a.ws) + static_cast<size_t>(blockIdx.x) * W * BLOCK;
+    const Geometry g{a.n - 1};
+    T* tab;                                   // this block's currents
+    T* aux;                                   // its prefix sums, SA, 1/P^2
+    if constexpr (PLACE == kPlaceGlobal) {
+        tab = reinterpret_cast<T*>(a.ws) + static_cast<size_t>(blockIdx.x) * g.words(D, DS) * BLOCK;
+        aux = tab + g.off_k(DS) * BLOCK;
+    } else if constexpr (PLACE == kPlaceSplit) {
+        tab = reinterpret_cast<T*>(a.ws) + static_cast<size_t>(blockIdx.x) * g.cur_words(DS) * BLOCK;
+        aux = reinterpret_cast<T*>(bg_smem);
     } else {
         tab = reinterpret_cast<T*>(bg_smem);
+        aux = tab + g.off_k(DS) * BLOCK;
     }
     const int64_t total = a.E * a.H;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * BLOCK;
     for (int64_t u = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; u < total; u += stride)
-        bg_point<F, D, DS, METRIC, BLOCK>(f, a, tab, u);
+        bg_point<F, D, DS, METRIC, BLOCK>(f, a, tab, aux, u);
 }
 
-template <class F, int D, int DS, int METRIC, int BLOCK, bool GLOBAL_TABLE>
+template <class F, int D, int DS, int METRIC, int BLOCK, int PLACE>
 __global__ void __launch_bounds__(BLOCK)
 bg_compact_kernel(const F f, const CompactArgs a) {
-    compact_body<F, D, DS, METRIC, BLOCK, GLOBAL_TABLE>(f, a);
+    compact_body<F, D, DS, METRIC, BLOCK, PLACE>(f, a);
 }
 
 }  // namespace bgk

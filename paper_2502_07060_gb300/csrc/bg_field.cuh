@@ -11,6 +11,9 @@
 //   acc2<K>(acc, c1, v1, c2, v2)  acc[0..K) += c1 v1 + c2 v2
 //   finish(acc, inv) -> T[]       J = R / P^2 from the accumulator
 //   amplitude(acc, eps_last)      A = eps_n . R_top
+//   TK, kdot / kkdot / kacc1 / kacc2: the same for momentum components
+//                                 (field elements, complex, or real doubles
+//                                 for physical points in C64ROps)
 //
 // F_p (Sec. 3: p < 2^31, every intermediate reduced mod p).  Montgomery
 // representation with R = 2^32; a value "at level L" is x R^L mod p.
@@ -29,7 +32,7 @@
 //     negated operand (p - a), so every pair is a plain sum.
 // C64 (Sec. 3, complex double): FMA-based complex arithmetic; dot products and
 // accumulations are 4 FP64 FMAs per complex term; the metric sign becomes the
-// sign of an FMA operand.
+// sign of an FMA operand.  C64ROps: real momenta, 2 FMAs per momentum term.
 #pragma once
 #include <cstdint>
 

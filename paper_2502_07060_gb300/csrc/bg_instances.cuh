@@ -19,7 +19,8 @@ struct KernelEntry {
     int field;          // bg_field: 0 = C64, 1 = F_p, 2 = C64 with real momenta
     int n;              // gluons; 0 for the compact kernel (any n)
     int D, DS, metric;
-    bool global_table;  // table in global scratch (true) or shared memory
+    bool global_table;  // (part of the) table in global scratch: the workspace is needed
+    bool split;         // currents in global scratch, the rest in shared memory
     bool compact;       // run-time n (bg_compact_kernel) or unrolled per n
     int block;          // threads per block
     int words;          // table elements per thread (unrolled kernels)
@@ -45,6 +46,7 @@ KernelEntry make_entry() {
     e.DS = DS;
     e.metric = M;
     e.global_table = G;
+    e.split = false;
     e.compact = false;
     e.block = B;
     e.words = Frame<NLEG - 1, D, DS>::WORDS;
@@ -54,13 +56,13 @@ KernelEntry make_entry() {
     return e;
 }
 
-template <class F, int D, int DS, int M, int B, bool G>
+template <class F, int D, int DS, int M, int B, int G>
 void launch_compact(const void* fp, const void* args, dim3 grid, size_t smem, cudaStream_t s) {
     const F& f = *static_cast<const F*>(fp);
     bg_compact_kernel<F, D, DS, M, B, G><<<grid, B, smem, s>>>(f, *static_cast<const CompactArgs*>(args));
 }
 
-template <class F, int D, int DS, int M, int B, bool G>
+template <class F, int D, int DS, int M, int B, int G>
 KernelEntry make_compact() {
     KernelEntry e;
     e.field = F::kField;
@@ -68,7 +70,8 @@ KernelEntry make_compact() {
     e.D = D;
     e.DS = DS;
     e.metric = M;
-    e.global_table = G;
+    e.global_table = G != kPlaceShared;
+    e.split = G == kPlaceSplit;
     e.compact = true;
     e.block = B;
     e.words = 0;
@@ -112,10 +115,11 @@ constexpr int kBlockC64Compact = 64;
 template <class F, int D, int DS, int M>
 void add_compact_dims(std::vector<KernelEntry>& v) {
     if constexpr (F::kIsFp) {
-        v.push_back(make_compact<F, D, DS, M, kBlockFpCompactSmem, false>());
-        v.push_back(make_compact<F, D, DS, M, kBlockFpCompactGlobal, true>());
+        v.push_back(make_compact<F, D, DS, M, kBlockFpCompactSmem, kPlaceShared>());
+        v.push_back(make_compact<F, D, DS, M, kBlockFpCompactGlobal, kPlaceGlobal>());
+        v.push_back(make_compact<F, D, DS, M, kBlockFpCompactGlobal, kPlaceSplit>());
     } else {
-        v.push_back(make_compact<F, D, DS, M, kBlockC64Compact, true>());
+        v.push_back(make_compact<F, D, DS, M, kBlockC64Compact, kPlaceGlobal>());
     }
 }
 

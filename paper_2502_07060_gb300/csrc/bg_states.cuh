@@ -33,8 +33,8 @@
 
 namespace bgk {
 
-constexpr int kStatesMaxLen = 12;           // pw[], cur[] ... indexed by length 0..11
-constexpr int kStatesWarps = 4;             // warps (points in flight) per block
+constexpr int kStatesMaxLegs = 12;          // legs (n <= 12)
+constexpr int kStatesWarps = 4;             // warps per block
 
 // x / d for x < 2^24 by a multiply and a shift (division by an invariant
 // integer, Granlund and Montgomery 1994): magic = ceil(2^k / d) with
@@ -55,40 +55,57 @@ inline DivU make_divu(uint32_t d) {
     return DivU{static_cast<uint32_t>(m), k};
 }
 
-// Table geometry of one point, in table elements (T); host-computed.
+// Table geometry of one point, in table elements (T); host-computed.  Leg l
+// has radix[l] states; range (i, L) = legs i..i+L-1 has W[i][L] versions.
 struct StatesGeometry {
-    int N, S;                        // recursion legs (n - 1), states per leg
-    int pw[kStatesMaxLen];           // S^L, L = 0..N
-    int cur[kStatesMaxLen];          // first element of the currents of length L (L = 1..N-1)
-    int sa[kStatesMaxLen];           // first SA entry of length L (L = 2..N-1)
-    int inv[kStatesMaxLen];          // first 1/P^2 entry of length L (L = 2..N-1), from off_inv
-    int ns;                          // internal ranges
-    int off_inv, off_el, off_k;      // 1/P^2, last leg's states [S][D_s], prefix sums [N+1][D]
-    int words;                       // elements per point
-    DivU div_s;                      // x / S
-    DivU div_pw[kStatesMaxLen];      // x / S^L
+    int N, S;                                    // recursion legs (n - 1); eps slots per leg
+    int P;                                       // points per warp
+    int H;                                       // outputs per point = W[0][N] * radix[N]
+    int radix[kStatesMaxLegs];
+    DivU div_leg[kStatesMaxLegs];                // x / radix[l]
+    int W[kStatesMaxLegs][kStatesMaxLegs + 1];   // W[i][L] = radix[i] ... radix[i+L-1]
+    int cur[kStatesMaxLegs][kStatesMaxLegs];     // [L][i] first element of the currents of (i, L)
+    int sa[kStatesMaxLegs][kStatesMaxLegs];      // [L][i] first SA entry of (i, L), L >= 2
+    int inv[kStatesMaxLegs];                     // [L] first 1/P^2 entry of length L (from off_inv)
+    int count[kStatesMaxLegs + 1];               // [m] (range, version) items of length m
+    int first[kStatesMaxLegs + 1][kStatesMaxLegs + 1];   // [m][i] first item of range i; [m][N-m+1] = count
+    DivU div_count[kStatesMaxLegs + 1];          // x / count[m]
+    int ns;                                      // internal ranges
+    int off_inv, off_el, off_k, off_flag;        // 1/P^2, last leg's states, prefix sums, singular flag
+    int words;                                   // elements per point
 };
 
 inline int states_up4(int x) { return (x + 3) & ~3; }
 
-// elem_t = sizeof(T), elem_k = sizeof(momentum element)
-inline StatesGeometry make_states_geometry(int n, int S, int D, int DS, int elem_t, int elem_k) {
+// radix[0..n): states per leg (1 <= radix[l] <= S); elem_t = sizeof(T),
+// elem_k = sizeof(momentum element)
+inline StatesGeometry make_states_geometry(int n, int S, const int* radix, int D, int DS, int elem_t,
+                                           int elem_k) {
     StatesGeometry g{};
     g.N = n - 1;
     g.S = S;
     const int N = g.N;
-    g.pw[0] = 1;
-    for (int L = 1; L <= N; ++L) g.pw[L] = g.pw[L - 1] * S;
+    for (int l = 0; l < n; ++l) {
+        g.radix[l] = radix[l];
+        g.div_leg[l] = make_divu(radix[l]);
+    }
+    for (int i = 0; i < n; ++i) {
+        g.W[i][0] = 1;
+        for (int L = 1; i + L <= n; ++L) g.W[i][L] = g.W[i][L - 1] * radix[i + L - 1];
+    }
+    g.H = g.W[0][N] * radix[N];
     int off = 0;
-    for (int L = 1; L < N; ++L) {
-        g.cur[L] = off;
-        off += (N - L + 1) * g.pw[L] * DS;
-    }
+    for (int L = 1; L < N; ++L)
+        for (int i = 0; i + L <= N; ++i) {
+            g.cur[L][i] = off;
+            off += g.W[i][L] * DS;
+        }
     off = states_up4(off);
-    for (int L = 2; L < N; ++L) {
-        g.sa[L] = off;
-        off += (N - L + 1) * g.pw[L];
-    }
+    for (int L = 2; L < N; ++L)
+        for (int i = 0; i + L <= N; ++i) {
+            g.sa[L][i] = off;
+            off += g.W[i][L];
+        }
     g.off_inv = states_up4(off);
     int idx = 0;
     for (int L = 2; L < N; ++L) {
@@ -97,11 +114,26 @@ inline StatesGeometry make_states_geometry(int n, int S, int D, int DS, int elem
     }
     g.ns = idx;
     g.off_el = states_up4(g.off_inv + idx);
-    g.off_k = states_up4(g.off_el + S * DS);
+    g.off_k = states_up4(g.off_el + radix[N] * DS);
     const int k_elems = ((N + 1) * D * elem_k + elem_t - 1) / elem_t;
-    g.words = states_up4(g.off_k + k_elems);
-    g.div_s = make_divu(S);
-    for (int L = 0; L <= N; ++L) g.div_pw[L] = make_divu(g.pw[L]);
+    g.off_flag = states_up4(g.off_k + k_elems);
+    g.words = g.off_flag + 4;
+    int maxc = 1;
+    for (int m = 2; m <= N; ++m) {
+        int c = 0;
+        for (int i = 0; i + m <= N; ++i) {
+            g.first[m][i] = c;
+            c += g.W[i][m];
+        }
+        g.first[m][N - m + 1] = c;
+        g.count[m] = c;
+        g.div_count[m] = make_divu(c);
+        if (c > maxc) maxc = c;
+    }
+    // points per warp: enough (point, item) pairs of the top length to fill the lanes
+    g.P = 32 / g.count[N];
+    if (g.P < 1) g.P = 1;
+    (void)maxc;
     return g;
 }
 
@@ -110,15 +142,16 @@ struct StatesArgs {
     int n, d_in, ds_in;
     const void* k;              // [E][n][d_in]
     const void* eps;            // [E][n][S][ds_in]
-    void* out;                  // [E][S^n]
+    void* out;                  // [E][H]
     uint8_t* status;            // [E] or null
     void* ws;                   // global tables (global placement) or null
 };
 
-// All S^n assignments of point e by the warp whose table is `tab`.
-template <class F, int D, int DS, int METRIC>
-__device__ __forceinline__ void states_point(const F& f, const StatesArgs& a, const StatesGeometry& g,
-                                             typename F::T* tab, int64_t e, int lane) {
+// The assignments of the points e0 .. e0+np-1 (np <= P) by one warp; point p's
+// table is tab + p * words.
+template <class F, int D, int DS, int METRIC, bool UNIFORM>
+__device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, const StatesGeometry& g,
+                                             typename F::T* tab, int64_t e0, int np, int lane) {
     using T = typename F::T;
     using C = typename F::C;
     using Acc = typename F::A;
@@ -127,72 +160,91 @@ __device__ __forceinline__ void states_point(const F& f, const StatesArgs& a, co
     using kio_t = typename F::kio_t;
     using IO = TableIO<T, F::kIsFp, 1>;         // contiguous vectors
     using KIO = TableIO<TK, F::kIsFp, 1>;
-    const int N = g.N, S = g.S, n = N + 1;
-    TK* Kr = reinterpret_cast<TK*>(tab + g.off_k);
-    const T* Y = tab + g.off_inv;
-    const T* EL = tab + g.off_el;
-    auto cur = [&](int len, int start, uint32_t ver) {
-        return tab + g.cur[len] + (start * g.pw[len] + static_cast<int>(ver)) * DS;
+    const int N = g.N, S = g.S, n = N + 1, W = g.words;
+    // every leg with the same number of states: one divisor and W[i][L] = S^L
+    // for every i (loop-invariant constants)
+    auto divl = [&](int leg) -> const DivU& {
+        if constexpr (UNIFORM) return g.div_leg[0];
+        else return g.div_leg[leg];
     };
-    auto sav = [&](int len, int start, uint32_t ver) {
-        return tab[g.sa[len] + start * g.pw[len] + static_cast<int>(ver)];
+    auto wv = [&](int i, int L) -> uint32_t {
+        if constexpr (UNIFORM) return static_cast<uint32_t>(g.W[0][L]);
+        else return static_cast<uint32_t>(g.W[i][L]);
     };
+    auto kr = [&](int p) { return reinterpret_cast<TK*>(tab + p * W + g.off_k); };
+    auto flag = [&](int p) { return reinterpret_cast<int*>(tab + p * W + g.off_flag); };
 
-    // s1: prefix sums K_0 = 0, K_{l+1} = K_l + k_l, one lane per component
-    if (lane < D) {
-        const kio_t* kp = static_cast<const kio_t*>(a.k) + e * n * a.d_in;
+    // s1: prefix sums K_0 = 0, K_{l+1} = K_l + k_l, one lane per (point, component)
+    for (int x = lane; x < np * D; x += 32) {
+        const int p = x / D, mu = x - p * D;
+        const kio_t* kp = static_cast<const kio_t*>(a.k) + (e0 + p) * n * a.d_in;
+        TK* Kr = kr(p);
         TK acc = f.kzero();
-        Kr[lane] = acc;
+        Kr[mu] = acc;
         for (int l = 0; l < N; ++l) {
-            if (lane < a.d_in) acc = f.kadd(acc, f.kfrom_io(kp[l * a.d_in + lane]));
-            Kr[(l + 1) * D + lane] = acc;
+            if (mu < a.d_in) acc = f.kadd(acc, f.kfrom_io(kp[l * a.d_in + mu]));
+            Kr[(l + 1) * D + mu] = acc;
         }
     }
-    // s2: polarisations -> currents of length 1 (version = state) and the
-    // last leg's states
+    // s2: polarisations -> currents of length 1 (version = state) and the last
+    // leg's states; singular flags cleared
     {
-        const io_t* ep = static_cast<const io_t*>(a.eps) + e * n * S * a.ds_in;
-        const int total = n * S * DS;
-        for (int x = lane; x < total; x += 32) {
-            const int mu = x % DS;
-            const int ls = x / DS;                 // l * S + t
+        const int per = n * S * DS;
+        for (int x = lane; x < np * per; x += 32) {
+            const int p = x / per, y = x - p * per;
+            const int mu = y % DS;
+            const int ls = y / DS;                 // l * S + t
+            const int l = ls / S, t = ls - l * S;
+            if (t >= g.radix[l]) continue;
+            const io_t* ep = static_cast<const io_t*>(a.eps) + (e0 + p) * n * S * a.ds_in;
             const T v = mu < a.ds_in ? f.from_io(ep[ls * a.ds_in + mu]) : f.zero();
-            if (ls < N * S) tab[g.cur[1] + x] = v;
-            else tab[g.off_el + (x - N * S * DS)] = v;
+            T* tp = tab + p * W;
+            if (l < N) tp[g.cur[1][l] + t * DS + mu] = v;
+            else tp[g.off_el + t * DS + mu] = v;
         }
+        for (int p = lane; p < np; p += 32) *flag(p) = 0;
     }
     __threadfence_block();
     __syncwarp();
-    // s3: 1/P^2 of every internal range, one lane per range
-    bool sing = false;
-    for (int r = lane; r < g.ns; r += 32) {
+    // s3: 1/P^2 of every internal range, one lane per (point, range)
+    for (int x = lane; x < np * g.ns; x += 32) {
+        const int p = x / g.ns, r = x - p * g.ns;
         int L = 2, i = r;
         while (i >= N - L + 1) {
             i -= N - L + 1;
             ++L;
         }
-        TK Ka[D], Kb[D], P[D];
+        const TK* Kr = kr(p);
+        TK Ka[D], Kb[D], Pv[D];
         KIO::template load<D>(Kr + i * D, Ka);
         KIO::template load<D>(Kr + (i + L) * D, Kb);
 #pragma unroll
-        for (int mu = 0; mu < D; ++mu) P[mu] = f.ksub(Kb[mu], Ka[mu]);
-        const T x = f.inv_input(f.template kkdot<D, METRIC>(P, P));
-        sing |= f.is_zero(x);
-        tab[g.off_inv + r] = f.inv_store(f.inv_scalar(x));
+        for (int mu = 0; mu < D; ++mu) Pv[mu] = f.ksub(Kb[mu], Ka[mu]);
+        const T xv = f.inv_input(f.template kkdot<D, METRIC>(Pv, Pv));
+        if (f.is_zero(xv)) *flag(p) = 1;
+        tab[p * W + g.off_inv + r] = f.inv_store(f.inv_scalar(xv));
     }
-    const bool singular = __any_sync(0xffffffffu, sing);
     __threadfence_block();
     __syncwarp();
 
-    // s4: the recursion by length; items (range start i, version sigma)
+    // s4: the recursion by length; items (point, range start i, version sigma)
     io_t* out = static_cast<io_t*>(a.out);
-    const int64_t H = static_cast<int64_t>(g.pw[N]) * S;
     for (int m = 2; m <= N; ++m) {
-        const int nver = g.pw[m];
-        const int count = (N - m + 1) * nver;
-        for (int it = lane; it < count; it += 32) {
-            const int i = static_cast<int>(g.div_pw[m].div(static_cast<uint32_t>(it)));
-            const uint32_t sig = static_cast<uint32_t>(it - i * nver);
+        const int count = g.count[m];
+        for (int x = lane; x < np * count; x += 32) {
+            const int p = static_cast<int>(g.div_count[m].div(static_cast<uint32_t>(x)));
+            const int it = x - p * count;
+            int i = 0;
+            while (it >= g.first[m][i + 1]) ++i;
+            const uint32_t sig = static_cast<uint32_t>(it - g.first[m][i]);
+            T* tp = tab + p * W;
+            const TK* Kr = kr(p);
+            auto cur = [&](int len, int start, uint32_t ver) {
+                return tp + g.cur[len][start] + static_cast<int>(ver) * DS;
+            };
+            auto sav = [&](int len, int start, uint32_t ver) {
+                return tp[g.sa[len][start] + static_cast<int>(ver)];
+            };
             TK Ki[D], Kj[D];
             KIO::template load<D>(Kr + i * D, Ki);
             KIO::template load<D>(Kr + (i + m) * D, Kj);
@@ -202,11 +254,11 @@ __device__ __forceinline__ void states_point(const F& f, const StatesArgs& a, co
             C mom_c = f.czero();
             TK mom_v[D];
             bool mom_pending = false;
-            uint32_t qB = sig;                  // sigma / S^(b+1): version of the suffix
+            uint32_t qB = sig;                  // sigma / W[i][b+1]: version of the suffix
             for (int b = 0; b < m - 1; ++b) {
                 const int lenA = b + 1, lenB = m - 1 - b;
-                qB = g.div_s.div(qB);
-                const uint32_t sA = sig - qB * static_cast<uint32_t>(g.pw[lenA]);
+                qB = divl(i + b).div(qB);
+                const uint32_t sA = sig - qB * wv(i, lenA);
                 T pb[DS], sf[DS];
                 TK Kt[D], PA[D], PB[D];
                 IO::template load<DS>(cur(lenA, i, sA), pb);
@@ -236,28 +288,28 @@ __device__ __forceinline__ void states_point(const F& f, const StatesArgs& a, co
                     mom_pending = true;
                 }
                 // four-gluon vertex: prefix [i, i+q], inner [i+q+1, i+b], suffix sf;
-                // Q = sigma / S^(q+1), prefix version sigma - Q S^(q+1), inner
-                // version Q - qB S^(b-q)
+                // Q = sigma / W[i][q+1], prefix version sigma - Q W[i][q+1],
+                // inner version Q - qB W[i+q+1][b-q]
                 uint32_t Q = sig;
                 int q = 0;
                 for (; q + 1 < b; q += 2) {
-                    const uint32_t Q0 = g.div_s.div(Q);
-                    const uint32_t Q1 = g.div_s.div(Q0);
+                    const uint32_t Q0 = divl(i + q).div(Q);
+                    const uint32_t Q1 = divl(i + q + 1).div(Q0);
                     Q = Q1;
                     T pa0[DS], pa1[DS], in0[DS], in1[DS];
-                    IO::template load<DS>(cur(q + 1, i, sig - Q0 * static_cast<uint32_t>(g.pw[q + 1])), pa0);
-                    IO::template load<DS>(cur(b - q, i + q + 1, Q0 - qB * static_cast<uint32_t>(g.pw[b - q])), in0);
-                    IO::template load<DS>(cur(q + 2, i, sig - Q1 * static_cast<uint32_t>(g.pw[q + 2])), pa1);
-                    IO::template load<DS>(cur(b - q - 1, i + q + 2, Q1 - qB * static_cast<uint32_t>(g.pw[b - q - 1])), in1);
+                    IO::template load<DS>(cur(q + 1, i, sig - Q0 * wv(i, q + 1)), pa0);
+                    IO::template load<DS>(cur(b - q, i + q + 1, Q0 - qB * wv(i + q + 1, b - q)), in0);
+                    IO::template load<DS>(cur(q + 2, i, sig - Q1 * wv(i, q + 2)), pa1);
+                    IO::template load<DS>(cur(b - q - 1, i + q + 2, Q1 - qB * wv(i + q + 2, b - q - 1)), in1);
                     const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
                     const C g1 = f.cdbl(f.template dot<DS, METRIC>(pa1, sf));
                     f.template acc2<DS>(acc, g0, in0, g1, in1);
                 }
                 if (q < b) {
-                    const uint32_t Q0 = g.div_s.div(Q);
+                    const uint32_t Q0 = divl(i + q).div(Q);
                     T pa0[DS], in0[DS];
-                    IO::template load<DS>(cur(q + 1, i, sig - Q0 * static_cast<uint32_t>(g.pw[q + 1])), pa0);
-                    IO::template load<DS>(cur(b - q, i + q + 1, Q0 - qB * static_cast<uint32_t>(g.pw[b - q])), in0);
+                    IO::template load<DS>(cur(q + 1, i, sig - Q0 * wv(i, q + 1)), pa0);
+                    IO::template load<DS>(cur(b - q, i + q + 1, Q0 - qB * wv(i + q + 1, b - q)), in0);
                     const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
                     f.template acc1<DS>(acc, g0, in0);
                 }
@@ -271,37 +323,43 @@ __device__ __forceinline__ void states_point(const F& f, const StatesArgs& a, co
             }
             if (m < N) {
                 T J[DS];
-                f.template finish<DS>(acc, Y[g.inv[m] + i], J);
-                IO::template store<DS>(tab + g.cur[m] + it * DS, J);
-                tab[g.sa[m] + it] = f.c_to_t(sa);
+                f.template finish<DS>(acc, tp[g.off_inv + g.inv[m] + i], J);
+                IO::template store<DS>(cur(m, i, sig), J);
+                tp[g.sa[m][i] + static_cast<int>(sig)] = f.c_to_t(sa);
             } else {
                 // the top range: contract with each state of the last leg
-                io_t* o = out + e * H + sig;
-                for (int t = 0; t < S; ++t) {
+                const bool singular = *flag(p) != 0;
+                io_t* o = out + (e0 + p) * g.H + sig;
+                for (int t = 0; t < g.radix[N]; ++t) {
                     T eL[DS];
-                    IO::template load<DS>(EL + t * DS, eL);
-                    o[static_cast<int64_t>(t) * nver] = singular ? f.zero_io()
-                                                                 : f.template amplitude<DS, METRIC>(acc, eL);
+                    IO::template load<DS>(tp + g.off_el + t * DS, eL);
+                    o[static_cast<int64_t>(t) * count] = singular ? f.zero_io()
+                                                                  : f.template amplitude<DS, METRIC>(acc, eL);
                 }
             }
         }
         __threadfence_block();
         __syncwarp();
     }
-    if (lane == 0 && a.status != nullptr) a.status[e] = singular ? 1 : 0;
+    if (a.status != nullptr)
+        for (int p = lane; p < np; p += 32) a.status[e0 + p] = *flag(p) ? 1 : 0;
+    __syncwarp();
 }
 
-template <class F, int D, int DS, int METRIC>
+template <class F, int D, int DS, int METRIC, bool UNIFORM>
 __global__ void __launch_bounds__(32 * kStatesWarps)
 bg_states_kernel(const F f, const StatesArgs a, const StatesGeometry g) {
     using T = typename F::T;
     extern __shared__ __align__(16) unsigned char bg_states_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t slot = static_cast<int64_t>(blockIdx.x) * kStatesWarps + warp;
-    T* tab = a.ws != nullptr ? reinterpret_cast<T*>(a.ws) + slot * g.words
-                             : reinterpret_cast<T*>(bg_states_smem) + warp * g.words;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * kStatesWarps;
-    for (int64_t e = slot; e < a.E; e += stride) states_point<F, D, DS, METRIC>(f, a, g, tab, e, lane);
+    T* tab = a.ws != nullptr ? reinterpret_cast<T*>(a.ws) + slot * g.P * g.words
+                             : reinterpret_cast<T*>(bg_states_smem) + warp * g.P * g.words;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kStatesWarps * g.P;
+    for (int64_t e0 = slot * g.P; e0 < a.E; e0 += stride) {
+        const int np = a.E - e0 < g.P ? static_cast<int>(a.E - e0) : g.P;
+        states_group<F, D, DS, METRIC, UNIFORM>(f, a, g, tab, e0, np, lane);
+    }
 }
 
 }  // namespace bgk
@@ -311,36 +369,40 @@ namespace bgk {
 // Registry row of a states kernel (one per field, D, D_s, metric).
 struct StatesEntry {
     int field, D, DS, metric;
+    bool uniform;                     // every leg with the same number of states
     int elem_bytes, elem_k_bytes;     // sizeof(T), sizeof(momentum element)
     const void* func;
     void (*launch)(const void* field_params, const StatesArgs& a, const StatesGeometry& g, dim3 grid,
                    size_t smem, cudaStream_t stream);
 };
 
-template <class F, int D, int DS, int M>
+template <class F, int D, int DS, int M, bool U>
 void launch_states(const void* fp, const StatesArgs& a, const StatesGeometry& g, dim3 grid, size_t smem,
                    cudaStream_t s) {
-    bg_states_kernel<F, D, DS, M><<<grid, 32 * kStatesWarps, smem, s>>>(*static_cast<const F*>(fp), a, g);
+    bg_states_kernel<F, D, DS, M, U><<<grid, 32 * kStatesWarps, smem, s>>>(*static_cast<const F*>(fp), a, g);
 }
 
-template <class F, int D, int DS, int M>
+template <class F, int D, int DS, int M, bool U>
 StatesEntry make_states() {
     StatesEntry e;
     e.field = F::kField;
     e.D = D;
     e.DS = DS;
     e.metric = M;
+    e.uniform = U;
     e.elem_bytes = sizeof(typename F::T);
     e.elem_k_bytes = sizeof(typename F::TK);
-    e.func = reinterpret_cast<const void*>(&bg_states_kernel<F, D, DS, M>);
-    e.launch = &launch_states<F, D, DS, M>;
+    e.func = reinterpret_cast<const void*>(&bg_states_kernel<F, D, DS, M, U>);
+    e.launch = &launch_states<F, D, DS, M, U>;
     return e;
 }
 
 template <class F, int D, int DS>
 void register_states(std::vector<StatesEntry>& v) {
-    v.push_back(make_states<F, D, DS, 0>());
-    v.push_back(make_states<F, D, DS, 1>());
+    v.push_back(make_states<F, D, DS, 0, true>());
+    v.push_back(make_states<F, D, DS, 1, true>());
+    v.push_back(make_states<F, D, DS, 0, false>());
+    v.push_back(make_states<F, D, DS, 1, false>());
 }
 
 }  // namespace bgk

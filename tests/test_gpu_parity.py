@@ -100,14 +100,24 @@ def test_fp_bit_exact(n, d, Ds, metric, p):
 
 
 @pytest.mark.parametrize("n", [5, 8, 9, 12])
-@pytest.mark.parametrize("table", ["shared", "global"])
+@pytest.mark.parametrize("table", ["shared", "global", "split"])
 def test_fp_table_placements_agree(n, table):
     E = 1000
     k, eps = G.fp_batch(7 + n, E, n, 6, 6, P, 0)
     ref, _ = C.amp_fp(k, eps, P, 0)
     out, _, plan = run_fp(k, eps, P, 0, table=table)
-    assert ("table=global" in plan.describe()) == (table == "global")
+    assert f"table={table}" in plan.describe()
     assert np.array_equal(out, ref)
+
+
+@pytest.mark.parametrize("n,d,Ds,metric,p", [(8, 4, 8, 1, PM), (10, 8, 8, 0, P), (6, 6, 6, 1, PM)])
+def test_fp_split_placement_bit_exact(n, d, Ds, metric, p):
+    E = 3 * 128 + 37
+    k, eps = G.fp_batch(500 + n, E, n, d, Ds, p, metric)
+    ref, rst = C.amp_fp(k, eps, p, metric)
+    out, st, plan = run_fp(k, eps, p, metric, table="split")
+    assert "table=split" in plan.describe()
+    assert np.array_equal(st, rst) and np.array_equal(out, ref)
 
 
 @pytest.mark.parametrize("n,d,metric", [(5, 4, 0), (6, 6, 1), (7, 8, 0), (8, 6, 0), (8, 4, 1)])
