@@ -673,9 +673,11 @@ def main():
     peaks = read_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0) or 2070.0
     n_sm = torch.cuda.get_device_properties(device).multi_processor_count
-    # F_p roofline: integer-multiply pipe, 64 IMAD per SM per clock, three
-    # multiply instructions per Montgomery multiplication.
-    peak_mulmod = n_sm * 64 * sm_max * 1e6 / 3
+    # F_p roofline: one 32x32 -> 64-bit product per field multiplication
+    # (reductions free), at the rate of the 64-bit multiply-add: 32 per SM per
+    # clock, half the 64-lane 32-bit IMAD rate (measured: mul.hi 30/clk/SM,
+    # four-product accumulation 27 field multiplications/clk/SM).
+    peak_mulmod = n_sm * 32 * sm_max * 1e6
     achieved = fp["value_per_rank"] * tally
     c64_flops = 6 * tally + 2 * 5348
     peak_fp64 = n_sm * 2 * 2 * sm_max * 1e6
@@ -697,8 +699,9 @@ def main():
                      "traffic": None if traffic_fp is None else traffic_fp * scale,
                      "ops_per_unit": tally, "kernel_ops_per_unit": kops,
                      "frac_kernel_ops": fp["value_per_rank"] * kops / peak_mulmod,
-                     "peak_derivation": f"{n_sm} SMs x 64 IMAD/clk x {sm_max:.0f} MHz / 3 IMAD per "
-                                        f"Montgomery multiplication (derived; measured IMAD rate 61-63/clk/SM)",
+                     "peak_derivation": f"{n_sm} SMs x 32 64-bit products/clk x {sm_max:.0f} MHz, one product "
+                                        f"per field multiplication (derived from the IMAD unit: 64 lanes/clk, 64-bit "
+                                        f"results at half rate; measured 27/clk/SM for the kernel's accumulation)",
                      "traffic_source": "profiles/fp_compact_n8_d6.md, ncu capture of 2^19 points "
                                        "scaled by the point count"},
         "c64": None if c64 is None else {

@@ -127,6 +127,13 @@ struct TableIO {
     }
 };
 
+// Inputs and outputs are touched once per point: streaming (evict-first)
+// accesses keep them from displacing the recursion table in L1 and L2.
+template <class X>
+__device__ __forceinline__ X ld_once(const X* p) { return __ldcs(p); }
+template <class X>
+__device__ __forceinline__ void st_once(X* p, X v) { __stcs(p, v); }
+
 // The whole recursion for work item u (point e = u / H, assignment h = u % H)
 // with the block's currents at `tab` and its prefix sums, SA and 1/P^2 at
 // `aux` (shared or global memory).
@@ -176,7 +183,7 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
         for (int l = 0; l < N; ++l) {
 #pragma unroll
             for (int mu = 0; mu < D; ++mu)
-                if (mu < a.d_in) Kacc[mu] = f.kadd(Kacc[mu], f.kfrom_io(kp[l * a.d_in + mu]));
+                if (mu < a.d_in) Kacc[mu] = f.kadd(Kacc[mu], f.kfrom_io(ld_once(kp + l * a.d_in + mu)));
             KIO::template store<D>(kvec(l + 1), Kacc);
         }
     }
@@ -187,7 +194,7 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
         const io_t* ep = ein + ((e * NLEG + l) * a.S + s) * a.ds_in;
         T v[DS];
 #pragma unroll
-        for (int mu = 0; mu < DS; ++mu) v[mu] = (mu < a.ds_in) ? f.from_io(ep[mu]) : f.zero();
+        for (int mu = 0; mu < DS; ++mu) v[mu] = (mu < a.ds_in) ? f.from_io(ld_once(ep + mu)) : f.zero();
         if (l < N) {
             IO::template store<DS>(jvec(1, l), v);     // current (1, l)
         } else {
@@ -369,7 +376,7 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
             }
         }
     }
-    out[u] = singular ? f.zero_io() : result;
+    st_once(out + u, singular ? f.zero_io() : result);
     if (a.status != nullptr && h == 0) a.status[e] = singular ? 1 : 0;
 }
 
