@@ -411,17 +411,19 @@ def mixed_workload(args, device):
 def helicity_workload(args, device):
     """All 2^n helicity assignments (n = 6..10, d = D_s = 4, two states per
     leg): F_p at p = 2^31 - 1 in the alternating metric and complex FP64 on
-    physical points (real momenta).  Times the all-assignment plan (shared
-    sub-currents) against the same assignments as an explicit table (one full
-    recursion per assignment)."""
+    physical points (real momenta), 2^20 points per n.  Times the
+    all-assignment plan (shared sub-currents) on the full batch, and the same
+    assignments as an explicit table (one full recursion per assignment) on
+    the first 2^18 (F_p) / 2^15 (complex) points of it."""
     import torch
     from paper_2502_07060_gb300 import bg
     res = []
     steps = 3
+    E = 1 << args.log2_points_helicity
     for field in ("fp", "c64"):
+        E_cmp = min(E, 1 << (18 if field == "fp" else 15))
         for n in range(6, 11):
             H = 1 << n
-            E = 1 << (args.log2_points_helicity if field == "fp" else args.log2_points_helicity - 3)
             table = np.array([[(h >> l) & 1 for l in range(n)] for h in range(H)], dtype=np.uint8)
             if field == "fp":
                 k, e = G.fp_batch(4000 + n, E, n, 4, 4, G.P_MERSENNE, 1, S=2)
@@ -437,22 +439,126 @@ def helicity_workload(args, device):
             out = torch.empty((E, H), dtype=ed.dtype, device=device)
             st = torch.empty(E, dtype=torch.uint8, device=device)
             stream = torch.cuda.current_stream(device)
-            row = {"field": field, "n": n, "points": E, "assignments": H}
-            for mode, a in (("shared_currents", "all"), ("per_assignment", table)):
+            row = {"field": field, "n": n, "points": E, "points_per_assignment_run": E_cmp,
+                   "assignments": H}
+            for mode, a, m in (("shared_currents", "all", E), ("per_assignment", table, E_cmp)):
                 plan = mk(a)
-                ws = plan.workspace(E, device)
-                ms = time_steps(lambda: plan.eval(kd, ed, out=out, status=st, workspace=ws, stream=stream),
+                ws = plan.workspace(m, device)
+                kv, ev, ov, sv = kd[:m], ed[:m], out[:m], st[:m]
+                ms = time_steps(lambda: plan.eval(kv, ev, out=ov, status=sv, workspace=ws, stream=stream),
                                 steps, args.warmup, stream, None, device)
-                row[mode] = {"ms_per_step": ms / steps, "value": E * H / (ms / steps / 1e3),
+                row[mode] = {"ms_per_step": ms / steps, "value": m * H / (ms / steps / 1e3),
                              "plan": plan.describe()}
                 del plan, ws
             row["speedup"] = row["shared_currents"]["value"] / row["per_assignment"]["value"]
             res.append(row)
             del kd, ed, out, st
             torch.cuda.empty_cache()
-    return {"workload": "all 2^n helicity assignments, n = 6..10, d = D_s = 4, S = 2 states per leg; "
-                        "F_p p = 2^31-1 (alternating metric) and complex FP64 with real momenta",
+    return {"workload": "all 2^n helicity assignments, n = 6..10, d = D_s = 4, S = 2 states per leg, "
+                        f"{E} points per n; F_p p = 2^31-1 (alternating metric) and complex FP64 with "
+                        "real momenta",
             "unit": "amplitudes/s", "steps": steps, "rows": res}
+
+
+def sweep_workload(args, device):
+    """Scaling of one bg_eval launch, the analogues of the paper's benchmark
+    figures (Sec. 3.2): time against the number of points E = 2^10..2^22 at
+    n = 8, d = D_s = 6 (Fig. 1b: flat until the GPU saturates, then linear);
+    against the number of gluons n = 4..12 at d = D_s = 8 (Fig. 1a); against
+    the dimension d = D_s = 4..8 at n = 6 and 9 (Fig. 2).  F_p at p = 2^31 - 19
+    and complex FP64 with real momenta (physical points), mostly-minus metric.
+    Each entry: 3 warm-up calls, then CUDA-event timing of enough calls to
+    cover 50 ms (at least 3)."""
+    import torch
+    from paper_2502_07060_gb300 import bg
+    stream = torch.cuda.current_stream(device)
+
+    def inputs(field, seed, E, n, d):
+        if field == "fp":
+            k, e = G.fp_batch(seed, E, n, d, d, P, 0)
+            plan = bg.Plan(n, d, d, bg.FIELD_FP, P, bg.MOSTLY_MINUS)
+            return plan, torch.from_numpy(k.view(np.int32)).to(device), torch.from_numpy(e.view(np.int32)).to(device)
+        k, e = G.c64_batch(seed, E, n, d, d, 0)
+        plan = bg.Plan(n, d, d, bg.FIELD_C64_REAL, 0, bg.MOSTLY_MINUS)
+        return (plan, torch.from_numpy(np.ascontiguousarray(k.real)).to(device),
+                torch.from_numpy(e).to(device))
+
+    def measure(plan, kd, ed, E):
+        out = torch.empty(E, dtype=ed.dtype, device=device)
+        st = torch.empty(E, dtype=torch.uint8, device=device)
+        ws = plan.workspace(E, device)
+        kv, ev = kd[:E], ed[:E]
+        step = lambda: plan.eval(kv, ev, out=out, status=st, workspace=ws, stream=stream)
+        one = time_steps(step, 1, 3, stream, None, device)
+        reps = int(min(200, max(3, np.ceil(50.0 / max(one, 1e-3)))))
+        ms = time_steps(step, reps, 1, stream, None, device) / reps
+        return {"E": E, "ms_per_call": ms, "amplitudes_per_s": E / (ms / 1e3), "calls": reps}
+
+    res = {"E_sweep": [], "n_sweep": [], "d_sweep": []}
+    for field, top in (("fp", 22), ("c64", 20)):
+        plan, kd, ed = inputs(field, 5100, 1 << top, 8, 6)
+        for lg in range(10, top + 1):
+            res["E_sweep"].append(dict(field=field, n=8, d=6, **measure(plan, kd, ed, 1 << lg)))
+        del kd, ed
+        torch.cuda.empty_cache()
+    for field, lg in (("fp", 20), ("c64", 17)):
+        for n in range(4, 13):
+            plan, kd, ed = inputs(field, 5200 + n, 1 << lg, n, 8)
+            res["n_sweep"].append(dict(field=field, n=n, d=8, **measure(plan, kd, ed, 1 << lg)))
+        for n in (6, 9):
+            for d in range(4, 9):
+                plan, kd, ed = inputs(field, 5300 + 10 * n + d, 1 << lg, n, d)
+                res["d_sweep"].append(dict(field=field, n=n, d=d, **measure(plan, kd, ed, 1 << lg)))
+        torch.cuda.empty_cache()
+    return {"workload": "one bg_eval launch: E = 2^10..2^22 at n=8 d=6; n = 4..12 at d = D_s = 8; "
+                        "d = D_s = 4..8 at n = 6, 9; F_p (p = 2^31-19) and complex FP64 (real momenta)",
+            "unit": "amplitudes/s", **res}
+
+
+def fourdim_workload(args, device):
+    """Trees of a one-loop cut (Sec. 2.3): legs 0 and n-1 d-dimensional, legs
+    1..n-2 four-dimensional states zero-padded into d dimensions.  Times the
+    ordinary plan against the mixed-dimension plan (bg_plan_create_mixed,
+    currents of four-dimensional ranges with four components) on the same
+    inputs: n = 6, 8, 10, 12, d = D_s = 6 and 8, F_p (2^20 points) and
+    complex FP64 with real momenta (2^17 points)."""
+    import torch
+    from paper_2502_07060_gb300 import bg
+    stream = torch.cuda.current_stream(device)
+    rows = []
+    for field, lg in (("fp", 20), ("c64", 17)):
+        E = 1 << lg
+        for d in (6, 8):
+            for n in (6, 8, 10, 12):
+                mask = ((1 << (n - 1)) - 1) & ~1
+                if field == "fp":
+                    k, e = G.fp_batch(6000 + 10 * n + d, E, n, d, d, P, 0, four_d=mask)
+                    kd = torch.from_numpy(k.view(np.int32)).to(device)
+                    ed = torch.from_numpy(e.view(np.int32)).to(device)
+                    fld, p = bg.FIELD_FP, P
+                else:
+                    k, e = G.c64_batch(6000 + 10 * n + d, E, n, d, d, 0, four_d=mask)
+                    kd = torch.from_numpy(np.ascontiguousarray(k.real)).to(device)
+                    ed = torch.from_numpy(e).to(device)
+                    fld, p = bg.FIELD_C64_REAL, 0
+                del k, e
+                out = torch.empty(E, dtype=ed.dtype, device=device)
+                st = torch.empty(E, dtype=torch.uint8, device=device)
+                row = {"field": field, "n": n, "d": d, "points": E, "four_dim_legs": mask}
+                for mode, m in (("plain", None), ("mixed", mask)):
+                    plan = bg.Plan(n, d, d, fld, p, bg.MOSTLY_MINUS, four_dim_legs=m)
+                    ws = plan.workspace(E, device)
+                    step = lambda: plan.eval(kd, ed, out=out, status=st, workspace=ws, stream=stream)
+                    ms = time_steps(step, 10, args.warmup, stream, None, device) / 10
+                    row[mode] = {"ms_per_call": ms, "value": E / (ms / 1e3), "plan": plan.describe()}
+                    del plan, ws
+                row["speedup"] = row["mixed"]["value"] / row["plain"]["value"]
+                rows.append(row)
+                del kd, ed, out, st
+                torch.cuda.empty_cache()
+    return {"workload": "cut trees: legs 1..n-2 four-dimensional, n = 6..12, d = D_s in {6, 8}; ordinary "
+                        "plan against the mixed-dimension plan on the same inputs",
+            "unit": "amplitudes/s", "rows": rows}
 
 
 def serve_workload(args, device):
@@ -584,12 +690,15 @@ def main():
                     help="comma list of fp, c64 (real momenta, the physical points), c64c (the same "
                          "points through the complex-momentum plan)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
-    ap.add_argument("--workload", choices=["metric", "mixed", "serve", "helicity"], default="metric",
+    ap.add_argument("--workload", choices=["metric", "mixed", "serve", "helicity", "sweep", "fourdim"],
+                    default="metric",
                     help="metric: n=8 d=6 headline line; mixed: uneven-batch comparison; "
                          "serve: p50/p99 latency of the request server; helicity: all 2^n "
-                         "helicities with shared sub-currents against one recursion per assignment")
-    ap.add_argument("--log2-points-helicity", type=int, default=18,
-                    help="F_p points per n of the helicity workload (complex: 8x fewer)")
+                         "helicities with shared sub-currents against one recursion per assignment; "
+                         "sweep: time against points, gluons and dimension; fourdim: cut trees with "
+                         "four-dimensional legs, ordinary against mixed-dimension plans")
+    ap.add_argument("--log2-points-helicity", type=int, default=20,
+                    help="points per n of the helicity workload")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args()
@@ -644,6 +753,14 @@ def main():
     if args.workload == "helicity":
         if rank == 0:
             print(json.dumps({"metric": METRIC, "helicity": helicity_workload(args, device)}))
+        return
+    if args.workload == "fourdim":
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "fourdim": fourdim_workload(args, device)}))
+        return
+    if args.workload == "sweep":
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "sweep": sweep_workload(args, device)}))
         return
     if args.workload == "serve":
         if rank == 0:

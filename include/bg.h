@@ -123,6 +123,31 @@ bg_status bg_plan_create_product(int n, int d, int D_s, bg_field field, uint32_t
                                  bg_metric metric, int n_states,
                                  const uint8_t* states_per_leg, bg_plan** out);
 
+/*
+ * bg_plan_create_mixed -- a plan whose legs are partly four-dimensional: the
+ * loop-level situation of Sec. 2.3, where only some external states are
+ * d-dimensional and the others are four-dimensional states zero-padded into
+ * d (resp. D_s) dimensions.  Bit l of four_dim_legs marks leg l (array index
+ * l) as four-dimensional: its momentum components 4..d-1 and polarisation
+ * components 4..D_s-1 are zero (precondition, not checked on the device).
+ * A current whose range holds only such legs lies in the first four
+ * components (the vertices of Sec. 2.2 combine currents and momenta
+ * linearly), so it is computed with four components instead of D_s -- the
+ * specialised four-dimensional recursion the paper leaves for future work.
+ * The values are those bg_plan_create gives on the same inputs (identical
+ * over F_p: only products with exact zeros are skipped).
+ *   four_dim_legs  bits 0..n-1 (higher bits: BG_ERR_INVALID_ARG); 0 gives the
+ *                  ordinary plan
+ *   assign         an explicit [H][n] table or NULL with H == 1; the
+ *                  all-assignment form (NULL with H > 1) is BG_ERR_UNSUPPORTED
+ * Other arguments and errors as bg_plan_create.  bg_batch_* evaluates such a
+ * plan at full width (same values).
+ */
+bg_status bg_plan_create_mixed(int n, int d, int D_s, bg_field field, uint32_t p,
+                               bg_metric metric, int n_states, int n_assign,
+                               const uint8_t* assign, uint32_t four_dim_legs,
+                               bg_plan** out);
+
 /* bg_plan_destroy -- free a plan (NULL is accepted).  No kernel of this plan
  * may still be running. */
 bg_status bg_plan_destroy(bg_plan* plan);

@@ -31,7 +31,7 @@ MOSTLY_MINUS = 0
 ALTERNATING = 1
 
 # bg_plan_create / bg_eval / ... as declared in include/bg.h
-EXPORTED = ("bg_plan_create", "bg_plan_create_product", "bg_cut_trace", "bg_plan_destroy", "bg_workspace_size", "bg_eval",
+EXPORTED = ("bg_plan_create", "bg_plan_create_product", "bg_plan_create_mixed", "bg_cut_trace", "bg_plan_destroy", "bg_workspace_size", "bg_eval",
             "bg_eval_noalloc", "bg_host_staging_size", "bg_eval_host", "bg_batch_workspace_size",
             "bg_batch_create", "bg_batch_launch", "bg_batch_describe", "bg_batch_destroy",
             "bg_batch_autotune", "bg_serve_create", "bg_serve_submit", "bg_serve_wait",
@@ -67,6 +67,10 @@ def load_library(path=None):
                                            ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(vp)]
     lib.bg_plan_create_product.restype = ctypes.c_int
+    lib.bg_plan_create_mixed.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_uint8), ctypes.c_uint32, ctypes.POINTER(vp)]
+    lib.bg_plan_create_mixed.restype = ctypes.c_int
     lib.bg_cut_trace.argtypes = [ctypes.c_int, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(vp), vp, vp]
     lib.bg_cut_trace.restype = ctypes.c_int
@@ -149,12 +153,13 @@ class Plan:
     """One (n, d, D_s, field, p, metric, states) configuration (bg_plan)."""
 
     def __init__(self, n, d, Ds, field, p=0, metric=MOSTLY_MINUS, n_states=1, assign=None,
-                 states_per_leg=None):
+                 states_per_leg=None, four_dim_legs=None):
         """assign: None (every leg takes state 0), an [H][n] table of state
         indices, or "all": every one of the n_states^n assignments, output
         index h = sum_l s_l n_states^l, evaluated with shared sub-currents.
         states_per_leg (instead of assign): the product plan of
-        bg_plan_create_product (leg l takes states 0..states_per_leg[l]-1)."""
+        bg_plan_create_product (leg l takes states 0..states_per_leg[l]-1).
+        four_dim_legs: bit mask of four-dimensional legs (bg_plan_create_mixed)."""
         self.n, self.d, self.Ds = n, d, Ds
         self.field, self.p, self.metric = field, p, metric
         self.n_states = n_states
@@ -188,7 +193,11 @@ class Plan:
             buf = a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
         self.n_assign = H
         h = ctypes.c_void_p()
-        _check(_lib.bg_plan_create(n, d, Ds, field, p, metric, n_states, H, buf, ctypes.byref(h)))
+        if four_dim_legs is not None:
+            _check(_lib.bg_plan_create_mixed(n, d, Ds, field, p, metric, n_states, H, buf,
+                                             int(four_dim_legs), ctypes.byref(h)))
+        else:
+            _check(_lib.bg_plan_create(n, d, Ds, field, p, metric, n_states, H, buf, ctypes.byref(h)))
         self._h = h
         self._ws = None
 

@@ -226,7 +226,7 @@ int bg_version(void) { return BG_VERSION; }
 // product plan (all assignments of the product of per-leg state sets).
 static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, bg_metric metric,
                              int n_states, int n_assign, const uint8_t* assign, const uint8_t* product_radix,
-                             bg_plan** out) {
+                             uint32_t four_d_legs, bg_plan** out) {
     g_last_error.clear();
     if (!out) return fail(BG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -256,6 +256,9 @@ static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, 
             return fail(BG_ERR_INVALID_ARG, "assign is NULL with n_assign = %d != n_states^n", n_assign);
         all_states = true;
     }
+    if (four_d_legs >> n) return fail(BG_ERR_INVALID_ARG, "four_dim_legs has bits above leg n-1");
+    if (four_d_legs && all_states)
+        return fail(BG_ERR_UNSUPPORTED, "four-dimensional legs with all-assignment plans");
     if (assign) {
         for (int64_t i = 0; i < (int64_t)n_assign * n; ++i)
             if (assign[i] >= n_states)
@@ -271,8 +274,12 @@ static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, 
     const bool want_unrolled = kenv && strcmp(kenv, "unrolled") == 0;
     const char* tenv = getenv("BG_TABLE");
     const int Dk = round_dim(d), DSk = round_dim(D_s);
+    // mixed kernels only pay where a current has more than four components
+    const bool want_mixed = four_d_legs != 0 && DSk > 4;
     const bgk::KernelEntry* best = nullptr;
     int words = 0;
+    if (want_unrolled && four_d_legs)
+        return fail(BG_ERR_UNSUPPORTED, "the unrolled kernel has no four-dimensional legs");
     if (want_unrolled) {
         const int Du = round_dim(D_s > d ? D_s : d);
         for (const auto& e : registry())
@@ -296,14 +303,14 @@ static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, 
         for (const auto& e : registry()) {
             const int place = e.split ? bgk::kPlaceSplit : e.global_table ? bgk::kPlaceGlobal : bgk::kPlaceShared;
             if (e.compact && e.field == (int)field && e.D == Dk && e.DS == DSk &&
-                e.metric == (int)metric && place == want)
+                e.metric == (int)metric && place == want && e.mixed == want_mixed)
                 best = &e;
         }
         if (best && best->split) words = geo.cur_words(DSk);
-        if (!best)      // the complex fields have only the global placement
+        if (!best)      // the complex fields have only the global placement, mixed F_p no split
             for (const auto& e : registry())
                 if (e.compact && e.field == (int)field && e.D == Dk && e.DS == DSk &&
-                    e.metric == (int)metric)
+                    e.metric == (int)metric && e.mixed == want_mixed && !e.split)
                     best = &e;
     }
     if (!best) return fail(BG_ERR_UNSUPPORTED, "no kernel for n=%d d=%d D_s=%d field=%d metric=%d", n, d,
@@ -313,6 +320,7 @@ static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, 
     if (!pl) return fail(BG_ERR_NOMEM, "host allocation failed");
     pl->n = n; pl->d = d; pl->Ds = D_s; pl->field = field; pl->p = p; pl->metric = metric;
     pl->S = n_states; pl->H = n_assign; pl->entry = best; pl->words = words;
+    pl->four_d_legs = best->mixed ? four_d_legs : 0u;
     if (assign) pl->assign.assign(assign, assign + (size_t)n_assign * n);
     if (field == BG_FIELD_FP) {
         uint32_t inv = p;                         // p^-1 mod 2^32 by Newton iteration
@@ -389,7 +397,18 @@ extern "C" {
 
 bg_status bg_plan_create(int n, int d, int D_s, bg_field field, uint32_t p, bg_metric metric,
                          int n_states, int n_assign, const uint8_t* assign, bg_plan** out) {
-    return create_plan(n, d, D_s, field, p, metric, n_states, n_assign, assign, nullptr, out);
+    return create_plan(n, d, D_s, field, p, metric, n_states, n_assign, assign, nullptr, 0u, out);
+}
+
+bg_status bg_plan_create_mixed(int n, int d, int D_s, bg_field field, uint32_t p, bg_metric metric,
+                               int n_states, int n_assign, const uint8_t* assign, uint32_t four_dim_legs,
+                               bg_plan** out) {
+    if (n_assign > 1 && !assign) {
+        g_last_error.clear();
+        if (out) *out = nullptr;
+        return fail(BG_ERR_UNSUPPORTED, "mixed plans take an explicit assignment table");
+    }
+    return create_plan(n, d, D_s, field, p, metric, n_states, n_assign, assign, nullptr, four_dim_legs, out);
 }
 
 bg_status bg_plan_create_product(int n, int d, int D_s, bg_field field, uint32_t p, bg_metric metric,
@@ -407,7 +426,7 @@ bg_status bg_plan_create_product(int n, int d, int D_s, bg_field field, uint32_t
         h *= states_per_leg[l];
         if (h * n > (1 << 20)) return fail(BG_ERR_INVALID_ARG, "product of states_per_leg too large");
     }
-    return create_plan(n, d, D_s, field, p, metric, n_states, (int)h, nullptr, states_per_leg, out);
+    return create_plan(n, d, D_s, field, p, metric, n_states, (int)h, nullptr, states_per_leg, 0u, out);
 }
 
 bg_status bg_plan_destroy(bg_plan* plan) {
@@ -457,12 +476,13 @@ bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
     }
     int w = snprintf(buf, len,
                      "field=%s n=%d d=%d D_s=%d kernel=%s kernel_D=%d kernel_D_s=%d metric=%s "
-                     "table=%s block=%d blocks_per_sm=%d smem=%zu words_per_thread=%d elem_bytes=%d",
+                     "table=%s block=%d blocks_per_sm=%d smem=%zu words_per_thread=%d elem_bytes=%d "
+                     "four_dim_legs=0x%x",
                      field_name(plan->field), plan->n, plan->d, plan->Ds,
                      e->compact ? "compact" : "unrolled", e->D, e->DS,
                      plan->metric == BG_METRIC_MOSTLY_MINUS ? "mostly_minus" : "alternating",
                      e->split ? "split" : e->global_table ? "global" : "shared", e->block, plan->blocks_per_sm,
-                     plan->smem_bytes, plan->words, e->elem_bytes);
+                     plan->smem_bytes, plan->words, e->elem_bytes, plan->four_d_legs);
     if (w < 0 || (size_t)w >= len) return fail(BG_ERR_INVALID_ARG, "buffer too small");
     return BG_OK;
 }
@@ -532,6 +552,7 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const voi
         a.d_in = plan->d; a.ds_in = plan->Ds;
         a.k = momenta; a.eps = eps; a.out = out; a.status = status;
         a.assign = plan->d_assign; a.ws = workspace;
+        a.four_d_legs = plan->four_d_legs;
         e->launch(compact_params(plan), &a, dim3((unsigned)blocks), plan->smem_bytes, stream);
     } else {
         bgk::LaunchArgs a;

@@ -31,6 +31,7 @@
 // the instruction cache.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "bg_field.cuh"
 
@@ -48,6 +49,7 @@ struct CompactArgs {
     uint8_t* status;            // [E] or null
     const uint8_t* assign;      // device [H][n] or null (H == 1)
     void* ws;                   // global table (global placement)
+    uint32_t four_d_legs;       // bit l: leg l is four-dimensional (read by MIXED kernels)
 };
 
 // Table geometry for N = n - 1 recursion legs (host and device), in table
@@ -108,6 +110,28 @@ struct TableIO {
             for (int mu = 0; mu < K; ++mu) v[mu] = p[mu * BLOCK];
         }
     }
+    // the first KL components (KL = K, or 4 <= K) of a K-component vector
+    template <int K, int KL>
+    __device__ static __forceinline__ void load_live(const T* p, T* v) {
+        static_assert(KL == K || (KL == 4 && K >= 4), "live prefix of four components");
+        if constexpr (KL == K) {
+            load<K>(p, v);
+        } else if constexpr (VEC) {
+            if constexpr (K % 4 == 0) {
+                const uint4 x = reinterpret_cast<const uint4*>(p)[0];
+                v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const uint2 x = reinterpret_cast<const uint2*>(p)[q];
+                    v[2 * q] = x.x; v[2 * q + 1] = x.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int mu = 0; mu < KL; ++mu) v[mu] = p[mu * BLOCK];
+        }
+    }
     template <int K>
     __device__ static __forceinline__ void store(T* p, const T* v) {
         if constexpr (VEC) {
@@ -137,7 +161,7 @@ __device__ __forceinline__ void st_once(X* p, X v) { __stcs(p, v); }
 // The whole recursion for work item u (point e = u / H, assignment h = u % H)
 // with the block's currents at `tab` and its prefix sums, SA and 1/P^2 at
 // `aux` (shared or global memory).
-template <class F, int D, int DS, int METRIC, int BLOCK>
+template <class F, int D, int DS, int METRIC, int BLOCK, bool MIXED = false>
 __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typename F::T* tab,
                                          typename F::T* aux, int64_t u) {
     using T = typename F::T;
@@ -250,130 +274,148 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
     // a4: the recursion, by increasing length m.  Slot indices of the
     // sub-currents are advanced incrementally (count(L) = N - L + 1 slots per
     // length L) instead of being recomputed from jbase() at every access.
+    // The range [i, i+m-1] is evaluated with DL momentum and DSL current
+    // components: D and DS, or four for a range of four-dimensional legs only
+    // (MIXED kernels), whose momenta and currents vanish beyond the first
+    // four components.
     io_t result = f.zero_io();
+    auto range = [&](auto live_d, auto live_ds, const int m, const int i) {
+        constexpr int DL = decltype(live_d)::value;
+        constexpr int DSL = decltype(live_ds)::value;
+        TK Ki[DL], Kj[DL];
+        KIO::template load_live<D, DL>(kvec(i), Ki);
+        KIO::template load_live<D, DL>(kvec(i + m), Kj);
+        Acc acc[DSL];
+        f.template acc_zero<DSL>(acc);
+        C sa = f.czero();
+        int ps = i;                          // slot of the prefix [i, i+b]      (length b+1)
+        int ss = g.jbase(m - 1) + i + 1;     // slot of the suffix [i+b+1, j]    (length m-1-b)
+        int es = i - N;                      // first inner slot [i+1, i+b]: jbase(b) + i + 1
+        // momentum terms 2 adj_b K_{i+b+1} of consecutive splits are
+        // accumulated in pairs (one reduction per pair)
+        C mom_c = f.czero();
+        TK mom_v[DL];
+        bool mom_pending = false;
+#pragma unroll 1
+        for (int b = 0; b < m - 1; ++b) {
+            const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
+            T pb[DSL], sf[DSL];
+            TK Kt[DL], PA[DL], PB[DL];
+            IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, ps), pb);
+            IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, ss), sf);
+            KIO::template load_live<D, DL>(kvec(i + b + 1), Kt);
+#pragma unroll
+            for (int mu = 0; mu < DL; ++mu) {
+                PA[mu] = f.ksub(Kt[mu], Ki[mu]);
+                PB[mu] = f.ksub(Kj[mu], Kt[mu]);
+            }
+            // three-gluon vertex of the split at s = i + b
+            const C adj = f.template dot<DSL, METRIC>(pb, sf);
+            const C pa_jb = f.template kdot<DL, METRIC>(PA, sf);
+            const C pb_ja = f.template kdot<DL, METRIC>(PB, pb);
+            sa = f.cadd(sa, adj);
+            C csuf = f.cdbl(pb_ja);
+            if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(Sr[(ps - N) * BLOCK]));     // SA(prefix)
+            C cpre = f.cneg(f.cdbl(pa_jb));
+            if (lenB >= 2) cpre = f.csub(cpre, f.t_to_c(Sr[(ss - N) * BLOCK]));     // SA(suffix)
+            f.template acc2<DSL>(acc, csuf, sf, cpre, pb);
+            // momentum part: adj (P_A - P_B) = adj (2 K_{i+b+1} - K_i - K_j);
+            // the K_i + K_j share is added once per range below
+            if (mom_pending) {
+                f.template kacc2<DL>(acc, mom_c, mom_v, f.cdbl(adj), Kt);
+                mom_pending = false;
+            } else {
+                mom_c = f.cdbl(adj);
+#pragma unroll
+                for (int mu = 0; mu < DL; ++mu) mom_v[mu] = Kt[mu];
+                mom_pending = true;
+            }
+            // four-gluon vertex: prefix [i, i+q], inner [i+q+1, i+b], suffix sf
+            int pq = i, dp = N;              // prefix slot, step to the next length
+            int iq = es, di = N - b + 1;     // inner slot (length b-q), step down
+            int q = 0;
+            // F_p: four gaps per iteration (independent loads and dots in
+            // flight); C64 is bound by the FP64 pipe and takes pairs only
+#pragma unroll 1
+            for (; F::kIsFp && q + 3 < b; q += 4) {
+                T pa0[DSL], pa1[DSL], pa2[DSL], pa3[DSL], in0[DSL], in1[DSL], in2[DSL], in3[DSL];
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa0);
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in0);
+                pq += dp; iq -= di;
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa1);
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in1);
+                pq += dp - 1; iq -= di + 1;
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa2);
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in2);
+                pq += dp - 2; iq -= di + 2;
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa3);
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in3);
+                pq += dp - 3; iq -= di + 3;
+                dp -= 4; di += 4;
+                const C g0 = f.cdbl(f.template dot<DSL, METRIC>(pa0, sf));
+                const C g1 = f.cdbl(f.template dot<DSL, METRIC>(pa1, sf));
+                const C g2 = f.cdbl(f.template dot<DSL, METRIC>(pa2, sf));
+                const C g3 = f.cdbl(f.template dot<DSL, METRIC>(pa3, sf));
+                f.template acc2<DSL>(acc, g0, in0, g1, in1);
+                f.template acc2<DSL>(acc, g2, in2, g3, in3);
+            }
+#pragma unroll 1
+            for (; q + 1 < b; q += 2) {
+                T pa0[DSL], pa1[DSL], in0[DSL], in1[DSL];
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa0);
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in0);
+                pq += dp; iq -= di;
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa1);
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in1);
+                pq += dp - 1; iq -= di + 1;
+                dp -= 2; di += 2;
+                const C g0 = f.cdbl(f.template dot<DSL, METRIC>(pa0, sf));
+                const C g1 = f.cdbl(f.template dot<DSL, METRIC>(pa1, sf));
+                f.template acc2<DSL>(acc, g0, in0, g1, in1);
+            }
+            if (q < b) {
+                T pa0[DSL], in0[DSL];
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa0);
+                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in0);
+                const C g0 = f.cdbl(f.template dot<DSL, METRIC>(pa0, sf));
+                f.template acc1<DSL>(acc, g0, in0);
+            }
+            ps += N - b;                     // prefix length b+1 -> b+2
+            ss -= N - lenB + 1;              // suffix length lenB -> lenB-1
+            es += N - b + 1;                 // inner slots ending at i+b+1
+        }
+        {
+            TK KiKj[DL];
+#pragma unroll
+            for (int mu = 0; mu < DL; ++mu) KiKj[mu] = f.kadd(Ki[mu], Kj[mu]);
+            if (mom_pending) f.template kacc2<DL>(acc, mom_c, mom_v, f.cneg(sa), KiKj);
+            else f.template kacc1<DL>(acc, f.cneg(sa), KiKj);     // - SA(i,j) (K_i + K_j)
+        }
+        if (m < N) {
+            const int sidx = g.sbase(m) + i;
+            T J[DS];
+            f.template finish<DSL>(acc, Y[sidx * BLOCK], J);
+#pragma unroll
+            for (int mu = DSL; mu < DS; ++mu) J[mu] = f.zero();     // components beyond a 4d range
+            IO::template store<DS>(jvec(m, i), J);
+            Sr[sidx * BLOCK] = f.c_to_t(sa);
+        } else {
+            // a5: contract the top bracket with the last polarisation
+            result = f.template amplitude<DSL, METRIC>(acc, eL);
+        }
+    };
 #pragma unroll 1
     for (int m = 2; m <= N; ++m) {
 #pragma unroll 1
         for (int i = 0; i + m - 1 < N; ++i) {
-            TK Ki[D], Kj[D];
-            KIO::template load<D>(kvec(i), Ki);
-            KIO::template load<D>(kvec(i + m), Kj);
-            Acc acc[DS];
-            f.template acc_zero<DS>(acc);
-            C sa = f.czero();
-            int ps = i;                          // slot of the prefix [i, i+b]      (length b+1)
-            int ss = g.jbase(m - 1) + i + 1;     // slot of the suffix [i+b+1, j]    (length m-1-b)
-            int es = i - N;                      // first inner slot [i+1, i+b]: jbase(b) + i + 1
-            // momentum terms 2 adj_b K_{i+b+1} of consecutive splits are
-            // accumulated in pairs (one reduction per pair)
-            C mom_c = f.czero();
-            TK mom_v[D];
-            bool mom_pending = false;
-#pragma unroll 1
-            for (int b = 0; b < m - 1; ++b) {
-                const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
-                T pb[DS], sf[DS];
-                TK Kt[D], PA[D], PB[D];
-                IO::template load<DS>(IO::template vec<DS>(Jr, ps), pb);
-                IO::template load<DS>(IO::template vec<DS>(Jr, ss), sf);
-                KIO::template load<D>(kvec(i + b + 1), Kt);
-#pragma unroll
-                for (int mu = 0; mu < D; ++mu) {
-                    PA[mu] = f.ksub(Kt[mu], Ki[mu]);
-                    PB[mu] = f.ksub(Kj[mu], Kt[mu]);
+            if constexpr (MIXED && DS > 4) {
+                const uint32_t legs = ((1u << m) - 1u) << i;
+                if ((a.four_d_legs & legs) == legs) {
+                    range(std::integral_constant<int, 4>{}, std::integral_constant<int, 4>{}, m, i);
+                    continue;
                 }
-                // three-gluon vertex of the split at s = i + b
-                const C adj = f.template dot<DS, METRIC>(pb, sf);
-                const C pa_jb = f.template kdot<D, METRIC>(PA, sf);
-                const C pb_ja = f.template kdot<D, METRIC>(PB, pb);
-                sa = f.cadd(sa, adj);
-                C csuf = f.cdbl(pb_ja);
-                if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(Sr[(ps - N) * BLOCK]));     // SA(prefix)
-                C cpre = f.cneg(f.cdbl(pa_jb));
-                if (lenB >= 2) cpre = f.csub(cpre, f.t_to_c(Sr[(ss - N) * BLOCK]));     // SA(suffix)
-                f.template acc2<DS>(acc, csuf, sf, cpre, pb);
-                // momentum part: adj (P_A - P_B) = adj (2 K_{i+b+1} - K_i - K_j);
-                // the K_i + K_j share is added once per range below
-                if (mom_pending) {
-                    f.template kacc2<D>(acc, mom_c, mom_v, f.cdbl(adj), Kt);
-                    mom_pending = false;
-                } else {
-                    mom_c = f.cdbl(adj);
-#pragma unroll
-                    for (int mu = 0; mu < D; ++mu) mom_v[mu] = Kt[mu];
-                    mom_pending = true;
-                }
-                // four-gluon vertex: prefix [i, i+q], inner [i+q+1, i+b], suffix sf
-                int pq = i, dp = N;              // prefix slot, step to the next length
-                int iq = es, di = N - b + 1;     // inner slot (length b-q), step down
-                int q = 0;
-                // F_p: four gaps per iteration (independent loads and dots in
-                // flight); C64 is bound by the FP64 pipe and takes pairs only
-#pragma unroll 1
-                for (; F::kIsFp && q + 3 < b; q += 4) {
-                    T pa0[DS], pa1[DS], pa2[DS], pa3[DS], in0[DS], in1[DS], in2[DS], in3[DS];
-                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa0);
-                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in0);
-                    pq += dp; iq -= di;
-                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa1);
-                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in1);
-                    pq += dp - 1; iq -= di + 1;
-                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa2);
-                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in2);
-                    pq += dp - 2; iq -= di + 2;
-                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa3);
-                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in3);
-                    pq += dp - 3; iq -= di + 3;
-                    dp -= 4; di += 4;
-                    const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
-                    const C g1 = f.cdbl(f.template dot<DS, METRIC>(pa1, sf));
-                    const C g2 = f.cdbl(f.template dot<DS, METRIC>(pa2, sf));
-                    const C g3 = f.cdbl(f.template dot<DS, METRIC>(pa3, sf));
-                    f.template acc2<DS>(acc, g0, in0, g1, in1);
-                    f.template acc2<DS>(acc, g2, in2, g3, in3);
-                }
-#pragma unroll 1
-                for (; q + 1 < b; q += 2) {
-                    T pa0[DS], pa1[DS], in0[DS], in1[DS];
-                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa0);
-                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in0);
-                    pq += dp; iq -= di;
-                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa1);
-                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in1);
-                    pq += dp - 1; iq -= di + 1;
-                    dp -= 2; di += 2;
-                    const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
-                    const C g1 = f.cdbl(f.template dot<DS, METRIC>(pa1, sf));
-                    f.template acc2<DS>(acc, g0, in0, g1, in1);
-                }
-                if (q < b) {
-                    T pa0[DS], in0[DS];
-                    IO::template load<DS>(IO::template vec<DS>(Jr, pq), pa0);
-                    IO::template load<DS>(IO::template vec<DS>(Jr, iq), in0);
-                    const C g0 = f.cdbl(f.template dot<DS, METRIC>(pa0, sf));
-                    f.template acc1<DS>(acc, g0, in0);
-                }
-                ps += N - b;                     // prefix length b+1 -> b+2
-                ss -= N - lenB + 1;              // suffix length lenB -> lenB-1
-                es += N - b + 1;                 // inner slots ending at i+b+1
             }
-            {
-                TK KiKj[D];
-#pragma unroll
-                for (int mu = 0; mu < D; ++mu) KiKj[mu] = f.kadd(Ki[mu], Kj[mu]);
-                if (mom_pending) f.template kacc2<D>(acc, mom_c, mom_v, f.cneg(sa), KiKj);
-                else f.template kacc1<D>(acc, f.cneg(sa), KiKj);     // - SA(i,j) (K_i + K_j)
-            }
-            if (m < N) {
-                const int sidx = g.sbase(m) + i;
-                T J[DS];
-                f.template finish<DS>(acc, Y[sidx * BLOCK], J);
-                IO::template store<DS>(jvec(m, i), J);
-                Sr[sidx * BLOCK] = f.c_to_t(sa);
-            } else {
-                // a5: contract the top bracket with the last polarisation
-                result = f.template amplitude<DS, METRIC>(acc, eL);
-            }
+            range(std::integral_constant<int, D>{}, std::integral_constant<int, DS>{}, m, i);
         }
     }
     st_once(out + u, singular ? f.zero_io() : result);
@@ -386,7 +428,7 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
     bg_point<F, D, DS, METRIC, BLOCK>(f, a, tab, tab + Geometry{a.n - 1}.off_k(DS) * BLOCK, u);
 }
 
-template <class F, int D, int DS, int METRIC, int BLOCK, int PLACE>
+template <class F, int D, int DS, int METRIC, int BLOCK, int PLACE, bool MIXED>
 __device__ __forceinline__ void compact_body(const F& f, const CompactArgs& a) {
     using T = typename F::T;
     extern __shared__ __align__(16) unsigned char bg_smem[];
@@ -406,13 +448,13 @@ __device__ __forceinline__ void compact_body(const F& f, const CompactArgs& a) {
     const int64_t total = a.E * a.H;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * BLOCK;
     for (int64_t u = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; u < total; u += stride)
-        bg_point<F, D, DS, METRIC, BLOCK>(f, a, tab, aux, u);
+        bg_point<F, D, DS, METRIC, BLOCK, MIXED>(f, a, tab, aux, u);
 }
 
-template <class F, int D, int DS, int METRIC, int BLOCK, int PLACE>
+template <class F, int D, int DS, int METRIC, int BLOCK, int PLACE, bool MIXED = false>
 __global__ void __launch_bounds__(BLOCK)
 bg_compact_kernel(const F f, const CompactArgs a) {
-    compact_body<F, D, DS, METRIC, BLOCK, PLACE>(f, a);
+    compact_body<F, D, DS, METRIC, BLOCK, PLACE, MIXED>(f, a);
 }
 
 }  // namespace bgk

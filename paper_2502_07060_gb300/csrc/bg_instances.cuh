@@ -22,6 +22,7 @@ struct KernelEntry {
     bool global_table;  // (part of the) table in global scratch: the workspace is needed
     bool split;         // currents in global scratch, the rest in shared memory
     bool compact;       // run-time n (bg_compact_kernel) or unrolled per n
+    bool mixed;         // evaluates ranges of four-dimensional legs with four components
     int block;          // threads per block
     int words;          // table elements per thread (unrolled kernels)
     int elem_bytes;     // sizeof(T)
@@ -48,6 +49,7 @@ KernelEntry make_entry() {
     e.global_table = G;
     e.split = false;
     e.compact = false;
+    e.mixed = false;
     e.block = B;
     e.words = Frame<NLEG - 1, D, DS>::WORDS;
     e.elem_bytes = sizeof(typename F::T);
@@ -56,13 +58,13 @@ KernelEntry make_entry() {
     return e;
 }
 
-template <class F, int D, int DS, int M, int B, int G>
+template <class F, int D, int DS, int M, int B, int G, bool X>
 void launch_compact(const void* fp, const void* args, dim3 grid, size_t smem, cudaStream_t s) {
     const F& f = *static_cast<const F*>(fp);
-    bg_compact_kernel<F, D, DS, M, B, G><<<grid, B, smem, s>>>(f, *static_cast<const CompactArgs*>(args));
+    bg_compact_kernel<F, D, DS, M, B, G, X><<<grid, B, smem, s>>>(f, *static_cast<const CompactArgs*>(args));
 }
 
-template <class F, int D, int DS, int M, int B, int G>
+template <class F, int D, int DS, int M, int B, int G, bool X = false>
 KernelEntry make_compact() {
     KernelEntry e;
     e.field = F::kField;
@@ -73,11 +75,12 @@ KernelEntry make_compact() {
     e.global_table = G != kPlaceShared;
     e.split = G == kPlaceSplit;
     e.compact = true;
+    e.mixed = X;
     e.block = B;
     e.words = 0;
     e.elem_bytes = sizeof(typename F::T);
-    e.func = reinterpret_cast<const void*>(&bg_compact_kernel<F, D, DS, M, B, G>);
-    e.launch = &launch_compact<F, D, DS, M, B, G>;
+    e.func = reinterpret_cast<const void*>(&bg_compact_kernel<F, D, DS, M, B, G, X>);
+    e.launch = &launch_compact<F, D, DS, M, B, G, X>;
     return e;
 }
 
@@ -112,14 +115,22 @@ constexpr int kBlockFpCompactSmem = 64;
 constexpr int kBlockFpCompactGlobal = 128;
 constexpr int kBlockC64Compact = 64;
 
+// Mixed-dimension variants (plans with four-dimensional legs) exist where a
+// current has more than four components: F_p with shared or global table,
+// the complex fields with global table.
 template <class F, int D, int DS, int M>
 void add_compact_dims(std::vector<KernelEntry>& v) {
     if constexpr (F::kIsFp) {
         v.push_back(make_compact<F, D, DS, M, kBlockFpCompactSmem, kPlaceShared>());
         v.push_back(make_compact<F, D, DS, M, kBlockFpCompactGlobal, kPlaceGlobal>());
         v.push_back(make_compact<F, D, DS, M, kBlockFpCompactGlobal, kPlaceSplit>());
+        if constexpr (DS > 4) {
+            v.push_back(make_compact<F, D, DS, M, kBlockFpCompactSmem, kPlaceShared, true>());
+            v.push_back(make_compact<F, D, DS, M, kBlockFpCompactGlobal, kPlaceGlobal, true>());
+        }
     } else {
         v.push_back(make_compact<F, D, DS, M, kBlockC64Compact, kPlaceGlobal>());
+        if constexpr (DS > 4) v.push_back(make_compact<F, D, DS, M, kBlockC64Compact, kPlaceGlobal, true>());
     }
 }
 

@@ -17,6 +17,7 @@ struct bg_plan {
     bg_metric metric;
     int S, H;
     std::vector<uint8_t> assign;      // host copy [H][n]
+    uint32_t four_d_legs = 0;         // bit l: leg l four-dimensional (mixed plans)
     uint8_t* d_assign = nullptr;      // device copy when H > 1
     int device = -1;                  // device of d_assign / attribute setup
     const bgk::KernelEntry* entry = nullptr;

@@ -91,7 +91,7 @@ extern "C" bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void*
     const bgk::KernelEntry* e = nullptr;
     for (const auto& k : bgi::registry())
         if (k.compact && k.global_table && !k.split && k.field == (int)plan->field && k.D == D &&
-            k.DS == DS && k.metric == (int)plan->metric)
+            k.DS == DS && k.metric == (int)plan->metric && k.mixed == plan->entry->mixed)
             e = &k;
     if (!e) return bgi::fail(BG_ERR_UNSUPPORTED, "no global-table kernel for this plan");
     const bgk::Geometry geo{plan->n - 1};
@@ -121,6 +121,7 @@ extern "C" bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void*
     a.d_in = plan->d; a.ds_in = plan->Ds;
     a.k = momenta; a.eps = eps; a.out = out; a.status = status;
     a.assign = plan->d_assign; a.ws = scratch;
+    a.four_d_legs = plan->four_d_legs;
     e->launch(bgi::compact_params(plan), &a, dim3((unsigned)blocks), 0, stream);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return bgi::fail(BG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(err));

@@ -191,16 +191,36 @@ def fp_null_vectors(rng, shape, d, p, metric=MOSTLY_MINUS):
     return out
 
 
-def fp_massless_point(rng, E, n, d, p, metric=MOSTLY_MINUS):
-    """E points of n null momenta in F_p^d with sum k = 0 (all outgoing)."""
+def _check_four_d(four_d, n):
+    if four_d >> (n - 1):
+        raise ValueError("four-dimensional legs must be among 0..n-2 (leg n-1 closes the point)")
+
+
+def fp_massless_point(rng, E, n, d, p, metric=MOSTLY_MINUS, four_d=0):
+    """E points of n null momenta in F_p^d with sum k = 0 (all outgoing).
+    four_d: bit mask of legs (among 0..n-2) whose momenta are four-dimensional
+    null vectors padded with zeros; the last leg takes the remainder."""
     eta = metric_diag(d, metric)
     k = np.empty((E, n, d), dtype=np.uint64)
-    k[:, :n - 2] = fp_null_vectors(rng, (E, n - 2), d, p, metric)
+    if four_d:
+        _check_four_d(four_d, n)
+        for l in range(n - 2):
+            if (four_d >> l) & 1:
+                k[:, l, :4] = fp_null_vectors(rng, (E,), 4, p, metric)
+                k[:, l, 4:] = 0
+            else:
+                k[:, l] = fp_null_vectors(rng, (E,), d, p, metric)
+    else:
+        k[:, :n - 2] = fp_null_vectors(rng, (E, n - 2), d, p, metric)
     Q = fneg(k[:, :n - 2].sum(axis=1) % np.uint64(p), p)
     todo = np.ones(E, dtype=bool)
     while todo.any():
         idx = np.flatnonzero(todo)
-        r = fp_null_vectors(rng, (len(idx),), d, p, metric)
+        if (four_d >> (n - 2)) & 1:
+            r = np.zeros((len(idx), d), dtype=np.uint64)
+            r[:, :4] = fp_null_vectors(rng, (len(idx),), 4, p, metric)
+        else:
+            r = fp_null_vectors(rng, (len(idx),), d, p, metric)
         Qi = Q[idx]
         qr = fdot(Qi, r, eta, p)
         q2 = fdot(Qi, Qi, eta, p)
@@ -214,9 +234,17 @@ def fp_massless_point(rng, E, n, d, p, metric=MOSTLY_MINUS):
     return k
 
 
-def fp_transverse_states(rng, k, Ds, p, metric=MOSTLY_MINUS, S=1):
+def fp_transverse_states(rng, k, Ds, p, metric=MOSTLY_MINUS, S=1, four_d=0):
     """S seeded states per leg, eps [E][n][S][Ds], transverse to k (padded to
-    Ds) and to a seeded null reference q per leg."""
+    Ds) and to a seeded null reference q per leg.  Legs in the bit mask
+    four_d get four-dimensional states (reference and seed vector in the
+    first four components), padded with zeros."""
+    if four_d:
+        eps = fp_transverse_states(rng, k, Ds, p, metric, S)
+        legs = [l for l in range(k.shape[1]) if (four_d >> l) & 1]
+        eps[:, legs] = 0
+        eps[:, legs, :, :4] = fp_transverse_states(rng, k[:, legs, :4], 4, p, metric, S)
+        return eps
     E, n, d = k.shape
     eta = metric_diag(Ds, metric)
     kp = np.zeros((E, n, Ds), dtype=np.uint64)
@@ -256,17 +284,17 @@ def _chunk_rng(seed, c):
     return np.random.Generator(np.random.Philox(np.random.SeedSequence([int(seed), int(c)])))
 
 
-def _fp_chunk(seed, c, m, n, d, Ds, p, metric, S):
+def _fp_chunk(seed, c, m, n, d, Ds, p, metric, S, four_d=0):
     rng = _chunk_rng(seed, c)
-    k = fp_massless_point(rng, m, n, d, p, metric)
-    eps = fp_transverse_states(rng, k, Ds, p, metric, S)
+    k = fp_massless_point(rng, m, n, d, p, metric, four_d)
+    eps = fp_transverse_states(rng, k, Ds, p, metric, S, four_d)
     return k.astype(np.uint32), (eps[:, :, 0, :] if S == 1 else eps).astype(np.uint32)
 
 
-def _c64_chunk(seed, c, m, n, d, Ds, metric, S):
+def _c64_chunk(seed, c, m, n, d, Ds, metric, S, four_d=0):
     rng = _chunk_rng(seed, c)
-    k = c64_massless_point(rng, m, n, d, metric)
-    eps = c64_transverse_states(rng, k, Ds, metric, S)
+    k = c64_massless_point(rng, m, n, d, metric, four_d)
+    eps = c64_transverse_states(rng, k, Ds, metric, S, four_d)
     return k.astype(np.complex128), (eps[:, :, 0, :] if S == 1 else eps)
 
 
@@ -285,10 +313,11 @@ def _run_chunks(fn, seed, E, args, workers):
         return list(ex.map(fn, *zip(*jobs)))
 
 
-def fp_batch(seed, E, n, d, Ds, p=P_DEFAULT, metric=MOSTLY_MINUS, S=1, workers=None):
+def fp_batch(seed, E, n, d, Ds, p=P_DEFAULT, metric=MOSTLY_MINUS, S=1, workers=None, four_d=0):
     """Seeded F_p batch: (k uint32 [E][n][d], eps uint32 [E][n][Ds]) when S == 1,
-    else eps uint32 [E][n][S][Ds]."""
-    parts = _run_chunks(_fp_chunk, seed, E, (n, d, Ds, p, metric, S), workers)
+    else eps uint32 [E][n][S][Ds].  four_d: bit mask of four-dimensional legs
+    (momenta and states zero beyond the first four components)."""
+    parts = _run_chunks(_fp_chunk, seed, E, (n, d, Ds, p, metric, S, four_d), workers)
     if not parts:
         return (np.empty((0, n, d), np.uint32),
                 np.empty((0, n, Ds) if S == 1 else (0, n, S, Ds), np.uint32))
@@ -328,15 +357,28 @@ def c64_null_vectors(rng, shape, d, metric=MOSTLY_MINUS, emax=1000.0):
     return v - (v2 / (2 * vq))[..., None] * q
 
 
-def c64_massless_point(rng, E, n, d, metric=MOSTLY_MINUS):
+def c64_massless_point(rng, E, n, d, metric=MOSTLY_MINUS, four_d=0):
     eta = metric_diag(d, metric).astype(np.float64)
     k = np.empty((E, n, d), dtype=np.float64)
-    k[:, :n - 2] = c64_null_vectors(rng, (E, n - 2), d, metric)
+    if four_d:
+        _check_four_d(four_d, n)
+        for l in range(n - 2):
+            if (four_d >> l) & 1:
+                k[:, l, :4] = c64_null_vectors(rng, (E,), 4, metric)
+                k[:, l, 4:] = 0.0
+            else:
+                k[:, l] = c64_null_vectors(rng, (E,), d, metric)
+    else:
+        k[:, :n - 2] = c64_null_vectors(rng, (E, n - 2), d, metric)
     Q = -k[:, :n - 2].sum(axis=1)
     todo = np.ones(E, dtype=bool)
     while todo.any():
         idx = np.flatnonzero(todo)
-        r = c64_null_vectors(rng, (len(idx),), d, metric)
+        if (four_d >> (n - 2)) & 1:
+            r = np.zeros((len(idx), d))
+            r[:, :4] = c64_null_vectors(rng, (len(idx),), 4, metric)
+        else:
+            r = c64_null_vectors(rng, (len(idx),), d, metric)
         Qi = Q[idx]
         qr = _cdot(Qi, r, eta)
         good = np.abs(qr) >= 1e-3 * np.linalg.norm(Qi, axis=-1) * np.linalg.norm(r, axis=-1)
@@ -348,7 +390,13 @@ def c64_massless_point(rng, E, n, d, metric=MOSTLY_MINUS):
     return k
 
 
-def c64_transverse_states(rng, k, Ds, metric=MOSTLY_MINUS, S=1):
+def c64_transverse_states(rng, k, Ds, metric=MOSTLY_MINUS, S=1, four_d=0):
+    if four_d:
+        eps = c64_transverse_states(rng, k, Ds, metric, S)
+        legs = [l for l in range(k.shape[1]) if (four_d >> l) & 1]
+        eps[:, legs] = 0
+        eps[:, legs, :, :4] = c64_transverse_states(rng, k[:, legs, :4], 4, metric, S)
+        return eps
     E, n, d = k.shape
     eta = metric_diag(Ds, metric).astype(np.float64)
     kp = np.zeros((E, n, Ds), dtype=np.complex128)
@@ -363,10 +411,11 @@ def c64_transverse_states(rng, k, Ds, metric=MOSTLY_MINUS, S=1):
     return v - a[..., None] * kpS - b[..., None] * qS
 
 
-def c64_batch(seed, E, n, d, Ds, metric=MOSTLY_MINUS, S=1, workers=None):
+def c64_batch(seed, E, n, d, Ds, metric=MOSTLY_MINUS, S=1, workers=None, four_d=0):
     """Seeded complex batch: (k complex128 [E][n][d] with zero imaginary part,
-    eps complex128 [E][n][Ds]) when S == 1, else eps [E][n][S][Ds]."""
-    parts = _run_chunks(_c64_chunk, seed, E, (n, d, Ds, metric, S), workers)
+    eps complex128 [E][n][Ds]) when S == 1, else eps [E][n][S][Ds].  four_d as
+    in fp_batch."""
+    parts = _run_chunks(_c64_chunk, seed, E, (n, d, Ds, metric, S, four_d), workers)
     if not parts:
         return (np.empty((0, n, d), np.complex128),
                 np.empty((0, n, Ds) if S == 1 else (0, n, S, Ds), np.complex128))

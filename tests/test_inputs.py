@@ -157,3 +157,28 @@ def test_golden_fixtures_reproduce():
         eps = [[Fraction(x) for x in v] for v in c["eps"]]
         a, st = O.amplitude(k, eps, c["metric"])
         assert st == 0 and a == Fraction(c["amplitude"])
+
+
+@pytest.mark.parametrize("n,d,Ds,metric,mask", [(8, 6, 6, 0, 0b1111110), (6, 8, 8, 1, 0b011010),
+                                                (5, 4, 6, 0, 0b0110), (12, 8, 8, 0, 0b011111111110)])
+def test_mixed_dimension_points(n, d, Ds, metric, mask):
+    """Points with four-dimensional legs (the loop-level setting of Sec. 2.3):
+    flagged legs have momenta and states that vanish beyond four components;
+    every momentum is null, the sum is zero and every state is transverse."""
+    k, e = G.fp_batch(9, 300, n, d, Ds, P, metric, workers=1, four_d=mask)
+    k = k.astype(np.uint64)
+    e = e.astype(np.uint64)
+    eta_k = G.metric_diag(d, metric)
+    eta_e = G.metric_diag(Ds, metric)
+    kp = np.zeros(k.shape[:2] + (Ds,), np.uint64)
+    kp[..., :d] = k
+    for l in range(n):
+        assert (G.fdot(k[:, l], k[:, l], eta_k, P) == 0).all()
+        assert (G.fdot(e[:, l], kp[:, l], eta_e, P) == 0).all()
+        if (mask >> l) & 1:
+            assert not k[:, l, 4:].any() and not e[:, l, 4:].any()
+    assert not (k.sum(axis=1) % np.uint64(P)).any()
+    if d > 4:
+        assert k[:, n - 1, 4:].any()          # the closing leg carries the extra components
+    with pytest.raises(ValueError):
+        G.fp_batch(9, 4, n, d, Ds, P, metric, workers=1, four_d=1 << (n - 1))

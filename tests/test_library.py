@@ -69,3 +69,16 @@ def test_eval_rejects_null_plan(lib):
     lib.bg_eval.argtypes = [ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 5 + \
         [ctypes.c_size_t, ctypes.c_void_p]
     assert lib.bg_eval(None, 1, None, None, None, None, None, 0, None) == 1
+
+
+def test_mixed_plan_rejects_bad_masks_on_host(lib):
+    """bg_plan_create_mixed: a four-dimensional-leg mask with bits at or above
+    n, and the all-assignment form, are refused before any CUDA call."""
+    lib.bg_plan_create_mixed.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]
+    h = ctypes.c_void_p()
+    assert lib.bg_plan_create_mixed(8, 6, 6, 1, 2147483629, 0, 1, 1, None, 1 << 8, ctypes.byref(h)) == 1
+    assert lib.bg_plan_create_mixed(5, 6, 6, 1, 2147483629, 0, 1, 1, None, 0xFFFFFFFF, ctypes.byref(h)) == 1
+    assert lib.bg_plan_create_mixed(5, 6, 6, 1, 2147483629, 0, 2, 32, None, 0b110, ctypes.byref(h)) == 2
+    assert not h.value
