@@ -208,8 +208,10 @@ bg_status bg_host_staging_size(const bg_plan* plan, int64_t chunk, size_t* bytes
  *   chunk         points per chunk, >= 1
  * Returns BG_ERR_INVALID_ARG for device pointers in place of host buffers, a
  * too small or misaligned staging buffer, or E < 0; BG_ERR_CUDA when a copy
- * or launch cannot be enqueued.  Calls from several host threads are
- * serialised while they enqueue.
+ * or launch cannot be enqueued -- such a call returns after the copies it had
+ * already enqueued have finished, and the contents of out and status are then
+ * unspecified.  Calls from several host threads are serialised while they
+ * enqueue.
  */
 bg_status bg_eval_host(const bg_plan* plan, int64_t E, const void* momenta,
                        const void* eps, void* out, uint8_t* status, int64_t chunk,
@@ -366,6 +368,31 @@ const char* bg_last_error(void);
 
 /* bg_version -- BG_VERSION of the library binary. */
 int bg_version(void);
+
+/*
+ * bg_debug_inject_fault -- testing aid for the failure paths (no counterpart
+ * in the paper).  Operations at `site` number 0, 1, 2, ... from this call on;
+ * operations skip .. skip+count-1 fail as if the CUDA runtime had refused
+ * them, without calling it (nothing reaches the GPU, so nothing can fault
+ * there), and every later one runs normally.  count = 0 disarms the site.
+ * Process-wide; not meant for production use.
+ *   BG_FAULT_DEVICE_ALLOC  device allocations: the assignment table of
+ *                          bg_plan_create*, the arena of bg_serve_create ->
+ *                          BG_ERR_NOMEM
+ *   BG_FAULT_LAUNCH        kernel and graph launches of bg_eval,
+ *                          bg_eval_noalloc, bg_batch_launch, bg_cut_trace ->
+ *                          BG_ERR_CUDA, outputs untouched
+ *   BG_FAULT_COPY          asynchronous copies of bg_eval_host (per chunk)
+ *                          and of served requests -> BG_ERR_CUDA (for a
+ *                          served request, from its bg_serve_wait)
+ * Returns BG_ERR_INVALID_ARG for an unknown site or negative skip / count.
+ */
+typedef enum {
+    BG_FAULT_DEVICE_ALLOC = 1,
+    BG_FAULT_LAUNCH = 2,
+    BG_FAULT_COPY = 3
+} bg_fault_site;
+bg_status bg_debug_inject_fault(bg_fault_site site, int skip, int count);
 
 #ifdef __cplusplus
 }

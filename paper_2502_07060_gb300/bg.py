@@ -36,7 +36,7 @@ EXPORTED = ("bg_plan_create", "bg_plan_create_product", "bg_plan_create_mixed", 
             "bg_batch_create", "bg_batch_launch", "bg_batch_describe", "bg_batch_destroy",
             "bg_batch_autotune", "bg_serve_create", "bg_serve_submit", "bg_serve_wait",
             "bg_serve_stats", "bg_serve_destroy", "bg_plan_describe", "bg_strerror", "bg_last_error",
-            "bg_version")
+            "bg_version", "bg_debug_inject_fault")
 
 LIB_PATH = _build.LIB
 
@@ -120,6 +120,8 @@ def load_library(path=None):
     lib.bg_strerror.restype = ctypes.c_char_p
     lib.bg_last_error.argtypes = []
     lib.bg_last_error.restype = ctypes.c_char_p
+    lib.bg_debug_inject_fault.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.bg_debug_inject_fault.restype = ctypes.c_int
     lib.bg_version.argtypes = []
     lib.bg_version.restype = ctypes.c_int
     return lib
@@ -459,3 +461,14 @@ def strerror(status):
 
 def version():
     return _lib.bg_version()
+
+
+FAULT_DEVICE_ALLOC = 1
+FAULT_LAUNCH = 2
+FAULT_COPY = 3
+
+
+def inject_fault(site, skip=0, count=1):
+    """bg_debug_inject_fault: operations skip .. skip+count-1 at `site` fail
+    as if the CUDA runtime had refused them (count = 0 disarms)."""
+    _check(_lib.bg_debug_inject_fault(site, skip, count))

@@ -2,6 +2,7 @@
 // validation, kernel selection and the single launch of bg_eval.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdlib>
 #include <cstdio>
@@ -34,6 +35,23 @@ thread_local std::string g_last_error;
 }  // namespace
 
 namespace bgi {
+
+namespace {
+struct FaultPlan {
+    std::atomic<int64_t> seen{0};     // operations at the site since the last arming
+    std::atomic<int64_t> first{0};    // first failing operation
+    std::atomic<int64_t> end{0};      // one past the last failing operation
+};
+FaultPlan g_fault[4];
+}  // namespace
+
+bool fault(int site) {
+    if (site < 1 || site > 3) return false;
+    FaultPlan& f = g_fault[site];
+    if (f.end.load(std::memory_order_relaxed) == 0) return false;
+    const int64_t k = f.seen.fetch_add(1);
+    return k >= f.first.load() && k < f.end.load();
+}
 
 bg_status fail(bg_status s, const char* fmt, ...) {
     char buf[512];
@@ -220,6 +238,17 @@ const char* bg_last_error(void) { return g_last_error.c_str(); }
 
 int bg_version(void) { return BG_VERSION; }
 
+bg_status bg_debug_inject_fault(bg_fault_site site, int skip, int count) {
+    if ((int)site < 1 || (int)site > 3 || skip < 0 || count < 0)
+        return fail(BG_ERR_INVALID_ARG, "bad fault site %d, skip %d or count %d", (int)site, skip, count);
+    bgi::FaultPlan& f = bgi::g_fault[(int)site];
+    f.end.store(0);
+    f.seen.store(0);
+    f.first.store(skip);
+    f.end.store(count > 0 ? (int64_t)skip + count : 0);
+    return BG_OK;
+}
+
 }  // extern "C"
 
 // Plan creation; product_radix (or NULL) gives the states per leg of a
@@ -377,7 +406,7 @@ static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, 
     }
     if (n_assign > 1 && !all_states) {
         size_t bytes = pl->assign.size();
-        if (cudaMalloc(&pl->d_assign, bytes) != cudaSuccess) {
+        if (bgi::fault(BG_FAULT_DEVICE_ALLOC) || cudaMalloc(&pl->d_assign, bytes) != cudaSuccess) {
             cudaGetLastError();
             delete pl;
             return fail(BG_ERR_NOMEM, "device allocation of %zu B failed", bytes);
@@ -489,6 +518,7 @@ bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
 
 bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
                   uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+    bgi::Range nvtx("bg_eval");
     g_last_error.clear();
     if (!plan) return fail(BG_ERR_INVALID_ARG, "plan is NULL");
     if (E < 0) return fail(BG_ERR_INVALID_ARG, "E = %lld < 0", (long long)E);
@@ -536,12 +566,14 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const voi
         a.E = E; a.n = plan->n; a.d_in = plan->d; a.ds_in = plan->Ds;
         a.k = momenta; a.eps = eps; a.out = out; a.status = status;
         a.ws = plan->states_global ? workspace : nullptr;
+        if (bgi::fault(BG_FAULT_LAUNCH)) return fail(BG_ERR_CUDA, "launch failed: injected fault");
         plan->sentry->launch(compact_params(plan), a, plan->sgeo, dim3((unsigned)blocks), plan->smem_bytes,
                              stream);
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return fail(BG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(err));
         return BG_OK;
     }
+    if (bgi::fault(BG_FAULT_LAUNCH)) return fail(BG_ERR_CUDA, "launch failed: injected fault");
     const int64_t items = E * plan->H;
     int64_t blocks = (items + e->block - 1) / e->block;
     const int64_t cap = e->global_table ? resident_blocks(plan) : resident_blocks(plan) * 256;

@@ -273,7 +273,9 @@ bg_status bg_batch_create(const bg_group* groups, int n_groups, const bg_batch_c
 }
 
 bg_status bg_batch_launch(const bg_batch* batch, cudaStream_t stream) {
+    bgi::Range nvtx("bg_batch_launch");
     if (!batch || !batch->exec) return bgi::fail(BG_ERR_INVALID_ARG, "batch is NULL");
+    if (bgi::fault(BG_FAULT_LAUNCH)) return bgi::fail(BG_ERR_CUDA, "graph launch failed: injected fault");
     cudaError_t err = cudaGraphLaunch(batch->exec, stream);
     if (err != cudaSuccess) {
         cudaGetLastError();

@@ -159,6 +159,8 @@ extern "C" bg_status bg_cut_trace(bg_field field, uint32_t p, int64_t E, int k, 
     }
     if ((uintptr_t)out % elem) return bgi::fail(BG_ERR_INVALID_ARG, "out misaligned");
     if ((st = bgi::check_device_ptr(out, "out", dev)) != BG_OK) return st;
+    if (bgi::fault(BG_FAULT_LAUNCH)) return bgi::fail(BG_ERR_CUDA, "launch failed: injected fault");
+    bgi::Range nvtx("bg_cut_trace");
     if (field == BG_FIELD_FP) launch_cut(ModP{p}, S, a, stream);
     else launch_cut(CplxD{}, S, a, stream);
     cudaError_t err = cudaGetLastError();

@@ -12,7 +12,8 @@
 //                    record "out done".
 // Finally the caller's stream waits for both slots' "out done", so the host
 // results are valid once the caller's stream reaches the call (the usual
-// stream-ordered semantics).  Host memory should be page-locked for the copies
+// stream-ordered semantics).  On a failure part-way, the call returns after
+// the copies it had enqueued have finished.  Host memory should be page-locked for the copies
 // to overlap; pageable memory works but serialises.
 #include <cuda_runtime.h>
 
@@ -83,6 +84,7 @@ extern "C" bg_status bg_host_staging_size(const bg_plan* plan, int64_t chunk, si
 extern "C" bg_status bg_eval_host(const bg_plan* plan, int64_t E, const void* momenta, const void* eps,
                                   void* out, uint8_t* status, int64_t chunk, void* staging,
                                   size_t staging_bytes, cudaStream_t stream) {
+    bgi::Range nvtx("bg_eval_host");
     if (!plan) return bgi::fail(BG_ERR_INVALID_ARG, "plan is NULL");
     if (E < 0 || chunk < 1) return bgi::fail(BG_ERR_INVALID_ARG, "E must be >= 0 and chunk >= 1");
     if (E == 0) return BG_OK;
@@ -123,6 +125,15 @@ extern "C" bg_status bg_eval_host(const bg_plan* plan, int64_t E, const void* mo
     const unsigned char* kin = static_cast<const unsigned char*>(momenta);
     const unsigned char* ein = static_cast<const unsigned char*>(eps);
     unsigned char* oh = static_cast<unsigned char*>(out);
+    // A failure after earlier chunks were enqueued returns only once the
+    // copies already enqueued have finished (they read and write the
+    // caller's buffers); kernels enqueued on `stream` stay ordered there.
+    auto drained = [&](bg_status st) {
+        cudaStreamSynchronize(hp->s_in);
+        cudaStreamSynchronize(hp->s_out);
+        cudaGetLastError();
+        return st;
+    };
     int64_t c = 0;
     for (int64_t start = 0; start < E; start += chunk, ++c) {
         const int s = (int)(c & 1);
@@ -131,6 +142,8 @@ extern "C" bg_status bg_eval_host(const bg_plan* plan, int64_t E, const void* mo
         unsigned char* de = dk + sz.k;
         unsigned char* dout = de + sz.eps;
         uint8_t* dst = reinterpret_cast<uint8_t*>(dout + sz.out);
+        if (bgi::fault(BG_FAULT_COPY))
+            return drained(bgi::fail(BG_ERR_CUDA, "enqueueing chunk %lld: injected copy fault", (long long)c));
         cudaError_t err = cudaStreamWaitEvent(hp->s_in, hp->k_done[s], 0);
         if (!err) err = cudaMemcpyAsync(dk, kin + start * k_pt, m * k_pt, cudaMemcpyHostToDevice, hp->s_in);
         if (!err) err = cudaMemcpyAsync(de, ein + start * e_pt, m * e_pt, cudaMemcpyHostToDevice, hp->s_in);
@@ -139,9 +152,9 @@ extern "C" bg_status bg_eval_host(const bg_plan* plan, int64_t E, const void* mo
         if (!err) err = cudaStreamWaitEvent(stream, hp->out_done[s], 0);
         if (err) {
             cudaGetLastError();
-            return bgi::fail(BG_ERR_CUDA, "enqueueing chunk %lld: %s", (long long)c, cudaGetErrorString(err));
+            return drained(bgi::fail(BG_ERR_CUDA, "enqueueing chunk %lld: %s", (long long)c, cudaGetErrorString(err)));
         }
-        if ((st = bg_eval(plan, m, dk, de, dout, dst, ws, ws_bytes, stream)) != BG_OK) return st;
+        if ((st = bg_eval(plan, m, dk, de, dout, dst, ws, ws_bytes, stream)) != BG_OK) return drained(st);
         err = cudaEventRecord(hp->k_done[s], stream);
         if (!err) err = cudaStreamWaitEvent(hp->s_out, hp->k_done[s], 0);
         if (!err) err = cudaMemcpyAsync(oh + start * o_pt, dout, m * o_pt, cudaMemcpyDeviceToHost, hp->s_out);
@@ -149,7 +162,7 @@ extern "C" bg_status bg_eval_host(const bg_plan* plan, int64_t E, const void* mo
         if (!err) err = cudaEventRecord(hp->out_done[s], hp->s_out);
         if (err) {
             cudaGetLastError();
-            return bgi::fail(BG_ERR_CUDA, "enqueueing chunk %lld: %s", (long long)c, cudaGetErrorString(err));
+            return drained(bgi::fail(BG_ERR_CUDA, "enqueueing chunk %lld: %s", (long long)c, cudaGetErrorString(err)));
         }
     }
     cudaError_t err = cudaStreamWaitEvent(stream, hp->out_done[0], 0);

@@ -2,6 +2,7 @@
 // (not part of the public C-ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <vector>
@@ -38,6 +39,18 @@ struct bg_plan {
 };
 
 namespace bgi {
+// True when the current operation at `site` (a bg_fault_site) is one that
+// bg_debug_inject_fault asked to fail; counts the operation either way.
+bool fault(int site);
+
+// NVTX range around an entry point (visible in Nsight; no cost without a tool)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
+
 const std::vector<bgk::KernelEntry>& registry();
 const std::vector<bgk::StatesEntry>& states_registry();
 bg_status fail(bg_status s, const char* fmt, ...);

@@ -59,6 +59,7 @@ bg_status scratch_address(int dev, void** out) {
 extern "C" bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void* momenta,
                                      const void* eps, void* out, uint8_t* status,
                                      cudaStream_t stream) {
+    bgi::Range nvtx("bg_eval_noalloc");
     if (!plan) return bgi::fail(BG_ERR_INVALID_ARG, "plan is NULL");
     if (E < 0) return bgi::fail(BG_ERR_INVALID_ARG, "E = %lld < 0", (long long)E);
     if (E == 0) return BG_OK;
@@ -116,6 +117,7 @@ extern "C" bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void*
     if (blocks > resident) blocks = resident;
     if (blocks > fit) blocks = fit;
 
+    if (bgi::fault(BG_FAULT_LAUNCH)) return bgi::fail(BG_ERR_CUDA, "launch failed: injected fault");
     bgk::CompactArgs a;
     a.E = E; a.H = plan->H; a.S = plan->S; a.n = plan->n;
     a.d_in = plan->d; a.ds_in = plan->Ds;

@@ -152,6 +152,8 @@ bg_status launch_request(bg_server* s, Request* r) {
     const size_t nk = (size_t)r->E * r->plan->n * r->plan->d * bgi::momentum_bytes(r->plan->field);
     const size_t ne = (size_t)r->E * r->plan->n * r->plan->S * r->plan->Ds * elem;
     const size_t no = (size_t)r->E * r->plan->H * elem;
+    bgi::Range nvtx("bg_serve_request");
+    if (bgi::fault(BG_FAULT_COPY)) return BG_ERR_CUDA;
     cudaError_t err = cudaMemcpyAsync(dk, r->k, nk, cudaMemcpyHostToDevice, st);
     if (!err) err = cudaMemcpyAsync(de, r->eps, ne, cudaMemcpyHostToDevice, st);
     if (err) { cudaGetLastError(); return BG_ERR_CUDA; }
@@ -244,7 +246,7 @@ bg_status bg_serve_create(size_t budget_bytes, int max_inflight, bg_server** out
         return bgi::fail(BG_ERR_CUDA, "no current CUDA device");
     }
     s->budget = budget_bytes & ~(kGranule - 1);
-    if (cudaMalloc(&s->arena_mem, s->budget) != cudaSuccess) {
+    if (bgi::fault(BG_FAULT_DEVICE_ALLOC) || cudaMalloc(&s->arena_mem, s->budget) != cudaSuccess) {
         cudaGetLastError();
         delete s;
         return bgi::fail(BG_ERR_NOMEM, "device arena of %zu B could not be allocated", budget_bytes);

@@ -82,3 +82,14 @@ def test_mixed_plan_rejects_bad_masks_on_host(lib):
     assert lib.bg_plan_create_mixed(5, 6, 6, 1, 2147483629, 0, 1, 1, None, 0xFFFFFFFF, ctypes.byref(h)) == 1
     assert lib.bg_plan_create_mixed(5, 6, 6, 1, 2147483629, 0, 2, 32, None, 0b110, ctypes.byref(h)) == 2
     assert not h.value
+
+
+def test_fault_injection_arguments(lib):
+    """bg_debug_inject_fault validates its site and counts on the host."""
+    lib.bg_debug_inject_fault.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    assert lib.bg_debug_inject_fault(0, 0, 1) == 1
+    assert lib.bg_debug_inject_fault(4, 0, 1) == 1
+    assert lib.bg_debug_inject_fault(2, -1, 1) == 1
+    assert lib.bg_debug_inject_fault(2, 0, -1) == 1
+    for site in (1, 2, 3):
+        assert lib.bg_debug_inject_fault(site, 0, 0) == 0      # disarm
