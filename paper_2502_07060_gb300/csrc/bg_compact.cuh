@@ -158,6 +158,38 @@ __device__ __forceinline__ X ld_once(const X* p) { return __ldcs(p); }
 template <class X>
 __device__ __forceinline__ void st_once(X* p, X v) { __stcs(p, v); }
 
+// One leg's F_p input vector of K components, the first k_in stored (the
+// rest zero padding).  A vector of exactly K components at an aligned
+// address (vec) is read with 16-byte (K = 4, 8) or 8-byte (K = 6) loads:
+// a thread's row is contiguous, so fewer and wider loads touch the same
+// sectors and the prologue's L1 traffic drops.
+template <int K>
+__device__ __forceinline__ void load_leg_fp(const uint32_t* p, int k_in, bool vec, uint32_t* v) {
+    if (vec) {
+        if constexpr (K % 4 == 0) {
+#pragma unroll
+            for (int q = 0; q < K / 4; ++q) {
+                const uint4 x = ld_once(reinterpret_cast<const uint4*>(p) + q);
+                v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+            }
+            return;
+        } else if constexpr (K % 2 == 0) {
+#pragma unroll
+            for (int q = 0; q < K / 2; ++q) {
+                const uint2 x = ld_once(reinterpret_cast<const uint2*>(p) + q);
+                v[2 * q] = x.x; v[2 * q + 1] = x.y;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int mu = 0; mu < K; ++mu) v[mu] = (mu < k_in) ? ld_once(p + mu) : 0u;
+}
+
+// alignment that load_leg_fp's vector path needs for K-component rows
+template <int K>
+__host__ __device__ constexpr int leg_align() { return K % 4 == 0 ? 16 : 8; }
+
 // The whole recursion for work item u (point e = u / H, assignment h = u % H)
 // with the block's currents at `tab` and its prefix sums, SA and 1/P^2 at
 // `aux` (shared or global memory).
@@ -203,22 +235,43 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) Kacc[mu] = f.kzero();
         KIO::template store<D>(kvec(0), Kacc);
+        if constexpr (F::kIsFp) {
+            const bool vec = a.d_in == D && reinterpret_cast<uintptr_t>(a.k) % leg_align<D>() == 0;
 #pragma unroll 1
-        for (int l = 0; l < N; ++l) {
+            for (int l = 0; l < N; ++l) {
+                uint32_t raw[D];
+                load_leg_fp<D>(kp + l * a.d_in, a.d_in, vec, raw);
 #pragma unroll
-            for (int mu = 0; mu < D; ++mu)
-                if (mu < a.d_in) Kacc[mu] = f.kadd(Kacc[mu], f.kfrom_io(ld_once(kp + l * a.d_in + mu)));
-            KIO::template store<D>(kvec(l + 1), Kacc);
+                for (int mu = 0; mu < D; ++mu) Kacc[mu] = f.kadd(Kacc[mu], f.kfrom_io(raw[mu]));
+                KIO::template store<D>(kvec(l + 1), Kacc);
+            }
+        } else {
+#pragma unroll 1
+            for (int l = 0; l < N; ++l) {
+#pragma unroll
+                for (int mu = 0; mu < D; ++mu)
+                    if (mu < a.d_in) Kacc[mu] = f.kadd(Kacc[mu], f.kfrom_io(ld_once(kp + l * a.d_in + mu)));
+                KIO::template store<D>(kvec(l + 1), Kacc);
+            }
         }
     }
     T eL[DS];
+    [[maybe_unused]] const bool vec_eps =
+        a.ds_in == DS && reinterpret_cast<uintptr_t>(a.eps) % leg_align<DS>() == 0;
 #pragma unroll 1
     for (int l = 0; l < NLEG; ++l) {
         const int s = (a.assign != nullptr) ? a.assign[h * NLEG + l] : 0;
         const io_t* ep = ein + ((e * NLEG + l) * a.S + s) * a.ds_in;
         T v[DS];
+        if constexpr (F::kIsFp) {
+            uint32_t raw[DS];
+            load_leg_fp<DS>(ep, a.ds_in, vec_eps, raw);
 #pragma unroll
-        for (int mu = 0; mu < DS; ++mu) v[mu] = (mu < a.ds_in) ? f.from_io(ld_once(ep + mu)) : f.zero();
+            for (int mu = 0; mu < DS; ++mu) v[mu] = f.from_io(raw[mu]);
+        } else {
+#pragma unroll
+            for (int mu = 0; mu < DS; ++mu) v[mu] = (mu < a.ds_in) ? f.from_io(ld_once(ep + mu)) : f.zero();
+        }
         if (l < N) {
             IO::template store<DS>(jvec(1, l), v);     // current (1, l)
         } else {
