@@ -613,13 +613,19 @@ def serve_workload(args, device):
     done_at = [0.0] * n_req
     tickets = queue.Queue()
 
+    failed = []
+
     def waiter():
         while True:
             item = tickets.get()
             if item is None:
                 return
             i, t = item
-            srv.wait(t)
+            try:
+                if not srv.wait(t, 120000):          # a generous deadline, never an endless wait
+                    failed.append(i)
+            except Exception:                       # noqa: BLE001 -- reported in the result
+                failed.append(i)
             done_at[i] = time.perf_counter()
 
     waiters = [threading.Thread(target=waiter) for _ in range(16)]
@@ -638,6 +644,7 @@ def serve_workload(args, device):
     t_end = max(done_at)
     served = summarise([done_at[i] - (t0 + arrivals[i]) for i in range(n_req)], t0, t_end)
     served["peak_arena_bytes"] = srv.stats()["peak_bytes"]
+    served["failed_requests"] = len(failed)
     srv.close()
 
     # (b) plain per-request launches, one at a time in arrival order
@@ -690,6 +697,7 @@ def main():
                     help="comma list of fp, c64 (real momenta, the physical points), c64c (the same "
                          "points through the complex-momentum plan)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving latency leg")
     ap.add_argument("--workload", choices=["metric", "mixed", "serve", "helicity", "sweep", "fourdim"],
                     default="metric",
                     help="metric: n=8 d=6 headline line; mixed: uneven-batch comparison; "
@@ -700,7 +708,7 @@ def main():
     ap.add_argument("--log2-points-helicity", type=int, default=20,
                     help="points per n of the helicity workload")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -851,6 +859,22 @@ def main():
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline("fp")
+    if rank == 0 and world == 1 and not args.no_serve:
+        # the metric's serving half (one GPU): p50/p99 latency of the request
+        # server against plain per-request launches (the serve workload)
+        try:
+            sv = serve_workload(args, device)
+            line["serving"] = {
+                "workload": sv["workload"], "unit": "ms",
+                "p50_ms": sv["server"]["p50_ms"], "p99_ms": sv["server"]["p99_ms"],
+                "throughput_points_per_s": sv["server"]["throughput_points_per_s"],
+                "failed_requests": sv["server"]["failed_requests"],
+                "plain_per_request_p50_ms": sv["plain_per_request"]["p50_ms"],
+                "plain_per_request_p99_ms": sv["plain_per_request"]["p99_ms"],
+                "plain_per_request_throughput_points_per_s":
+                    sv["plain_per_request"]["throughput_points_per_s"]}
+        except Exception as exc:                    # noqa: BLE001 -- keep the throughput line
+            line["serving"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
