@@ -56,7 +56,7 @@ def kernel_mults(n, d, Ds):
     for m in range(2, N + 1):
         ranges = N - m + 1
         per = (m - 1) * Ds                       # adjacent dots
-        per += (m - 1) * 2 * d                   # P_A.J_B and P_B.J_A
+        per += (m - 1) * 2 * d                   # P.J_B and P.J_A (range momentum P)
         per += (m - 1) * d                       # momentum part of V3
         per += (m - 1) * 2 * Ds                  # prefix and suffix scalar-vector products
         per += (m - 1) * (m - 2) // 2 * 2 * Ds   # gap dots and inner scalar-vector products
@@ -81,14 +81,13 @@ def kernel_fp64_ops(n, d, Ds, real_k):
     tot = 0
     for m in range(2, N + 1):
         ranges = N - m + 1
-        per = (m - 1) * 2 * d * kc               # P_A, P_B
-        per += (m - 1) * 4 * Ds                  # adjacent dots
-        per += (m - 1) * 2 * d * km              # P_A.J_B and P_B.J_A
+        per = (m - 1) * 4 * Ds                   # adjacent dots
+        per += (m - 1) * 2 * d * km              # P.J_B and P.J_A (current conservation)
         per += (m - 1) * (2 + 2 + 4 + 2)         # coefficient algebra (SA, doubling)
         per += (m - 1) * 8 * Ds                  # prefix and suffix scalar-vector products
         per += (m - 1) * d * km                  # momentum term
         per += (m - 1) * (m - 2) // 2 * (8 * Ds + 2)   # gap dots and inner products
-        per += d * kc + d * km                   # K_i + K_j and -SA (K_i + K_j)
+        per += 2 * d * kc + d * km               # P = K_j - K_i, K_i + K_j and -SA (K_i + K_j)
         if m < N:
             per += Ds * (2 if real_k else 4)     # J = R / P^2
             per += d * kc + d * (1 if real_k else 4)   # P^2

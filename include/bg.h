@@ -179,7 +179,11 @@ bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes);
  * Buffers must be on the device that is current at the call, and momenta,
  * eps and out must be aligned to their element size.  Preconditions not
  * checked on the device: canonical F_p inputs (< p), sum k = 0, k_i^2 = 0,
- * eps_i . k_i = 0 (violations give well-defined but meaningless numbers).
+ * eps_i . k_i = 0 for every state.  The kernels use the current conservation
+ * that on-shell, transverse inputs imply (P_X . J_X = 0 for every internal
+ * current, so the three-gluon coefficients are formed with the range
+ * momentum); on inputs that violate the preconditions the numbers are
+ * well-defined but not the literal recursion's.
  */
 bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta,
                   const void* eps, void* out, uint8_t* status,

@@ -18,7 +18,10 @@
 //     = 2 sum_s (J_A.J_B) K_{s+1} - SA([i,j]) (K_i + K_{j+1}),
 // where SA(X) = sum over the splits X = Y|Z of J_Y.J_Z is accumulated while X
 // itself is built and stored next to its current.  Per range of length m this
-// costs m(m+1)/2 - 1 vector updates instead of 2(m-1) + 3 C(m-1,2).
+// costs m(m+1)/2 - 1 vector updates instead of 2(m-1) + 3 C(m-1,2).  The
+// coefficients P_B.J_A and P_A.J_B are taken as P.J_A and P.J_B with P the
+// range momentum: currents of on-shell legs with transverse states are
+// conserved (P_X.J_X = 0), the documented precondition of the inputs.
 //
 // Per-point table for N = n - 1 legs (layout: TableIO below):
 //   currents of length 1..N-1 (D_s each), prefix sums K_0..K_N of the momenta
@@ -335,9 +338,22 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
     auto range = [&](auto live_d, auto live_ds, const int m, const int i) {
         constexpr int DL = decltype(live_d)::value;
         constexpr int DSL = decltype(live_ds)::value;
-        TK Ki[DL], Kj[DL];
-        KIO::template load_live<D, DL>(kvec(i), Ki);
-        KIO::template load_live<D, DL>(kvec(i + m), Kj);
+        // K_i + K_{j+1} (the -SA(i,j) momentum term) and the range momentum
+        // P = P_[i,j] = K_{j+1} - K_i.  Current conservation (P_X . J_X = 0
+        // for every current of on-shell legs with transverse states) gives
+        // P_B . J_A = P . J_A and P_A . J_B = P . J_B for every split A|B, so
+        // the split momenta P_A, P_B are never formed.
+        TK KiKj[DL], P[DL];
+        {
+            TK Ki[DL], Kj[DL];
+            KIO::template load_live<D, DL>(kvec(i), Ki);
+            KIO::template load_live<D, DL>(kvec(i + m), Kj);
+#pragma unroll
+            for (int mu = 0; mu < DL; ++mu) {
+                KiKj[mu] = f.kadd(Ki[mu], Kj[mu]);
+                P[mu] = f.ksub(Kj[mu], Ki[mu]);
+            }
+        }
         Acc acc[DSL];
         f.template acc_zero<DSL>(acc);
         C sa = f.czero();
@@ -353,19 +369,14 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
         for (int b = 0; b < m - 1; ++b) {
             const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
             T pb[DSL], sf[DSL];
-            TK Kt[DL], PA[DL], PB[DL];
+            TK Kt[DL];
             IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, ps), pb);
             IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, ss), sf);
             KIO::template load_live<D, DL>(kvec(i + b + 1), Kt);
-#pragma unroll
-            for (int mu = 0; mu < DL; ++mu) {
-                PA[mu] = f.ksub(Kt[mu], Ki[mu]);
-                PB[mu] = f.ksub(Kj[mu], Kt[mu]);
-            }
             // three-gluon vertex of the split at s = i + b
             const C adj = f.template dot<DSL, METRIC>(pb, sf);
-            const C pa_jb = f.template kdot<DL, METRIC>(PA, sf);
-            const C pb_ja = f.template kdot<DL, METRIC>(PB, pb);
+            const C pa_jb = f.template kdot<DL, METRIC>(P, sf);     // P_A . J_B = P . J_B
+            const C pb_ja = f.template kdot<DL, METRIC>(P, pb);     // P_B . J_A = P . J_A
             sa = f.cadd(sa, adj);
             C csuf = f.cdbl(pb_ja);
             if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(Sr[(ps - N) * BLOCK]));     // SA(prefix)
@@ -437,13 +448,8 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
             ss -= N - lenB + 1;              // suffix length lenB -> lenB-1
             es += N - b + 1;                 // inner slots ending at i+b+1
         }
-        {
-            TK KiKj[DL];
-#pragma unroll
-            for (int mu = 0; mu < DL; ++mu) KiKj[mu] = f.kadd(Ki[mu], Kj[mu]);
-            if (mom_pending) f.template kacc2<DL>(acc, mom_c, mom_v, f.cneg(sa), KiKj);
-            else f.template kacc1<DL>(acc, f.cneg(sa), KiKj);     // - SA(i,j) (K_i + K_j)
-        }
+        if (mom_pending) f.template kacc2<DL>(acc, mom_c, mom_v, f.cneg(sa), KiKj);
+        else f.template kacc1<DL>(acc, f.cneg(sa), KiKj);         // - SA(i,j) (K_i + K_j)
         if (m < N) {
             const int sidx = g.sbase(m) + i;
             T J[DS];
