@@ -245,9 +245,19 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
             auto sav = [&](int len, int start, uint32_t ver) {
                 return tp[g.sa[len][start] + static_cast<int>(ver)];
             };
-            TK Ki[D], Kj[D];
-            KIO::template load<D>(Kr + i * D, Ki);
-            KIO::template load<D>(Kr + (i + m) * D, Kj);
+            // K_i + K_{j+1} and the range momentum P (current conservation:
+            // P_B . J_A = P . J_A and P_A . J_B = P . J_B, as in bg_compact.cuh)
+            TK KiKj[D], P[D];
+            {
+                TK Ki[D], Kj[D];
+                KIO::template load<D>(Kr + i * D, Ki);
+                KIO::template load<D>(Kr + (i + m) * D, Kj);
+#pragma unroll
+                for (int mu = 0; mu < D; ++mu) {
+                    KiKj[mu] = f.kadd(Ki[mu], Kj[mu]);
+                    P[mu] = f.ksub(Kj[mu], Ki[mu]);
+                }
+            }
             Acc acc[DS];
             f.template acc_zero<DS>(acc);
             C sa = f.czero();
@@ -260,18 +270,13 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
                 qB = divl(i + b).div(qB);
                 const uint32_t sA = sig - qB * wv(i, lenA);
                 T pb[DS], sf[DS];
-                TK Kt[D], PA[D], PB[D];
+                TK Kt[D];
                 IO::template load<DS>(cur(lenA, i, sA), pb);
                 IO::template load<DS>(cur(lenB, i + b + 1, qB), sf);
                 KIO::template load<D>(Kr + (i + b + 1) * D, Kt);
-#pragma unroll
-                for (int mu = 0; mu < D; ++mu) {
-                    PA[mu] = f.ksub(Kt[mu], Ki[mu]);
-                    PB[mu] = f.ksub(Kj[mu], Kt[mu]);
-                }
                 const C adj = f.template dot<DS, METRIC>(pb, sf);
-                const C pa_jb = f.template kdot<D, METRIC>(PA, sf);
-                const C pb_ja = f.template kdot<D, METRIC>(PB, pb);
+                const C pa_jb = f.template kdot<D, METRIC>(P, sf);
+                const C pb_ja = f.template kdot<D, METRIC>(P, pb);
                 sa = f.cadd(sa, adj);
                 C csuf = f.cdbl(pb_ja);
                 if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(sav(lenA, i, sA)));
@@ -314,13 +319,8 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
                     f.template acc1<DS>(acc, g0, in0);
                 }
             }
-            {
-                TK KiKj[D];
-#pragma unroll
-                for (int mu = 0; mu < D; ++mu) KiKj[mu] = f.kadd(Ki[mu], Kj[mu]);
-                if (mom_pending) f.template kacc2<D>(acc, mom_c, mom_v, f.cneg(sa), KiKj);
-                else f.template kacc1<D>(acc, f.cneg(sa), KiKj);
-            }
+            if (mom_pending) f.template kacc2<D>(acc, mom_c, mom_v, f.cneg(sa), KiKj);
+            else f.template kacc1<D>(acc, f.cneg(sa), KiKj);
             if (m < N) {
                 T J[DS];
                 f.template finish<DS>(acc, tp[g.off_inv + g.inv[m] + i], J);
