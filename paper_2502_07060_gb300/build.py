@@ -63,8 +63,12 @@ def build(jobs=None, verbose=False, force=False):
         objs.append(o)
         if force or _stale(o, s, hdr_mtime):
             todo.append((s, o))
-    # largest translation units first so the pool drains evenly
-    todo.sort(key=lambda so: ("n1" in so[0], so[0]), reverse=True)
+    # the slowest translation units (the two batch kernels, the unrolled
+    # per-n kernels) first, so the pool drains evenly
+    def weight(src):
+        b = os.path.basename(src)
+        return (b.startswith("bg_batch_"), b.startswith("bg_inst_fp_n"), b)
+    todo.sort(key=lambda so: weight(so[0]), reverse=True)
     logs = {}
     if todo:
         with ThreadPoolExecutor(max_workers=jobs or os.cpu_count() or 4) as ex:

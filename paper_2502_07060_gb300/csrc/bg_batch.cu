@@ -22,8 +22,8 @@
 
 namespace {
 
-constexpr int kBlockFpBatch = 128;
-constexpr int kBlockC64Batch = 64;
+using bgk::kBlockC64Batch;
+using bgk::kBlockFpBatch;
 constexpr int kTuneTiles[] = {256, 1024, 4096};     // autotune candidates (points per tile)
 constexpr int kTuneFpCaps[] = {0, 4, 2};            // F_p blocks per SM (0 = all that fit)
 constexpr int kTuneC64Caps[] = {0, 3, 2, 1};        // C64 blocks per SM
@@ -118,8 +118,7 @@ bg_status build_layout(const bg_group* groups, int n_groups, const bg_batch_conf
     for (int f = 0; f < 2; ++f) {
         FieldPart& P = L->part[f];
         if (P.tiles.empty()) continue;
-        const void* func = f ? (const void*)&bgk::bg_batch_kernel<bgk::FpOps, kBlockFpBatch>
-                             : (const void*)&bgk::bg_batch_kernel<bgk::C64Ops, kBlockC64Batch>;
+        const void* func = f ? bgk::batch_kernel_fp() : bgk::batch_kernel_c64();
         const int block = f ? kBlockFpBatch : kBlockC64Batch;
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, block, 0) != cudaSuccess || occ < 1) {
@@ -248,8 +247,8 @@ bg_status bg_batch_create(const bg_group* groups, int n_groups, const bg_batch_c
         a.counter = reinterpret_cast<int*>(b->ws) + f;
         a.tables = b->ws + P.off_tables;
         a.words = P.words;
-        if (f) bgk::bg_batch_kernel<bgk::FpOps, kBlockFpBatch><<<P.blocks, kBlockFpBatch, 0, s0>>>(a);
-        else bgk::bg_batch_kernel<bgk::C64Ops, kBlockC64Batch><<<P.blocks, kBlockC64Batch, 0, s1>>>(a);
+        if (f) bgk::launch_batch_fp(a, P.blocks, s0);
+        else bgk::launch_batch_c64(a, P.blocks, s1);
         err = cudaGetLastError();
     }
     if (!err) err = cudaEventRecord(join, s1);

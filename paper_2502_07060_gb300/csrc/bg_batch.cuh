@@ -103,4 +103,14 @@ __global__ void __launch_bounds__(BLOCK) bg_batch_kernel(const BatchArgs a) {
     }
 }
 
+// The two batch kernels are instantiated in translation units of their own
+// (bg_batch_fp.cu, bg_batch_c64.cu): each holds the recursion body of every
+// (D, D_s, metric), and compiled apart they build in parallel.
+constexpr int kBlockFpBatch = 128;
+constexpr int kBlockC64Batch = 64;
+const void* batch_kernel_fp();     // the __global__ functions (occupancy queries)
+const void* batch_kernel_c64();
+void launch_batch_fp(const BatchArgs& a, int blocks, cudaStream_t s);
+void launch_batch_c64(const BatchArgs& a, int blocks, cudaStream_t s);
+
 }  // namespace bgk
