@@ -327,7 +327,7 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
         }
     }
 
-    // a4: the recursion, by increasing length m.  Slot indices of the
+    // a4: the recursion over all ranges [i, i+m-1].  Slot indices of the
     // sub-currents are advanced incrementally (count(L) = N - L + 1 slots per
     // length L) instead of being recomputed from jbase() at every access.
     // The range [i, i+m-1] is evaluated with DL momentum and DSL current
@@ -464,9 +464,14 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
         }
     };
 #pragma unroll 1
-    for (int m = 2; m <= N; ++m) {
+    // Ranges by right end j, and for each j from the shortest [j-1, j] to the
+    // longest [0, j]: every sub-range is finished before it is read, and
+    // consecutive ranges share their suffix currents [s+1, j] (better L1 reuse
+    // than ordering by length; measured 1-3 % at n = 8).
+    for (int jj = 1; jj < N; ++jj) {
 #pragma unroll 1
-        for (int i = 0; i + m - 1 < N; ++i) {
+        for (int i = jj - 1; i >= 0; --i) {
+            const int m = jj - i + 1;
             if constexpr (MIXED && DS > 4) {
                 const uint32_t legs = ((1u << m) - 1u) << i;
                 if ((a.four_d_legs & legs) == legs) {
