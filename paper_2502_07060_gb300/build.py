@@ -83,7 +83,23 @@ def build(jobs=None, verbose=False, force=False):
     if verbose:
         for s, log in logs.items():
             print(f"== {os.path.basename(s)}\n{log}")
+    build_pipe_benchmark()
     return LIB
+
+
+PEAKS_SRC = os.path.join(CSRC, "peaks", "pipe_throughput.cu")
+PEAKS_BIN = os.path.join(OUT, "pipe_throughput")
+
+
+def build_pipe_benchmark():
+    """The stand-alone multiply-pipe benchmark behind the roofline peaks
+    (run it as _build/pipe_throughput on a GB300)."""
+    if os.path.exists(PEAKS_BIN) and os.path.getmtime(PEAKS_BIN) >= os.path.getmtime(PEAKS_SRC):
+        return PEAKS_BIN
+    tmp = PEAKS_BIN + f".tmp{os.getpid()}"
+    subprocess.run([_nvcc(), *ARCH, "-O3", "-o", tmp, PEAKS_SRC], check=True, capture_output=True, text=True)
+    os.replace(tmp, PEAKS_BIN)
+    return PEAKS_BIN
 
 
 if __name__ == "__main__":
