@@ -391,6 +391,19 @@ int bg_version(void);
  *                          served request, from its bg_serve_wait)
  * Returns BG_ERR_INVALID_ARG for an unknown site or negative skip / count.
  */
+/*
+ * bg_debug_bounds_report -- testing aid for memory safety (no counterpart in
+ * the paper).  A library compiled with BG_CHECKED compares every index into
+ * the recursion tables with the extent of its region before the access; a
+ * violation is recorded as (site << 32 | index) -- the first one since the
+ * last report -- and the access is redirected to slot 0 of the thread's own
+ * table.  This call returns *checked = 1 and that record (0 = none) for the
+ * current device in such a build and clears it; in an ordinary build it
+ * returns *checked = 0 and *first_violation = 0 (no checks are compiled).
+ * Call it after the evaluations have completed (synchronise first).
+ */
+bg_status bg_debug_bounds_report(int* checked, uint64_t* first_violation);
+
 typedef enum {
     BG_FAULT_DEVICE_ALLOC = 1,
     BG_FAULT_LAUNCH = 2,

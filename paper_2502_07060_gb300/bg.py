@@ -36,9 +36,11 @@ EXPORTED = ("bg_plan_create", "bg_plan_create_product", "bg_plan_create_mixed", 
             "bg_batch_create", "bg_batch_launch", "bg_batch_describe", "bg_batch_destroy",
             "bg_batch_autotune", "bg_serve_create", "bg_serve_submit", "bg_serve_wait",
             "bg_serve_stats", "bg_serve_destroy", "bg_plan_describe", "bg_strerror", "bg_last_error",
-            "bg_version", "bg_debug_inject_fault")
+            "bg_version", "bg_debug_inject_fault", "bg_debug_bounds_report")
 
-LIB_PATH = _build.LIB
+# BG_LIBRARY selects another build of the same library (the bounds-checked
+# one, _build.build(checked=True)); default: the ordinary in-tree build
+LIB_PATH = os.environ.get("BG_LIBRARY") or _build.LIB
 
 
 class BgGroup(ctypes.Structure):
@@ -120,6 +122,8 @@ def load_library(path=None):
     lib.bg_strerror.restype = ctypes.c_char_p
     lib.bg_last_error.argtypes = []
     lib.bg_last_error.restype = ctypes.c_char_p
+    lib.bg_debug_bounds_report.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64)]
+    lib.bg_debug_bounds_report.restype = ctypes.c_int
     lib.bg_debug_inject_fault.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.bg_debug_inject_fault.restype = ctypes.c_int
     lib.bg_version.argtypes = []
@@ -472,3 +476,10 @@ def inject_fault(site, skip=0, count=1):
     """bg_debug_inject_fault: operations skip .. skip+count-1 at `site` fail
     as if the CUDA runtime had refused them (count = 0 disarms)."""
     _check(_lib.bg_debug_inject_fault(site, skip, count))
+
+
+def bounds_report():
+    """bg_debug_bounds_report: (checked build?, first violation or 0); clears it."""
+    c, v = ctypes.c_int(), ctypes.c_uint64()
+    _check(_lib.bg_debug_bounds_report(ctypes.byref(c), ctypes.byref(v)))
+    return bool(c.value), v.value

@@ -40,8 +40,8 @@ def _stale(obj, src, hdr_mtime):
     return t < os.path.getmtime(src) or t < hdr_mtime
 
 
-def _compile(src, obj, verbose):
-    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-I", INCLUDE, "-c", src, "-o", obj + ".tmp"]
+def _compile(src, obj, verbose, extra=()):
+    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", src, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -51,15 +51,23 @@ def _compile(src, obj, verbose):
     return r.stderr
 
 
-def build(jobs=None, verbose=False, force=False):
-    """Compile and link libbg.so; returns its path."""
-    os.makedirs(os.path.join(OUT, "obj"), exist_ok=True)
+CHECKED_OUT = os.path.join(OUT, "checked")
+CHECKED_LIB = os.path.join(CHECKED_OUT, "libbg.so")
+
+
+def build(jobs=None, verbose=False, force=False, checked=False):
+    """Compile and link libbg.so; returns its path.  checked=True builds the
+    bounds-checked variant (-DBG_CHECKED) into _build/checked/ instead."""
+    out = CHECKED_OUT if checked else OUT
+    lib = CHECKED_LIB if checked else LIB
+    extra = ["-DBG_CHECKED"] if checked else []
+    os.makedirs(os.path.join(out, "obj"), exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_mtime = max(os.path.getmtime(h) for h in _headers())
     todo = []
     objs = []
     for s in srcs:
-        o = os.path.join(OUT, "obj", os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(out, "obj", os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, s, hdr_mtime):
             todo.append((s, o))
@@ -72,19 +80,20 @@ def build(jobs=None, verbose=False, force=False):
     logs = {}
     if todo:
         with ThreadPoolExecutor(max_workers=jobs or os.cpu_count() or 4) as ex:
-            futs = {ex.submit(_compile, s, o, verbose): s for s, o in todo}
+            futs = {ex.submit(_compile, s, o, verbose, extra): s for s, o in todo}
             for f, s in futs.items():
                 logs[s] = f.result()
-    if todo or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if todo or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
         subprocess.run(cmd, check=True, capture_output=True, text=True)
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose:
         for s, log in logs.items():
             print(f"== {os.path.basename(s)}\n{log}")
-    build_pipe_benchmark()
-    return LIB
+    if not checked:
+        build_pipe_benchmark()
+    return lib
 
 
 PEAKS_SRC = os.path.join(CSRC, "peaks", "pipe_throughput.cu")

@@ -32,6 +32,9 @@ BG_REGS(c64r, 4) BG_REGS(c64r, 6) BG_REGS(c64r, 8)
 
 namespace {
 thread_local std::string g_last_error;
+#ifdef BG_CHECKED
+__device__ unsigned long long g_bounds_violation;   // first out-of-range table index (checked builds)
+#endif
 }  // namespace
 
 namespace bgi {
@@ -44,6 +47,23 @@ struct FaultPlan {
 };
 FaultPlan g_fault[4];
 }  // namespace
+
+unsigned long long* violation_word(int device) {
+#ifdef BG_CHECKED
+    static std::mutex mu;
+    static void* addr[64] = {};
+    if (device < 0 || device >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[device] && cudaGetSymbolAddress(&addr[device], g_bounds_violation) != cudaSuccess) {
+        cudaGetLastError();
+        addr[device] = nullptr;
+    }
+    return static_cast<unsigned long long*>(addr[device]);
+#else
+    (void)device;
+    return nullptr;
+#endif
+}
 
 bool fault(int site) {
     if (site < 1 || site > 3) return false;
@@ -237,6 +257,23 @@ const char* bg_strerror(bg_status s) {
 const char* bg_last_error(void) { return g_last_error.c_str(); }
 
 int bg_version(void) { return BG_VERSION; }
+
+bg_status bg_debug_bounds_report(int* checked, uint64_t* first_violation) {
+    if (!checked || !first_violation) return fail(BG_ERR_INVALID_ARG, "checked and first_violation must be non-NULL");
+    *checked = 0;
+    *first_violation = 0;
+#ifdef BG_CHECKED
+    unsigned long long v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_violation, sizeof v) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_bounds_violation, &zero, sizeof zero) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BG_ERR_CUDA, "could not read the bounds-violation word");
+    }
+    *checked = 1;
+    *first_violation = v;
+#endif
+    return BG_OK;
+}
 
 bg_status bg_debug_inject_fault(bg_fault_site site, int skip, int count) {
     if ((int)site < 1 || (int)site > 3 || skip < 0 || count < 0)
@@ -566,6 +603,7 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const voi
         a.E = E; a.n = plan->n; a.d_in = plan->d; a.ds_in = plan->Ds;
         a.k = momenta; a.eps = eps; a.out = out; a.status = status;
         a.ws = plan->states_global ? workspace : nullptr;
+        a.violation = bgi::violation_word(dev);
         if (bgi::fault(BG_FAULT_LAUNCH)) return fail(BG_ERR_CUDA, "launch failed: injected fault");
         plan->sentry->launch(compact_params(plan), a, plan->sgeo, dim3((unsigned)blocks), plan->smem_bytes,
                              stream);
@@ -585,6 +623,7 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const voi
         a.k = momenta; a.eps = eps; a.out = out; a.status = status;
         a.assign = plan->d_assign; a.ws = workspace;
         a.four_d_legs = plan->four_d_legs;
+        a.violation = bgi::violation_word(dev);
         e->launch(compact_params(plan), &a, dim3((unsigned)blocks), plan->smem_bytes, stream);
     } else {
         bgk::LaunchArgs a;

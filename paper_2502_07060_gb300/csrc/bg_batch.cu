@@ -98,6 +98,7 @@ bg_status build_layout(const bg_group* groups, int n_groups, const bg_batch_conf
         bgd.args.assign = pl->d_assign;
         bgd.args.ws = nullptr;
         bgd.args.four_d_legs = 0;   // full width: exact for mixed plans as well
+        bgd.args.violation = bgi::violation_word(pl->device);
         bgd.variant = 2 * bgk::batch_pair_index(D, DS) + (int)pl->metric +
                       (pl->field == BG_FIELD_C64_REAL ? bgk::kBatchVariants : 0);
         bgd.fp = pl->fpo;

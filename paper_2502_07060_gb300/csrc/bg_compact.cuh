@@ -53,7 +53,26 @@ struct CompactArgs {
     const uint8_t* assign;      // device [H][n] or null (H == 1)
     void* ws;                   // global table (global placement)
     uint32_t four_d_legs;       // bit l: leg l is four-dimensional (read by MIXED kernels)
+    unsigned long long* violation;   // checked builds: first out-of-range table index
 };
+
+// Table-index checking (builds compiled with BG_CHECKED; without it the checks
+// vanish).  Every slot index is compared with the extent of its region before
+// the access; a violation records (site << 32 | index) in *violation (the
+// first one wins) and the access goes to slot 0 instead, so a wrong index
+// never leaves the thread's own table.
+__device__ __forceinline__ int checked_slot(unsigned long long* violation, int idx, int extent, int site) {
+#ifdef BG_CHECKED
+    if (idx < 0 || idx >= extent) {
+        if (violation != nullptr)
+            atomicCAS(violation, 0ull, (static_cast<unsigned long long>(site) << 32) | static_cast<uint32_t>(idx));
+        return 0;
+    }
+#else
+    (void)violation; (void)extent; (void)site;
+#endif
+    return idx;
+}
 
 // Table geometry for N = n - 1 recursion legs (host and device), in table
 // elements per thread.  Region starts are rounded up to 4 elements so that
@@ -218,8 +237,12 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
     TK* Kr = reinterpret_cast<TK*>(aux) + (VEC ? t * D : t);      // prefix sums
     T* Sr = aux + (OFF_SA - OFF_K) * BLOCK + t;                    // SA per internal range
     T* Ir = aux + (OFF_INV - OFF_K) * BLOCK + t;                   // 1/P^2 per internal range
-    auto jvec = [&](int len, int start) { return IO::template vec<DS>(Jr, g.jbase(len) + start); };
-    auto kvec = [&](int i) { return KIO::template vec<D>(Kr, i); };
+    const int NJ = g.nj(), NS_ = g.ns();
+    // slot addressing of the four table regions (checked in BG_CHECKED builds)
+    auto jslot = [&](int slot) { return IO::template vec<DS>(Jr, checked_slot(a.violation, slot, NJ, 1)); };
+    auto jvec = [&](int len, int start) { return jslot(g.jbase(len) + start); };
+    auto kvec = [&](int i) { return KIO::template vec<D>(Kr, checked_slot(a.violation, i, N + 1, 2)); };
+    auto sidx_ok = [&](int i) { return checked_slot(a.violation, i, NS_, 3) * BLOCK; };
     const kio_t* kin = static_cast<const kio_t*>(a.k);
     const io_t* ein = static_cast<const io_t*>(a.eps);
     io_t* out = static_cast<io_t*>(a.out);
@@ -294,7 +317,7 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
             KIO::template load<D>(kvec(i + m), Kb);
 #pragma unroll
             for (int mu = 0; mu < D; ++mu) P[mu] = f.ksub(Kb[mu], Ka[mu]);
-            X[(g.sbase(m) + i) * BLOCK] = f.inv_input(f.template kkdot<D, METRIC>(P, P));
+            X[sidx_ok(g.sbase(m) + i)] = f.inv_input(f.template kkdot<D, METRIC>(P, P));
         }
     }
     // a3: all inverses.  F_p: Montgomery simultaneous inversion (prefix
@@ -306,24 +329,24 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
         Y[0] = c;
 #pragma unroll 1
         for (int s = 1; s < NS; ++s) {
-            c = f.inv_mul(c, X[s * BLOCK]);
-            Y[s * BLOCK] = c;
+            c = f.inv_mul(c, X[sidx_ok(s)]);
+            Y[sidx_ok(s)] = c;
         }
         singular = f.is_zero(c);
         T r = f.inv_scalar(c);
 #pragma unroll 1
         for (int s = NS - 1; s > 0; --s) {
-            const T x = X[s * BLOCK];
-            Y[s * BLOCK] = f.inv_store(f.inv_mul(Y[(s - 1) * BLOCK], r));
+            const T x = X[sidx_ok(s)];
+            Y[sidx_ok(s)] = f.inv_store(f.inv_mul(Y[sidx_ok(s - 1)], r));
             r = f.inv_mul(r, x);
         }
         Y[0] = f.inv_store(r);
     } else {
 #pragma unroll 1
         for (int s = 0; s < NS; ++s) {
-            const T x = X[s * BLOCK];
+            const T x = X[sidx_ok(s)];
             singular |= f.is_zero(x);
-            Y[s * BLOCK] = f.inv_scalar(x);
+            Y[sidx_ok(s)] = f.inv_scalar(x);
         }
     }
 
@@ -370,8 +393,8 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
             const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
             T pb[DSL], sf[DSL];
             TK Kt[DL];
-            IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, ps), pb);
-            IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, ss), sf);
+            IO::template load_live<DS, DSL>(jslot(ps), pb);
+            IO::template load_live<DS, DSL>(jslot(ss), sf);
             KIO::template load_live<D, DL>(kvec(i + b + 1), Kt);
             // three-gluon vertex of the split at s = i + b
             const C adj = f.template dot<DSL, METRIC>(pb, sf);
@@ -379,9 +402,9 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
             const C pb_ja = f.template kdot<DL, METRIC>(P, pb);     // P_B . J_A = P . J_A
             sa = f.cadd(sa, adj);
             C csuf = f.cdbl(pb_ja);
-            if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(Sr[(ps - N) * BLOCK]));     // SA(prefix)
+            if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(Sr[sidx_ok(ps - N)]));     // SA(prefix)
             C cpre = f.cneg(f.cdbl(pa_jb));
-            if (lenB >= 2) cpre = f.csub(cpre, f.t_to_c(Sr[(ss - N) * BLOCK]));     // SA(suffix)
+            if (lenB >= 2) cpre = f.csub(cpre, f.t_to_c(Sr[sidx_ok(ss - N)]));     // SA(suffix)
             f.template acc2<DSL>(acc, csuf, sf, cpre, pb);
             // momentum part: adj (P_A - P_B) = adj (2 K_{i+b+1} - K_i - K_j);
             // the K_i + K_j share is added once per range below
@@ -403,17 +426,17 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
 #pragma unroll 1
             for (; F::kIsFp && q + 3 < b; q += 4) {
                 T pa0[DSL], pa1[DSL], pa2[DSL], pa3[DSL], in0[DSL], in1[DSL], in2[DSL], in3[DSL];
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa0);
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in0);
+                IO::template load_live<DS, DSL>(jslot(pq), pa0);
+                IO::template load_live<DS, DSL>(jslot(iq), in0);
                 pq += dp; iq -= di;
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa1);
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in1);
+                IO::template load_live<DS, DSL>(jslot(pq), pa1);
+                IO::template load_live<DS, DSL>(jslot(iq), in1);
                 pq += dp - 1; iq -= di + 1;
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa2);
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in2);
+                IO::template load_live<DS, DSL>(jslot(pq), pa2);
+                IO::template load_live<DS, DSL>(jslot(iq), in2);
                 pq += dp - 2; iq -= di + 2;
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa3);
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in3);
+                IO::template load_live<DS, DSL>(jslot(pq), pa3);
+                IO::template load_live<DS, DSL>(jslot(iq), in3);
                 pq += dp - 3; iq -= di + 3;
                 dp -= 4; di += 4;
                 const C g0 = f.cdbl(f.template dot<DSL, METRIC>(pa0, sf));
@@ -426,11 +449,11 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
 #pragma unroll 1
             for (; q + 1 < b; q += 2) {
                 T pa0[DSL], pa1[DSL], in0[DSL], in1[DSL];
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa0);
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in0);
+                IO::template load_live<DS, DSL>(jslot(pq), pa0);
+                IO::template load_live<DS, DSL>(jslot(iq), in0);
                 pq += dp; iq -= di;
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa1);
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in1);
+                IO::template load_live<DS, DSL>(jslot(pq), pa1);
+                IO::template load_live<DS, DSL>(jslot(iq), in1);
                 pq += dp - 1; iq -= di + 1;
                 dp -= 2; di += 2;
                 const C g0 = f.cdbl(f.template dot<DSL, METRIC>(pa0, sf));
@@ -439,8 +462,8 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
             }
             if (q < b) {
                 T pa0[DSL], in0[DSL];
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, pq), pa0);
-                IO::template load_live<DS, DSL>(IO::template vec<DS>(Jr, iq), in0);
+                IO::template load_live<DS, DSL>(jslot(pq), pa0);
+                IO::template load_live<DS, DSL>(jslot(iq), in0);
                 const C g0 = f.cdbl(f.template dot<DSL, METRIC>(pa0, sf));
                 f.template acc1<DSL>(acc, g0, in0);
             }
@@ -453,11 +476,11 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
         if (m < N) {
             const int sidx = g.sbase(m) + i;
             T J[DS];
-            f.template finish<DSL>(acc, Y[sidx * BLOCK], J);
+            f.template finish<DSL>(acc, Y[sidx_ok(sidx)], J);
 #pragma unroll
             for (int mu = DSL; mu < DS; ++mu) J[mu] = f.zero();     // components beyond a 4d range
             IO::template store<DS>(jvec(m, i), J);
-            Sr[sidx * BLOCK] = f.c_to_t(sa);
+            Sr[sidx_ok(sidx)] = f.c_to_t(sa);
         } else {
             // a5: contract the top bracket with the last polarisation
             result = f.template amplitude<DSL, METRIC>(acc, eL);

@@ -43,6 +43,11 @@ namespace bgi {
 // bg_debug_inject_fault asked to fail; counts the operation either way.
 bool fault(int site);
 
+// Device word receiving the first out-of-range table index of a launch in
+// builds compiled with BG_CHECKED (null otherwise): a static __device__
+// variable whose address is looked up once per device -- nothing allocated.
+unsigned long long* violation_word(int device);
+
 // NVTX range around an entry point (visible in Nsight; no cost without a tool)
 struct Range {
     explicit Range(const char* name) { nvtxRangePushA(name); }

@@ -124,6 +124,7 @@ extern "C" bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void*
     a.k = momenta; a.eps = eps; a.out = out; a.status = status;
     a.assign = plan->d_assign; a.ws = scratch;
     a.four_d_legs = plan->four_d_legs;
+    a.violation = bgi::violation_word(dev);
     e->launch(bgi::compact_params(plan), &a, dim3((unsigned)blocks), 0, stream);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return bgi::fail(BG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(err));

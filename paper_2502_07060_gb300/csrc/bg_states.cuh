@@ -145,6 +145,7 @@ struct StatesArgs {
     void* out;                  // [E][H]
     uint8_t* status;            // [E] or null
     void* ws;                   // global tables (global placement) or null
+    unsigned long long* violation;   // checked builds: first out-of-range table index
 };
 
 // The assignments of the points e0 .. e0+np-1 (np <= P) by one warp; point p's
@@ -173,6 +174,10 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
     };
     auto kr = [&](int p) { return reinterpret_cast<TK*>(tab + p * W + g.off_k); };
     auto flag = [&](int p) { return reinterpret_cast<int*>(tab + p * W + g.off_flag); };
+    // offset of a `width`-element access in a point's table (checked in
+    // BG_CHECKED builds), and of a prefix-sum component in the K region
+    auto at = [&](int off, int width, int site) { return checked_slot(a.violation, off, W - width + 1, site); };
+    auto kat = [&](int idx) { return checked_slot(a.violation, idx, (N + 1) * D, 14); };
 
     // s1: prefix sums K_0 = 0, K_{l+1} = K_l + k_l, one lane per (point, component)
     for (int x = lane; x < np * D; x += 32) {
@@ -180,10 +185,10 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
         const kio_t* kp = static_cast<const kio_t*>(a.k) + (e0 + p) * n * a.d_in;
         TK* Kr = kr(p);
         TK acc = f.kzero();
-        Kr[mu] = acc;
+        Kr[kat(mu)] = acc;
         for (int l = 0; l < N; ++l) {
             if (mu < a.d_in) acc = f.kadd(acc, f.kfrom_io(kp[l * a.d_in + mu]));
-            Kr[(l + 1) * D + mu] = acc;
+            Kr[kat((l + 1) * D + mu)] = acc;
         }
     }
     // s2: polarisations -> currents of length 1 (version = state) and the last
@@ -199,8 +204,8 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
             const io_t* ep = static_cast<const io_t*>(a.eps) + (e0 + p) * n * S * a.ds_in;
             const T v = mu < a.ds_in ? f.from_io(ep[ls * a.ds_in + mu]) : f.zero();
             T* tp = tab + p * W;
-            if (l < N) tp[g.cur[1][l] + t * DS + mu] = v;
-            else tp[g.off_el + t * DS + mu] = v;
+            if (l < N) tp[at(g.cur[1][l] + t * DS + mu, 1, 11)] = v;
+            else tp[at(g.off_el + t * DS + mu, 1, 12)] = v;
         }
         for (int p = lane; p < np; p += 32) *flag(p) = 0;
     }
@@ -216,13 +221,13 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
         }
         const TK* Kr = kr(p);
         TK Ka[D], Kb[D], Pv[D];
-        KIO::template load<D>(Kr + i * D, Ka);
-        KIO::template load<D>(Kr + (i + L) * D, Kb);
+        KIO::template load<D>(Kr + kat(i * D), Ka);
+        KIO::template load<D>(Kr + kat((i + L) * D), Kb);
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) Pv[mu] = f.ksub(Kb[mu], Ka[mu]);
         const T xv = f.inv_input(f.template kkdot<D, METRIC>(Pv, Pv));
         if (f.is_zero(xv)) *flag(p) = 1;
-        tab[p * W + g.off_inv + r] = f.inv_store(f.inv_scalar(xv));
+        tab[p * W + at(g.off_inv + r, 1, 13)] = f.inv_store(f.inv_scalar(xv));
     }
     __threadfence_block();
     __syncwarp();
@@ -240,18 +245,18 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
             T* tp = tab + p * W;
             const TK* Kr = kr(p);
             auto cur = [&](int len, int start, uint32_t ver) {
-                return tp + g.cur[len][start] + static_cast<int>(ver) * DS;
+                return tp + at(g.cur[len][start] + static_cast<int>(ver) * DS, DS, 15);
             };
             auto sav = [&](int len, int start, uint32_t ver) {
-                return tp[g.sa[len][start] + static_cast<int>(ver)];
+                return tp[at(g.sa[len][start] + static_cast<int>(ver), 1, 16)];
             };
             // K_i + K_{j+1} and the range momentum P (current conservation:
             // P_B . J_A = P . J_A and P_A . J_B = P . J_B, as in bg_compact.cuh)
             TK KiKj[D], P[D];
             {
                 TK Ki[D], Kj[D];
-                KIO::template load<D>(Kr + i * D, Ki);
-                KIO::template load<D>(Kr + (i + m) * D, Kj);
+                KIO::template load<D>(Kr + kat(i * D), Ki);
+                KIO::template load<D>(Kr + kat((i + m) * D), Kj);
 #pragma unroll
                 for (int mu = 0; mu < D; ++mu) {
                     KiKj[mu] = f.kadd(Ki[mu], Kj[mu]);
@@ -273,7 +278,7 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
                 TK Kt[D];
                 IO::template load<DS>(cur(lenA, i, sA), pb);
                 IO::template load<DS>(cur(lenB, i + b + 1, qB), sf);
-                KIO::template load<D>(Kr + (i + b + 1) * D, Kt);
+                KIO::template load<D>(Kr + kat((i + b + 1) * D), Kt);
                 const C adj = f.template dot<DS, METRIC>(pb, sf);
                 const C pa_jb = f.template kdot<D, METRIC>(P, sf);
                 const C pb_ja = f.template kdot<D, METRIC>(P, pb);
@@ -323,16 +328,16 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
             else f.template kacc1<D>(acc, f.cneg(sa), KiKj);
             if (m < N) {
                 T J[DS];
-                f.template finish<DS>(acc, tp[g.off_inv + g.inv[m] + i], J);
+                f.template finish<DS>(acc, tp[at(g.off_inv + g.inv[m] + i, 1, 17)], J);
                 IO::template store<DS>(cur(m, i, sig), J);
-                tp[g.sa[m][i] + static_cast<int>(sig)] = f.c_to_t(sa);
+                tp[at(g.sa[m][i] + static_cast<int>(sig), 1, 18)] = f.c_to_t(sa);
             } else {
                 // the top range: contract with each state of the last leg
                 const bool singular = *flag(p) != 0;
                 io_t* o = out + (e0 + p) * g.H + sig;
                 for (int t = 0; t < g.radix[N]; ++t) {
                     T eL[DS];
-                    IO::template load<DS>(tp + g.off_el + t * DS, eL);
+                    IO::template load<DS>(tp + at(g.off_el + t * DS, DS, 19), eL);
                     o[static_cast<int64_t>(t) * count] = singular ? f.zero_io()
                                                                   : f.template amplitude<DS, METRIC>(acc, eL);
                 }
