@@ -52,22 +52,29 @@ __device__ __forceinline__ FpOps batch_field<FpOps>(const BatchGroup& g) { retur
 template <>
 __device__ __forceinline__ C64Ops batch_field<C64Ops>(const BatchGroup&) { return C64Ops{}; }
 
+// One (D, D_s, metric) body as a function of its own (not inlined): each body
+// gets its own register allocation instead of the union of all of them
+template <class F, int D, int DS, int M, int BLOCK>
+__device__ __noinline__ void batch_point(const F f, const CompactArgs* a, typename F::T* tab, int64_t u) {
+    bg_point<F, D, DS, M, BLOCK>(f, *a, tab, u);
+}
+
 template <class F, int BLOCK>
 __device__ __forceinline__ void batch_dims(const F& f, const CompactArgs& a, int variant,
                                            typename F::T* tab, int64_t u) {
     switch (variant) {
-        case 0: bg_point<F, 4, 4, 0, BLOCK>(f, a, tab, u); break;
-        case 1: bg_point<F, 4, 4, 1, BLOCK>(f, a, tab, u); break;
-        case 2: bg_point<F, 4, 6, 0, BLOCK>(f, a, tab, u); break;
-        case 3: bg_point<F, 4, 6, 1, BLOCK>(f, a, tab, u); break;
-        case 4: bg_point<F, 4, 8, 0, BLOCK>(f, a, tab, u); break;
-        case 5: bg_point<F, 4, 8, 1, BLOCK>(f, a, tab, u); break;
-        case 6: bg_point<F, 6, 6, 0, BLOCK>(f, a, tab, u); break;
-        case 7: bg_point<F, 6, 6, 1, BLOCK>(f, a, tab, u); break;
-        case 8: bg_point<F, 6, 8, 0, BLOCK>(f, a, tab, u); break;
-        case 9: bg_point<F, 6, 8, 1, BLOCK>(f, a, tab, u); break;
-        case 10: bg_point<F, 8, 8, 0, BLOCK>(f, a, tab, u); break;
-        default: bg_point<F, 8, 8, 1, BLOCK>(f, a, tab, u); break;
+        case 0: batch_point<F, 4, 4, 0, BLOCK>(f, &a, tab, u); break;
+        case 1: batch_point<F, 4, 4, 1, BLOCK>(f, &a, tab, u); break;
+        case 2: batch_point<F, 4, 6, 0, BLOCK>(f, &a, tab, u); break;
+        case 3: batch_point<F, 4, 6, 1, BLOCK>(f, &a, tab, u); break;
+        case 4: batch_point<F, 4, 8, 0, BLOCK>(f, &a, tab, u); break;
+        case 5: batch_point<F, 4, 8, 1, BLOCK>(f, &a, tab, u); break;
+        case 6: batch_point<F, 6, 6, 0, BLOCK>(f, &a, tab, u); break;
+        case 7: batch_point<F, 6, 6, 1, BLOCK>(f, &a, tab, u); break;
+        case 8: batch_point<F, 6, 8, 0, BLOCK>(f, &a, tab, u); break;
+        case 9: batch_point<F, 6, 8, 1, BLOCK>(f, &a, tab, u); break;
+        case 10: batch_point<F, 8, 8, 0, BLOCK>(f, &a, tab, u); break;
+        default: batch_point<F, 8, 8, 1, BLOCK>(f, &a, tab, u); break;
     }
 }
 
@@ -84,7 +91,7 @@ __device__ __forceinline__ void batch_item(const F& f, const CompactArgs& a, int
 }
 
 template <class F, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) bg_batch_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(BLOCK, 1) bg_batch_kernel(const BatchArgs a) {
     using T = typename F::T;
     __shared__ int s_tile;
     T* tab = reinterpret_cast<T*>(a.tables) + static_cast<size_t>(blockIdx.x) * a.words * BLOCK;
