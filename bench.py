@@ -564,9 +564,11 @@ def serve_workload(args, device):
     """Poisson arrivals (mean rate --serve-rate per second) of requests with
     log-uniform sizes 1..65536 points, n uniform in 4..12, d = D_s uniform in
     {4, 6, 8}, field uniform; latency = completion - arrival.  Served by
-    (a) bg_server (continuous admission, 8 stream slots) and (b) plain
-    per-request evaluation, one request at a time (copy in, bg_eval, copy out,
-    synchronise), in arrival order."""
+    (a) bg_server (continuous admission, 8 stream slots) with host buffers
+    staged through its arena, (c) the same server with the momenta and states
+    resident on the device (a pool uploaded once; results still returned to
+    host memory), and (b) plain per-request evaluation, one request at a time
+    (copy in, bg_eval, copy out, synchronise), in arrival order."""
     import queue
     import threading
 
@@ -590,6 +592,7 @@ def serve_workload(args, device):
     gaps = rng.exponential(1.0 / args.serve_rate, n_req)
     arrivals = np.cumsum(gaps)
     reqs = []
+    placement = []
     for i in range(n_req):
         cfg = configs[rng.integers(len(configs))]
         E = int(np.clip(np.exp(rng.uniform(0, np.log(65536))), 1, 65536))
@@ -598,6 +601,7 @@ def serve_workload(args, device):
         out = torch.empty(E, dtype=hk.dtype).pin_memory()
         st = torch.empty(E, dtype=torch.uint8).pin_memory()
         reqs.append((plans[cfg], hk[off:off + E], he[off:off + E], out, st, E))
+        placement.append((cfg, off))
     total_pts = sum(r[5] for r in reqs)
 
     def summarise(lat, t0, t_end):
@@ -607,44 +611,55 @@ def serve_workload(args, device):
                 "throughput_points_per_s": total_pts / (t_end - t0),
                 "throughput_requests_per_s": n_req / (t_end - t0)}
 
-    # (a) server
-    srv = bg.Server(8 << 30, max_inflight=8)
-    done_at = [0.0] * n_req
-    tickets = queue.Queue()
+    def run_server(req_list):
+        srv = bg.Server(8 << 30, max_inflight=8)
+        done_at = [0.0] * n_req
+        tickets = queue.Queue()
+        failed = []
 
-    failed = []
-
-    def waiter():
-        while True:
-            item = tickets.get()
-            if item is None:
-                return
-            i, t = item
-            try:
-                if not srv.wait(t, 120000):          # a generous deadline, never an endless wait
+        def waiter():
+            while True:
+                item = tickets.get()
+                if item is None:
+                    return
+                i, t = item
+                try:
+                    if not srv.wait(t, 120000):      # a generous deadline, never an endless wait
+                        failed.append(i)
+                except Exception:                   # noqa: BLE001 -- reported in the result
                     failed.append(i)
-            except Exception:                       # noqa: BLE001 -- reported in the result
-                failed.append(i)
-            done_at[i] = time.perf_counter()
+                done_at[i] = time.perf_counter()
 
-    waiters = [threading.Thread(target=waiter) for _ in range(16)]
-    for w in waiters:
-        w.start()
-    t0 = time.perf_counter()
-    for i, r in enumerate(reqs):
-        delay = t0 + arrivals[i] - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        tickets.put((i, srv.submit(r[0], r[1], r[2], r[3], r[4])))
-    for _ in waiters:
-        tickets.put(None)
-    for w in waiters:
-        w.join()
-    t_end = max(done_at)
-    served = summarise([done_at[i] - (t0 + arrivals[i]) for i in range(n_req)], t0, t_end)
-    served["peak_arena_bytes"] = srv.stats()["peak_bytes"]
-    served["failed_requests"] = len(failed)
-    srv.close()
+        waiters = [threading.Thread(target=waiter) for _ in range(16)]
+        for w in waiters:
+            w.start()
+        t0 = time.perf_counter()
+        for i, r in enumerate(req_list):
+            delay = t0 + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.put((i, srv.submit(r[0], r[1], r[2], r[3], r[4])))
+        for _ in waiters:
+            tickets.put(None)
+        for w in waiters:
+            w.join()
+        res = summarise([done_at[i] - (t0 + arrivals[i]) for i in range(n_req)], t0, max(done_at))
+        res["peak_arena_bytes"] = srv.stats()["peak_bytes"]
+        res["failed_requests"] = len(failed)
+        srv.close()
+        return res
+
+    # (a) server, host buffers staged through its arena
+    served = run_server(reqs)
+    # (c) server, momenta and states resident on the device (a pool uploaded
+    # once), results returned to host memory
+    dpools = {cfg: (hk.to(device), he.to(device)) for cfg, (hk, he) in pools.items()}
+    torch.cuda.synchronize(device)
+    resident = [(r[0], dpools[cfg][0][off:off + r[5]], dpools[cfg][1][off:off + r[5]], r[3], r[4], r[5])
+                for r, (cfg, off) in zip(reqs, placement)]
+    served_resident = run_server(resident)
+    del resident, dpools
+    torch.cuda.empty_cache()
 
     # (b) plain per-request launches, one at a time in arrival order
     stream = torch.cuda.current_stream(device)
@@ -680,7 +695,7 @@ def serve_workload(args, device):
     return {"workload": f"Poisson arrivals at {args.serve_rate}/s for {args.serve_seconds} s, "
                         f"{n_req} requests, sizes log-uniform 1..65536 (total {total_pts} points), "
                         "n uniform 4..12, d = D_s uniform {4, 6, 8}, F_p or C64",
-            "server": served, "plain_per_request": plain}
+            "server": served, "server_resident_inputs": served_resident, "plain_per_request": plain}
 
 
 def main():
@@ -867,7 +882,9 @@ def main():
                 "workload": sv["workload"], "unit": "ms",
                 "p50_ms": sv["server"]["p50_ms"], "p99_ms": sv["server"]["p99_ms"],
                 "throughput_points_per_s": sv["server"]["throughput_points_per_s"],
-                "failed_requests": sv["server"]["failed_requests"],
+                "failed_requests": sv["server"]["failed_requests"] + sv["server_resident_inputs"]["failed_requests"],
+                "resident_inputs_p50_ms": sv["server_resident_inputs"]["p50_ms"],
+                "resident_inputs_p99_ms": sv["server_resident_inputs"]["p99_ms"],
                 "plain_per_request_p50_ms": sv["plain_per_request"]["p50_ms"],
                 "plain_per_request_p99_ms": sv["plain_per_request"]["p99_ms"],
                 "plain_per_request_throughput_points_per_s":

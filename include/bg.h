@@ -315,17 +315,21 @@ bg_status bg_batch_autotune(const bg_group* groups, int n_groups, void* workspac
  * requests are still running -- so the copies and kernels of concurrent
  * requests overlap on the device.  Admission is first-come-first-served, but
  * a request that does not fit may be overtaken by later ones until it has
- * waited 50 ms.  Host buffers (momenta, eps, out, status as for bg_eval) must
- * stay valid until bg_serve_wait returns; page-locked memory lets copies
- * overlap.  Every result equals what bg_eval gives for the request alone.
+ * waited 50 ms.  Each buffer (momenta, eps, out, status, layouts as for
+ * bg_eval) is either host memory, staged through the arena (page-locked
+ * memory lets the copies overlap), or device memory of the server's device,
+ * used in place with no copy and no arena bytes: momenta and states kept
+ * resident on the device across requests, outputs left on the device.  All
+ * buffers must stay valid until bg_serve_wait returns.  Every result equals
+ * what bg_eval gives for the request alone.
  */
 typedef struct bg_server bg_server;
 
 bg_status bg_serve_create(size_t budget_bytes, int max_inflight, bg_server** out);
 
 /* bg_serve_submit -- queue E >= 1 points of `plan`; returns a ticket.
- * BG_ERR_INVALID_ARG when the request can never fit the budget; BG_ERR_BUSY
- * after bg_serve_destroy has begun. */
+ * BG_ERR_INVALID_ARG when the request can never fit the budget or a buffer
+ * lives on another device; BG_ERR_BUSY after bg_serve_destroy has begun. */
 bg_status bg_serve_submit(bg_server* srv, const bg_plan* plan, int64_t E, const void* momenta,
                           const void* eps, void* out, uint8_t* status, uint64_t* ticket);
 

@@ -16,6 +16,9 @@
 //   * each admitted request runs on its own stream slot: host->device copies,
 //     one bg_eval launch, device->host copies, then a host function (run by
 //     the CUDA driver, no CUDA calls in it) that marks the slot finished;
+//     buffers already in device memory (a resident pool of momenta and
+//     states, outputs kept on the device) are used in place, with no copy and
+//     no arena bytes;
 //   * bg_serve_wait blocks on a condition variable with a deadline and
 //     returns BG_ERR_TIMEOUT when the request is not done by then.
 #include <cuda_runtime.h>
@@ -91,6 +94,7 @@ struct Request {
     const void* eps;
     void* out;
     uint8_t* status;
+    bool k_dev = false, e_dev = false, out_dev = false, st_dev = false;   // resident on the device
     size_t bytes_k, bytes_e, bytes_o, bytes_s, bytes_ws, total;
     Clock::time_point submitted;
     State state = State::Pending;
@@ -143,24 +147,32 @@ void CUDART_CB slot_finished(void* arg) {
 bg_status launch_request(bg_server* s, Request* r) {
     cudaStream_t st = s->streams[r->slot];
     unsigned char* base = s->arena_mem + r->off;
-    unsigned char* dk = base;
-    unsigned char* de = dk + r->bytes_k;
-    unsigned char* dout = de + r->bytes_e;
-    uint8_t* dst = reinterpret_cast<uint8_t*>(dout + r->bytes_o);
-    unsigned char* ws = dout + r->bytes_o + r->bytes_s;
+    // arena layout: staged momenta, eps, outputs, status, then the workspace;
+    // device-resident buffers take no arena bytes and are used in place
+    unsigned char* ak = base;
+    unsigned char* ae = ak + r->bytes_k;
+    unsigned char* aout = ae + r->bytes_e;
+    unsigned char* ast = aout + r->bytes_o;
+    unsigned char* ws = ast + r->bytes_s;
+    const void* dk = r->k_dev ? r->k : ak;
+    const void* de = r->e_dev ? r->eps : ae;
+    void* dout = r->out_dev ? r->out : aout;
+    uint8_t* dst = r->st_dev ? r->status : reinterpret_cast<uint8_t*>(ast);
     const size_t elem = bgi::value_bytes(r->plan->field);
     const size_t nk = (size_t)r->E * r->plan->n * r->plan->d * bgi::momentum_bytes(r->plan->field);
     const size_t ne = (size_t)r->E * r->plan->n * r->plan->S * r->plan->Ds * elem;
     const size_t no = (size_t)r->E * r->plan->H * elem;
     bgi::Range nvtx("bg_serve_request");
     if (bgi::fault(BG_FAULT_COPY)) return BG_ERR_CUDA;
-    cudaError_t err = cudaMemcpyAsync(dk, r->k, nk, cudaMemcpyHostToDevice, st);
-    if (!err) err = cudaMemcpyAsync(de, r->eps, ne, cudaMemcpyHostToDevice, st);
+    cudaError_t err = cudaSuccess;
+    if (!r->k_dev) err = cudaMemcpyAsync(ak, r->k, nk, cudaMemcpyHostToDevice, st);
+    if (!err && !r->e_dev) err = cudaMemcpyAsync(ae, r->eps, ne, cudaMemcpyHostToDevice, st);
     if (err) { cudaGetLastError(); return BG_ERR_CUDA; }
     bg_status bs = bg_eval(r->plan, r->E, dk, de, dout, dst, r->bytes_ws ? ws : nullptr, r->bytes_ws, st);
     if (bs != BG_OK) return bs;
-    err = cudaMemcpyAsync(r->out, dout, no, cudaMemcpyDeviceToHost, st);
-    if (!err && r->status) err = cudaMemcpyAsync(r->status, dst, (size_t)r->E, cudaMemcpyDeviceToHost, st);
+    if (!r->out_dev) err = cudaMemcpyAsync(r->out, dout, no, cudaMemcpyDeviceToHost, st);
+    if (!err && r->status && !r->st_dev)
+        err = cudaMemcpyAsync(r->status, dst, (size_t)r->E, cudaMemcpyDeviceToHost, st);
     SlotDone* sd = new (std::nothrow) SlotDone{s, r->slot};
     if (!sd) return BG_ERR_NOMEM;
     if (!err) err = cudaLaunchHostFunc(st, slot_finished, sd);
@@ -273,9 +285,28 @@ bg_status bg_serve_create(size_t budget_bytes, int max_inflight, bg_server** out
 bg_status bg_serve_submit(bg_server* srv, const bg_plan* plan, int64_t E, const void* momenta,
                           const void* eps, void* out, uint8_t* status, uint64_t* ticket) {
     if (!srv || !plan || !ticket) return bgi::fail(BG_ERR_INVALID_ARG, "server, plan and ticket are required");
-    if (E < 1 || !momenta || !eps || !out) return bgi::fail(BG_ERR_INVALID_ARG, "E >= 1 and host buffers required");
+    if (E < 1 || !momenta || !eps || !out) return bgi::fail(BG_ERR_INVALID_ARG, "E >= 1 and buffers required");
     if (plan->d_assign && plan->device != srv->device)
         return bgi::fail(BG_ERR_INVALID_ARG, "plan and server are on different devices");
+    // each buffer is host memory (staged through the arena) or device memory
+    // of the server's device (used in place: resident inputs, outputs left on
+    // the device)
+    int where[4] = {0, 0, 0, 0};      // 0 host, 1 this device
+    const void* bufs[4] = {momenta, eps, out, status};
+    for (int b = 0; b < 4; ++b) {
+        if (!bufs[b]) continue;
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, bufs[b]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;                 // unregistered host memory
+        }
+        if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) {
+            if (attr.type == cudaMemoryTypeDevice && attr.device != srv->device)
+                return bgi::fail(BG_ERR_INVALID_ARG, "buffer %d is on device %d, the server's is %d", b,
+                                 attr.device, srv->device);
+            where[b] = 1;
+        }
+    }
     Request* r = new (std::nothrow) Request();
     if (!r) return bgi::fail(BG_ERR_NOMEM, "host allocation failed");
     const size_t elem = bgi::value_bytes(plan->field);
@@ -285,10 +316,14 @@ bg_status bg_serve_submit(bg_server* srv, const bg_plan* plan, int64_t E, const 
     r->eps = eps;
     r->out = out;
     r->status = status;
-    r->bytes_k = up_granule((size_t)E * plan->n * plan->d * bgi::momentum_bytes(plan->field));
-    r->bytes_e = up_granule((size_t)E * plan->n * plan->S * plan->Ds * elem);
-    r->bytes_o = up_granule((size_t)E * plan->H * elem);
-    r->bytes_s = up_granule((size_t)E);
+    r->k_dev = where[0] != 0;
+    r->e_dev = where[1] != 0;
+    r->out_dev = where[2] != 0;
+    r->st_dev = where[3] != 0;
+    r->bytes_k = r->k_dev ? 0 : up_granule((size_t)E * plan->n * plan->d * bgi::momentum_bytes(plan->field));
+    r->bytes_e = r->e_dev ? 0 : up_granule((size_t)E * plan->n * plan->S * plan->Ds * elem);
+    r->bytes_o = r->out_dev ? 0 : up_granule((size_t)E * plan->H * elem);
+    r->bytes_s = r->st_dev ? 0 : up_granule((size_t)E);
     size_t ws = 0;
     bg_workspace_size(plan, E, &ws);
     r->bytes_ws = up_granule(ws);

@@ -101,3 +101,46 @@ def test_budget_admission():
         assert torch.equal(o, _alone(p, k, e)[0])
     assert one <= srv.stats()["peak_bytes"] <= budget
     srv.close()
+
+
+def test_device_resident_inputs_and_outputs():
+    """Requests may reference a pool of momenta and states kept on the device
+    (and leave their outputs there): no copy and no arena bytes for those
+    buffers, same results as bg_eval, mixed with staged host requests."""
+    import torch
+    from paper_2502_07060_gb300 import bg
+    n, d, pool = 8, 6, 20000
+    k, e = G.fp_batch(77, pool, n, d, d, P, 0)
+    dk = torch.from_numpy(k.view(np.int32)).cuda()            # resident pool
+    de = torch.from_numpy(e.view(np.int32)).cuda()
+    plan = bg.Plan(n, d, d, bg.FIELD_FP, P)
+    ref, _ = plan.eval(dk, de)
+    torch.cuda.synchronize()
+    ref = ref.cpu()
+    srv = bg.Server(64 << 20, max_inflight=4)
+    jobs = []
+    rng = np.random.default_rng(4)
+    for i in range(24):
+        E = int(rng.integers(1, 3000))
+        off = int(rng.integers(0, pool - E))
+        if i % 3 == 0:                                       # staged host request
+            hk = torch.from_numpy(k[off:off + E].view(np.int32)).pin_memory()
+            he = torch.from_numpy(e[off:off + E].view(np.int32)).pin_memory()
+            out = torch.empty(E, dtype=torch.int32).pin_memory()
+            st = torch.empty(E, dtype=torch.uint8).pin_memory()
+            t = srv.submit(plan, hk, he, out, st)
+        else:                                                # resident inputs
+            out = torch.empty(E, dtype=torch.int32, device="cuda" if i % 3 == 1 else "cpu")
+            if out.device.type == "cpu":
+                out = out.pin_memory()
+            st = torch.empty(E, dtype=torch.uint8, device=out.device)
+            if out.device.type == "cpu":
+                st = st.pin_memory()
+            t = srv.submit(plan, dk[off:off + E], de[off:off + E], out, st)
+        jobs.append((t, off, E, out))
+    for t, off, E, out in jobs:
+        assert srv.wait(t, timeout_ms=60000)
+        assert torch.equal(out.cpu(), ref[off:off + E])
+    stats = srv.stats()
+    assert stats["completed"] == 24 and stats["bytes_in_use"] == 0
+    srv.close()
