@@ -574,7 +574,7 @@ def serve_workload(args, device):
 
     import torch
     from paper_2502_07060_gb300 import bg
-    rng = np.random.default_rng(2026)
+    rng = np.random.default_rng(args.serve_seed)
     configs = [(f, n, d) for f in ("fp", "c64") for n in range(4, 13) for d in (4, 6, 8)]
     pool_pts = 1 << 16
     pools, plans = {}, {}
@@ -693,7 +693,8 @@ def serve_workload(args, device):
     wt.join()
     plain = summarise([done_plain[i] - (t0 + arrivals[i]) for i in range(n_req)], t0, max(done_plain))
     return {"workload": f"Poisson arrivals at {args.serve_rate}/s for {args.serve_seconds} s, "
-                        f"{n_req} requests, sizes log-uniform 1..65536 (total {total_pts} points), "
+                        f"{n_req} requests (seed {args.serve_seed}), sizes log-uniform 1..65536 "
+                        f"(total {total_pts} points), "
                         "n uniform 4..12, d = D_s uniform {4, 6, 8}, F_p or C64",
             "server": served, "server_resident_inputs": served_resident, "plain_per_request": plain}
 
@@ -723,6 +724,8 @@ def main():
                     help="points per n of the helicity workload")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-seed", type=int, default=2026,
+                    help="seed of the arrival times, sizes, configurations and pool offsets")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -163,6 +163,21 @@ bg_status check_device_ptr(const void* ptr, const char* what, int device) {
     return BG_OK;
 }
 
+// Memory a kernel on `device` may read and write: device memory of that
+// device, or -- where the caller allows it -- page-locked host memory mapped
+// into the device's address space at the same address (unified addressing),
+// which kernels access over the host link without a copy.
+bg_status check_kernel_ptr(const void* ptr, const char* what, int device, bool mapped_host_ok) {
+    if (mapped_host_ok) {
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, ptr) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+            attr.devicePointer == ptr)
+            return BG_OK;
+        cudaGetLastError();
+    }
+    return check_device_ptr(ptr, what, device);
+}
+
 int round_dim(int x) { return x <= 4 ? 4 : (x <= 6 ? 6 : 8); }
 
 // The dynamic shared-memory limit is an attribute of the kernel function, not
@@ -553,9 +568,11 @@ bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
     return BG_OK;
 }
 
-bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
-                  uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream) {
-    bgi::Range nvtx("bg_eval");
+namespace {
+
+bg_status eval_impl(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
+                    uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream,
+                    bool mapped_host_ok) {
     g_last_error.clear();
     if (!plan) return fail(BG_ERR_INVALID_ARG, "plan is NULL");
     if (E < 0) return fail(BG_ERR_INVALID_ARG, "E = %lld < 0", (long long)E);
@@ -574,10 +591,10 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const voi
     if (plan->d_assign && dev != plan->device)
         return fail(BG_ERR_CUDA, "plan was created on device %d, current device is %d", plan->device, dev);
     bg_status st;
-    if ((st = check_device_ptr(momenta, "momenta", dev)) != BG_OK) return st;
-    if ((st = check_device_ptr(eps, "eps", dev)) != BG_OK) return st;
-    if ((st = check_device_ptr(out, "out", dev)) != BG_OK) return st;
-    if (status && (st = check_device_ptr(status, "status", dev)) != BG_OK) return st;
+    if ((st = bgi::check_kernel_ptr(momenta, "momenta", dev, mapped_host_ok)) != BG_OK) return st;
+    if ((st = bgi::check_kernel_ptr(eps, "eps", dev, mapped_host_ok)) != BG_OK) return st;
+    if ((st = bgi::check_kernel_ptr(out, "out", dev, mapped_host_ok)) != BG_OK) return st;
+    if (status && (st = bgi::check_kernel_ptr(status, "status", dev, mapped_host_ok)) != BG_OK) return st;
 
     const bgk::KernelEntry* e = plan->entry;
     size_t need = 0;
@@ -639,4 +656,22 @@ bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const voi
     return BG_OK;
 }
 
+}  // namespace
+
+bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
+                  uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+    bgi::Range nvtx("bg_eval");
+    return eval_impl(plan, E, momenta, eps, out, status, workspace, workspace_bytes, stream, false);
+}
+
 }  // extern "C"
+
+namespace bgi {
+
+bg_status eval_mapped(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
+                      uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+    Range nvtx("bg_eval_mapped");
+    return eval_impl(plan, E, momenta, eps, out, status, workspace, workspace_bytes, stream, true);
+}
+
+}  // namespace bgi

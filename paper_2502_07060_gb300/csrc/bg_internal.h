@@ -60,6 +60,12 @@ const std::vector<bgk::KernelEntry>& registry();
 const std::vector<bgk::StatesEntry>& states_registry();
 bg_status fail(bg_status s, const char* fmt, ...);
 bg_status check_device_ptr(const void* ptr, const char* what, int device);
+bg_status check_kernel_ptr(const void* ptr, const char* what, int device, bool mapped_host_ok);
+// bg_eval that also takes page-locked host buffers mapped at the same address
+// (momenta, eps, out, status; the workspace stays device memory): the kernel
+// reads and writes them over the host link.
+bg_status eval_mapped(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
+                      uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream);
 int round_dim(int x);
 bg_status ensure_smem_limit(const void* func, int device, size_t bytes);
 

@@ -18,7 +18,12 @@
 //     the CUDA driver, no CUDA calls in it) that marks the slot finished;
 //     buffers already in device memory (a resident pool of momenta and
 //     states, outputs kept on the device) are used in place, with no copy and
-//     no arena bytes;
+//     no arena bytes, and so are the page-locked host buffers of a request
+//     of at most kZeroCopyBytes of host data (the kernel reads and writes
+//     them over the host link), which keeps small requests off the copy
+//     engines, where they would queue behind large transfers;
+//   * the dispatcher enqueues copies and kernels with the server mutex
+//     released, so the completion host functions never wait on it;
 //   * bg_serve_wait blocks on a condition variable with a deadline and
 //     returns BG_ERR_TIMEOUT when the request is not done by then.
 #include <cuda_runtime.h>
@@ -39,6 +44,12 @@ namespace {
 
 constexpr size_t kGranule = 256;
 constexpr double kStarveMs = 50.0;
+// Requests whose host buffers are page-locked, mapped and at most this many
+// bytes in all are served without copies: the kernel reads its inputs and
+// writes its results over the host link.  A copy-engine transfer costs tens
+// of microseconds before the first byte moves and small copies queue behind
+// large ones; the mapped path takes small requests off the copy engines.
+constexpr size_t kZeroCopyBytes = size_t(1) << 20;
 
 using Clock = std::chrono::steady_clock;
 
@@ -94,7 +105,10 @@ struct Request {
     const void* eps;
     void* out;
     uint8_t* status;
-    bool k_dev = false, e_dev = false, out_dev = false, st_dev = false;   // resident on the device
+    // buffers used in place (device memory, or mapped host memory of a small
+    // request) rather than staged through the arena
+    bool k_dev = false, e_dev = false, out_dev = false, st_dev = false;
+    bool mapped = false;                     // some buffer in place is mapped host memory
     size_t bytes_k, bytes_e, bytes_o, bytes_s, bytes_ws, total;
     Clock::time_point submitted;
     State state = State::Pending;
@@ -168,7 +182,9 @@ bg_status launch_request(bg_server* s, Request* r) {
     if (!r->k_dev) err = cudaMemcpyAsync(ak, r->k, nk, cudaMemcpyHostToDevice, st);
     if (!err && !r->e_dev) err = cudaMemcpyAsync(ae, r->eps, ne, cudaMemcpyHostToDevice, st);
     if (err) { cudaGetLastError(); return BG_ERR_CUDA; }
-    bg_status bs = bg_eval(r->plan, r->E, dk, de, dout, dst, r->bytes_ws ? ws : nullptr, r->bytes_ws, st);
+    bg_status bs = r->mapped
+        ? bgi::eval_mapped(r->plan, r->E, dk, de, dout, dst, r->bytes_ws ? ws : nullptr, r->bytes_ws, st)
+        : bg_eval(r->plan, r->E, dk, de, dout, dst, r->bytes_ws ? ws : nullptr, r->bytes_ws, st);
     if (bs != BG_OK) return bs;
     if (!r->out_dev) err = cudaMemcpyAsync(r->out, dout, no, cudaMemcpyDeviceToHost, st);
     if (!err && r->status && !r->st_dev)
@@ -180,8 +196,14 @@ bg_status launch_request(bg_server* s, Request* r) {
     return BG_OK;
 }
 
+// The dispatcher decides admissions under the server mutex but enqueues the
+// copies, kernels and host functions with the mutex released: the host
+// function of a finishing request takes the mutex on the driver's callback
+// thread, and a dispatcher holding it across CUDA calls would hold up every
+// stream's completion behind those calls.
 void dispatcher(bg_server* s) {
     cudaSetDevice(s->device);
+    std::vector<Request*> admitted;
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
         // collect finished slots
@@ -198,9 +220,10 @@ void dispatcher(bg_server* s) {
             }
         }
         if (progressed) s->cv_done.notify_all();
-        // admit
+        // admit: reserve a slot and arena bytes for each request that fits
         const auto now = Clock::now();
         bool blocked_head = false;
+        admitted.clear();
         for (auto it = s->pending.begin(); it != s->pending.end();) {
             int slot = -1;
             for (size_t i = 0; i < s->slot_req.size(); ++i)
@@ -216,21 +239,36 @@ void dispatcher(bg_server* s) {
                 s->slot_done[slot] = 0;
                 if (s->arena->used() > s->peak_used) s->peak_used = s->arena->used();
                 it = s->pending.erase(it);
-                bg_status st = launch_request(s, r);
-                if (st != BG_OK) {              // nothing of r was enqueued after the failure point
-                    cudaStreamSynchronize(s->streams[slot]);
-                    s->arena->release(r->off, r->total);
-                    s->slot_req[slot] = nullptr;
-                    r->state = State::Failed;
-                    r->result = st;
-                    s->cv_done.notify_all();
-                }
+                admitted.push_back(r);
                 continue;
             }
             // does not fit: later requests may overtake unless this one starves
             const double waited = std::chrono::duration<double, std::milli>(now - r->submitted).count();
             if (waited > kStarveMs) blocked_head = true;
             ++it;
+        }
+        if (!admitted.empty()) {
+            // enqueue outside the mutex; a running request is neither freed
+            // by bg_serve_wait nor touched by submit, and its slot stays
+            // reserved until the dispatcher itself releases it
+            lk.unlock();
+            for (Request* r : admitted) {
+                r->result = launch_request(s, r);
+                if (r->result != BG_OK)         // nothing of r was enqueued after the failure point
+                    cudaStreamSynchronize(s->streams[r->slot]);
+            }
+            lk.lock();
+            bool failed = false;
+            for (Request* r : admitted) {
+                if (r->result == BG_OK) continue;
+                s->arena->release(r->off, r->total);
+                s->slot_req[r->slot] = nullptr;
+                s->slot_done[r->slot] = 0;
+                r->state = State::Failed;
+                failed = true;
+            }
+            if (failed) s->cv_done.notify_all();
+            continue;                           // completions may have arrived meanwhile
         }
         if (s->stop && s->pending.empty()) {
             bool busy = false;
@@ -291,7 +329,7 @@ bg_status bg_serve_submit(bg_server* srv, const bg_plan* plan, int64_t E, const 
     // each buffer is host memory (staged through the arena) or device memory
     // of the server's device (used in place: resident inputs, outputs left on
     // the device)
-    int where[4] = {0, 0, 0, 0};      // 0 host, 1 this device
+    int where[4] = {0, 0, 0, 0};      // 0 host, 1 this device, 2 mapped page-locked host memory
     const void* bufs[4] = {momenta, eps, out, status};
     for (int b = 0; b < 4; ++b) {
         if (!bufs[b]) continue;
@@ -305,6 +343,8 @@ bg_status bg_serve_submit(bg_server* srv, const bg_plan* plan, int64_t E, const 
                 return bgi::fail(BG_ERR_INVALID_ARG, "buffer %d is on device %d, the server's is %d", b,
                                  attr.device, srv->device);
             where[b] = 1;
+        } else if (attr.type == cudaMemoryTypeHost && attr.devicePointer == bufs[b]) {
+            where[b] = 2;
         }
     }
     Request* r = new (std::nothrow) Request();
@@ -316,10 +356,27 @@ bg_status bg_serve_submit(bg_server* srv, const bg_plan* plan, int64_t E, const 
     r->eps = eps;
     r->out = out;
     r->status = status;
-    r->k_dev = where[0] != 0;
-    r->e_dev = where[1] != 0;
-    r->out_dev = where[2] != 0;
-    r->st_dev = where[3] != 0;
+    // host buffers of a small request that are all mapped are used in place
+    const size_t sizes[4] = {(size_t)E * plan->n * plan->d * bgi::momentum_bytes(plan->field),
+                             (size_t)E * plan->n * plan->S * plan->Ds * elem, (size_t)E * plan->H * elem,
+                             (size_t)E};
+    size_t host_bytes = 0;
+    bool all_mapped = true;
+    for (int b = 0; b < 4; ++b) {
+        if (!bufs[b] || where[b] == 1) continue;
+        host_bytes += sizes[b];
+        all_mapped &= where[b] == 2;
+    }
+    const bool zero_copy = all_mapped && host_bytes <= kZeroCopyBytes;
+    bool in_place[4];
+    for (int b = 0; b < 4; ++b) {
+        in_place[b] = where[b] == 1 || (zero_copy && where[b] == 2);
+        r->mapped |= zero_copy && where[b] == 2;
+    }
+    r->k_dev = in_place[0];
+    r->e_dev = in_place[1];
+    r->out_dev = in_place[2];
+    r->st_dev = in_place[3];
     r->bytes_k = r->k_dev ? 0 : up_granule((size_t)E * plan->n * plan->d * bgi::momentum_bytes(plan->field));
     r->bytes_e = r->e_dev ? 0 : up_granule((size_t)E * plan->n * plan->S * plan->Ds * elem);
     r->bytes_o = r->out_dev ? 0 : up_granule((size_t)E * plan->H * elem);

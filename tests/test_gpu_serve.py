@@ -144,3 +144,34 @@ def test_device_resident_inputs_and_outputs():
     stats = srv.stats()
     assert stats["completed"] == 24 and stats["bytes_in_use"] == 0
     srv.close()
+
+
+def test_small_pinned_requests_are_served_in_place():
+    """The page-locked host buffers of a small request are used in place: the
+    kernel reads the inputs and writes the results over the host link, so no
+    arena bytes beyond the kernel workspace are taken.  The same request from
+    pageable host memory is staged through the arena.  Both give bg_eval's
+    results."""
+    import torch
+    from paper_2502_07060_gb300 import bg
+
+    def up(x):
+        return (x + 255) // 256 * 256
+    for field, n, d, E in (("fp", 8, 6, 1000), ("c64", 6, 4, 300), ("c64r", 5, 8, 257), ("fp", 12, 8, 1)):
+        plan, hk, he, out, st = _request(bg, field, n, d, E, 1200 + n)
+        ro, rs = _alone(plan, hk, he)
+        ws = up(plan.workspace_size(E))
+        srv = bg.Server(64 << 20, max_inflight=2)
+        assert srv.wait(srv.submit(plan, hk, he, out, st), timeout_ms=60000)
+        assert torch.equal(out, ro) and torch.equal(st, rs), plan.describe()
+        assert srv.stats()["peak_bytes"] == ws
+        srv.close()
+        pk = torch.from_numpy(hk.numpy().copy())
+        pe = torch.from_numpy(he.numpy().copy())
+        po, ps = torch.empty(out.shape, dtype=out.dtype), torch.empty(E, dtype=torch.uint8)
+        assert not (pk.is_pinned() or pe.is_pinned() or po.is_pinned() or ps.is_pinned())
+        srv = bg.Server(64 << 20, max_inflight=2)
+        assert srv.wait(srv.submit(plan, pk, pe, po, ps), timeout_ms=60000)
+        assert torch.equal(po, ro) and torch.equal(ps, rs), plan.describe()
+        assert srv.stats()["peak_bytes"] > ws
+        srv.close()
