@@ -316,12 +316,17 @@ bg_status bg_batch_autotune(const bg_group* groups, int n_groups, void* workspac
  * requests overlap on the device.  Admission is first-come-first-served, but
  * a request that does not fit may be overtaken by later ones until it has
  * waited 50 ms.  Each buffer (momenta, eps, out, status, layouts as for
- * bg_eval) is either host memory, staged through the arena (page-locked
- * memory lets the copies overlap), or device memory of the server's device,
- * used in place with no copy and no arena bytes: momenta and states kept
- * resident on the device across requests, outputs left on the device.  All
- * buffers must stay valid until bg_serve_wait returns.  Every result equals
- * what bg_eval gives for the request alone.
+ * bg_eval) is one of:
+ *   - device memory of the server's device, used in place with no copy and
+ *     no arena bytes (momenta and states kept resident on the device across
+ *     requests, outputs left on the device);
+ *   - page-locked host memory mapped into the device's address space (as
+ *     cudaHostAlloc / cudaMallocHost give under unified addressing), also
+ *     used in place: the kernel reads the inputs and writes the results over
+ *     the host link, without copy-engine transfers;
+ *   - pageable host memory, staged through the arena by copies.
+ * All buffers must stay valid, and inputs unchanged, until bg_serve_wait
+ * returns.  Every result equals what bg_eval gives for the request alone.
  */
 typedef struct bg_server bg_server;
 

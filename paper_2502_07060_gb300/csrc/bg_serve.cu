@@ -18,10 +18,13 @@
 //     the CUDA driver, no CUDA calls in it) that marks the slot finished;
 //     buffers already in device memory (a resident pool of momenta and
 //     states, outputs kept on the device) are used in place, with no copy and
-//     no arena bytes, and so are the page-locked host buffers of a request
-//     of at most kZeroCopyBytes of host data (the kernel reads and writes
-//     them over the host link), which keeps small requests off the copy
-//     engines, where they would queue behind large transfers;
+//     no arena bytes, and so are page-locked host buffers mapped into the
+//     device's address space: the kernel reads its inputs and writes its
+//     results over the host link.  The kernels read each input once and are
+//     compute-bound, so this costs them little, while a copy-engine transfer
+//     costs tens of microseconds before its first byte moves, small copies
+//     queue behind large ones and a staged request holds its slot through its
+//     copy.  Only pageable host buffers are staged through the arena;
 //   * the dispatcher enqueues copies and kernels with the server mutex
 //     released, so the completion host functions never wait on it;
 //   * bg_serve_wait blocks on a condition variable with a deadline and
@@ -44,12 +47,6 @@ namespace {
 
 constexpr size_t kGranule = 256;
 constexpr double kStarveMs = 50.0;
-// Requests whose host buffers are page-locked, mapped and at most this many
-// bytes in all are served without copies: the kernel reads its inputs and
-// writes its results over the host link.  A copy-engine transfer costs tens
-// of microseconds before the first byte moves and small copies queue behind
-// large ones; the mapped path takes small requests off the copy engines.
-constexpr size_t kZeroCopyBytes = size_t(1) << 20;
 
 using Clock = std::chrono::steady_clock;
 
@@ -105,8 +102,8 @@ struct Request {
     const void* eps;
     void* out;
     uint8_t* status;
-    // buffers used in place (device memory, or mapped host memory of a small
-    // request) rather than staged through the arena
+    // buffers used in place (device memory, or mapped page-locked host
+    // memory) rather than staged through the arena
     bool k_dev = false, e_dev = false, out_dev = false, st_dev = false;
     bool mapped = false;                     // some buffer in place is mapped host memory
     size_t bytes_k, bytes_e, bytes_o, bytes_s, bytes_ws, total;
@@ -356,22 +353,11 @@ bg_status bg_serve_submit(bg_server* srv, const bg_plan* plan, int64_t E, const 
     r->eps = eps;
     r->out = out;
     r->status = status;
-    // host buffers of a small request that are all mapped are used in place
-    const size_t sizes[4] = {(size_t)E * plan->n * plan->d * bgi::momentum_bytes(plan->field),
-                             (size_t)E * plan->n * plan->S * plan->Ds * elem, (size_t)E * plan->H * elem,
-                             (size_t)E};
-    size_t host_bytes = 0;
-    bool all_mapped = true;
-    for (int b = 0; b < 4; ++b) {
-        if (!bufs[b] || where[b] == 1) continue;
-        host_bytes += sizes[b];
-        all_mapped &= where[b] == 2;
-    }
-    const bool zero_copy = all_mapped && host_bytes <= kZeroCopyBytes;
+    // device memory and mapped page-locked host memory are used in place
     bool in_place[4];
     for (int b = 0; b < 4; ++b) {
-        in_place[b] = where[b] == 1 || (zero_copy && where[b] == 2);
-        r->mapped |= zero_copy && where[b] == 2;
+        in_place[b] = where[b] != 0;
+        r->mapped |= where[b] == 2;
     }
     r->k_dev = in_place[0];
     r->e_dev = in_place[1];

@@ -33,6 +33,14 @@ def _request(bg, field, n, d, E, seed):
     return plan, hk, he, out, st
 
 
+def _pageable(req):
+    """The same request with pageable host buffers (staged through the arena)."""
+    import torch
+    plan, hk, he, out, st = req
+    return (plan, torch.from_numpy(hk.numpy().copy()), torch.from_numpy(he.numpy().copy()),
+            torch.empty(out.shape, dtype=out.dtype), torch.empty(st.shape, dtype=st.dtype))
+
+
 def _alone(plan, hk, he):
     import torch
     o, s = plan.eval(hk.cuda(), he.cuda())
@@ -84,7 +92,7 @@ def test_wait_times_out_then_completes():
 def test_budget_admission():
     import torch
     from paper_2502_07060_gb300 import bg
-    reqs = [_request(bg, "fp", 8, 6, 20000, 700 + i) for i in range(5)]
+    reqs = [_pageable(_request(bg, "fp", 8, 6, 20000, 700 + i)) for i in range(5)]
 
     def up(x):
         return (x + 255) // 256 * 256
@@ -93,7 +101,7 @@ def test_budget_admission():
     budget = int(one * 1.5)
     srv = bg.Server(budget, max_inflight=4)                       # room for one request at a time
     with pytest.raises(bg.BGError) as ei:                              # can never fit
-        srv.submit(*_request(bg, "fp", 8, 6, 200000, 1))
+        srv.submit(*_pageable(_request(bg, "fp", 8, 6, 200000, 1)))
     assert ei.value.status == bg.BG_ERR_INVALID_ARG
     ts = [srv.submit(*r) for r in reqs]
     assert all(srv.wait(t, timeout_ms=60000) for t in ts)
@@ -146,31 +154,29 @@ def test_device_resident_inputs_and_outputs():
     srv.close()
 
 
-def test_small_pinned_requests_are_served_in_place():
-    """The page-locked host buffers of a small request are used in place: the
-    kernel reads the inputs and writes the results over the host link, so no
-    arena bytes beyond the kernel workspace are taken.  The same request from
-    pageable host memory is staged through the arena.  Both give bg_eval's
-    results."""
+def test_page_locked_requests_are_served_in_place():
+    """Page-locked host buffers are used in place: the kernel reads the inputs
+    and writes the results over the host link, so no arena bytes beyond the
+    kernel workspace are taken.  The same request from pageable host memory is
+    staged through the arena.  Both give bg_eval's results."""
     import torch
     from paper_2502_07060_gb300 import bg
 
     def up(x):
         return (x + 255) // 256 * 256
-    for field, n, d, E in (("fp", 8, 6, 1000), ("c64", 6, 4, 300), ("c64r", 5, 8, 257), ("fp", 12, 8, 1)):
+    for field, n, d, E in (("fp", 8, 6, 1000), ("c64", 6, 4, 300), ("c64r", 5, 8, 257), ("fp", 12, 8, 1),
+                           ("c64", 12, 8, 40000)):
         plan, hk, he, out, st = _request(bg, field, n, d, E, 1200 + n)
         ro, rs = _alone(plan, hk, he)
         ws = up(plan.workspace_size(E))
-        srv = bg.Server(64 << 20, max_inflight=2)
+        srv = bg.Server(2 << 30, max_inflight=2)
         assert srv.wait(srv.submit(plan, hk, he, out, st), timeout_ms=60000)
         assert torch.equal(out, ro) and torch.equal(st, rs), plan.describe()
         assert srv.stats()["peak_bytes"] == ws
         srv.close()
-        pk = torch.from_numpy(hk.numpy().copy())
-        pe = torch.from_numpy(he.numpy().copy())
-        po, ps = torch.empty(out.shape, dtype=out.dtype), torch.empty(E, dtype=torch.uint8)
+        _, pk, pe, po, ps = _pageable((plan, hk, he, out, st))
         assert not (pk.is_pinned() or pe.is_pinned() or po.is_pinned() or ps.is_pinned())
-        srv = bg.Server(64 << 20, max_inflight=2)
+        srv = bg.Server(2 << 30, max_inflight=2)
         assert srv.wait(srv.submit(plan, pk, pe, po, ps), timeout_ms=60000)
         assert torch.equal(po, ro) and torch.equal(ps, rs), plan.describe()
         assert srv.stats()["peak_bytes"] > ws
