@@ -178,6 +178,41 @@ bg_status check_kernel_ptr(const void* ptr, const char* what, int device, bool m
     return check_device_ptr(ptr, what, device);
 }
 
+bool mapped_host(const void* p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeHost && attr.devicePointer == p;
+}
+
+namespace {
+
+// Field operations per amplitude of the recursion counted literally (the
+// three- and four-gluon splits of every range, the propagators and the final
+// contraction; momenta d-, currents D-dimensional): a cost estimate only.
+double ops_per_amplitude(int n, int d, int D) {
+    const double N = n - 1, R = N * (N + 1) / 2;
+    const double s3 = n * (n - 1.0) * (n - 2) / 6, s4 = s3 * (n - 3) / 4;
+    return s3 * (3.0 * D + 3.0 * d) + s4 * 6.0 * D + (R - N) * (d + D) + 3 * (R - N - 1) + D;
+}
+
+}  // namespace
+
+// The kernels sustain about 4.3e12 (F_p), 2.5e11 (complex, real momenta) and
+// 1.9e11 (complex momenta) of these operations per second (n = 8, d = 6 on a
+// GB300), and their per-thread loads of mapped host memory reach about
+// 100 GB/s over the host link: in place pays while the batch needs at most
+// 80 GB/s of it.  At n = 8, d = 6 that keeps F_p batches (about 350 GB/s)
+// on copies and takes complex ones (about 60 GB/s) in place.
+bool in_place_pays(const bg_plan* plan, int64_t E, size_t host_bytes) {
+    if (host_bytes <= kInPlaceBytes) return true;
+    const double rate = plan->field == BG_FIELD_FP ? 4.3e12 : plan->field == BG_FIELD_C64_REAL ? 2.5e11 : 1.9e11;
+    const double seconds = (double)E * plan->H * ops_per_amplitude(plan->n, plan->d, plan->Ds) / rate;
+    return (double)host_bytes <= 80e9 * seconds;
+}
+
 int round_dim(int x) { return x <= 4 ? 4 : (x <= 6 ? 6 : 8); }
 
 // The dynamic shared-memory limit is an attribute of the kernel function, not

@@ -15,6 +15,12 @@
 // stream-ordered semantics).  On a failure part-way, the call returns after
 // the copies it had enqueued have finished.  Host memory should be page-locked for the copies
 // to overlap; pageable memory works but serialises.
+//
+// When all four buffers are page-locked host memory mapped into the device's
+// address space and the batch's arithmetic hides the host-link traffic
+// (bgi::in_place_pays: small batches, or large ones heavy enough per point,
+// such as complex FP64 at n = 8), one kernel reads the inputs and writes the
+// results in place instead: no copies, no chunk boundaries.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -118,6 +124,19 @@ extern "C" bg_status bg_eval_host(const bg_plan* plan, int64_t E, const void* mo
     const size_t k_pt = (size_t)plan->n * plan->d * bgi::momentum_bytes(plan->field);
     const size_t e_pt = (size_t)plan->n * plan->S * plan->Ds * elem;
     const size_t o_pt = (size_t)plan->H * elem;
+
+    // Page-locked host buffers mapped into the device's address space are
+    // read and written in place by one launch when the recursion's arithmetic
+    // hides the host-link traffic (the workspace then sits at the start of
+    // the staging buffer); otherwise the chunked copy pipeline below runs.
+    if (bgi::mapped_host(momenta) && bgi::mapped_host(eps) && bgi::mapped_host(out) && bgi::mapped_host(status) &&
+        bgi::in_place_pays(plan, E, (size_t)E * (k_pt + e_pt + o_pt + 1))) {
+        size_t ws_need = 0;
+        if ((st = bg_workspace_size(plan, E, &ws_need)) != BG_OK) return st;
+        if (ws_need <= staging_bytes)
+            return bgi::eval_mapped(plan, E, momenta, eps, out, status, ws_need ? staging : nullptr, ws_need,
+                                    stream);
+    }
 
     std::lock_guard<std::mutex> lock(g_pipe_mutex);
     HostPipe* hp = nullptr;

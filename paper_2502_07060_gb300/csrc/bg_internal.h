@@ -66,6 +66,15 @@ bg_status check_kernel_ptr(const void* ptr, const char* what, int device, bool m
 // reads and writes them over the host link.
 bg_status eval_mapped(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
                       uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream);
+// True when `p` is page-locked host memory mapped into the device's address
+// space at the same address (the kernels can read and write it directly).
+bool mapped_host(const void* p);
+// Whether kernels should read a batch of E points from mapped host memory in
+// place rather than have it copied in first: always for batches of at most
+// kInPlaceBytes of host data (latency dominates), and otherwise when the
+// recursion's arithmetic per point hides the traffic over the host link.
+constexpr size_t kInPlaceBytes = size_t(64) << 20;
+bool in_place_pays(const bg_plan* plan, int64_t E, size_t host_bytes);
 int round_dim(int x);
 bg_status ensure_smem_limit(const void* func, int device, size_t bytes);
 

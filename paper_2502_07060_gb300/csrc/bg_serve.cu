@@ -20,11 +20,12 @@
 //     states, outputs kept on the device) are used in place, with no copy and
 //     no arena bytes, and so are page-locked host buffers mapped into the
 //     device's address space: the kernel reads its inputs and writes its
-//     results over the host link.  The kernels read each input once and are
-//     compute-bound, so this costs them little, while a copy-engine transfer
-//     costs tens of microseconds before its first byte moves, small copies
-//     queue behind large ones and a staged request holds its slot through its
-//     copy.  Only pageable host buffers are staged through the arena;
+//     results over the host link.  A copy-engine transfer costs tens of
+//     microseconds before its first byte moves, small copies queue behind
+//     large ones and a staged request holds its slot through its copy, while
+//     the kernels read each input once.  Pageable host buffers, and mapped
+//     ones of large requests whose kernels the link would bound
+//     (bgi::in_place_pays), are staged through the arena by copies;
 //   * the dispatcher enqueues copies and kernels with the server mutex
 //     released, so the completion host functions never wait on it;
 //   * bg_serve_wait blocks on a condition variable with a deadline and
@@ -353,11 +354,21 @@ bg_status bg_serve_submit(bg_server* srv, const bg_plan* plan, int64_t E, const 
     r->eps = eps;
     r->out = out;
     r->status = status;
-    // device memory and mapped page-locked host memory are used in place
+    // device memory is used in place, and so is mapped page-locked host
+    // memory unless the request is large and light enough per point for the
+    // host link to bound its kernel (then copies, overlapping other requests'
+    // kernels, serve it better)
+    const size_t sizes[4] = {(size_t)E * plan->n * plan->d * bgi::momentum_bytes(plan->field),
+                             (size_t)E * plan->n * plan->S * plan->Ds * elem, (size_t)E * plan->H * elem,
+                             (size_t)E};
+    size_t mapped_bytes = 0;
+    for (int b = 0; b < 4; ++b)
+        if (where[b] == 2) mapped_bytes += sizes[b];
+    const bool use_mapped = mapped_bytes > 0 && bgi::in_place_pays(plan, E, mapped_bytes);
     bool in_place[4];
     for (int b = 0; b < 4; ++b) {
-        in_place[b] = where[b] != 0;
-        r->mapped |= where[b] == 2;
+        in_place[b] = where[b] == 1 || (where[b] == 2 && use_mapped);
+        r->mapped |= where[b] == 2 && use_mapped;
     }
     r->k_dev = in_place[0];
     r->e_dev = in_place[1];

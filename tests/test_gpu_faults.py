@@ -68,16 +68,17 @@ def test_launch_failure_leaves_outputs_untouched():
 def test_host_pipeline_copy_failure_then_recovery(skip):
     """A copy that cannot be enqueued at chunk `skip` ends the call with
     BG_ERR_CUDA after the chunks already in flight have drained; the same
-    staging buffer then serves a complete evaluation."""
+    staging buffer then serves a complete evaluation.  (Pageable buffers: a
+    batch this small from page-locked ones is read in place, without copies.)"""
     import torch
     from paper_2502_07060_gb300 import bg
     k, eps, ref, _, _ = _inputs()
     E = len(k)
     plan = bg.Plan(7, 6, 6, bg.FIELD_FP, P, bg.MOSTLY_MINUS)
-    hk = torch.from_numpy(k.view(np.int32)).pin_memory()
-    he = torch.from_numpy(eps.view(np.int32)).pin_memory()
-    hout = torch.empty(E, dtype=torch.int32).pin_memory()
-    hst = torch.empty(E, dtype=torch.uint8).pin_memory()
+    hk = torch.from_numpy(k.view(np.int32).copy())
+    he = torch.from_numpy(eps.view(np.int32).copy())
+    hout = torch.empty(E, dtype=torch.int32)
+    hst = torch.empty(E, dtype=torch.uint8)
     bg.inject_fault(bg.FAULT_COPY, skip, 1)
     with pytest.raises(bg.BGError) as e:
         plan.eval_host(hk, he, out=hout, status=hst, chunk=500)
