@@ -324,8 +324,10 @@ def run_field(field, E, steps, warmup, rank, dist, device, seed, e2e=True):
     if not e2e:
         return res
     # end to end through the public C-ABI call with HOST buffers
-    # (bg_eval_host): pinned inputs -> device -> kernel -> pinned results, in
-    # chunks whose copies overlap the kernels
+    # (bg_eval_host), pinned inputs and results: every byte crosses the host
+    # link each step, either by chunked copies overlapping the kernels (F_p)
+    # or read and written in place by the kernel (complex FP64, whose
+    # arithmetic per point hides the link traffic)
     pk = hk.pin_memory()
     pe = he.pin_memory()
     hout = torch.empty(E, dtype=de.dtype).pin_memory()
