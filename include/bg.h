@@ -203,9 +203,17 @@ bg_status bg_host_staging_size(const bg_plan* plan, int64_t chunk, size_t* bytes
  * two staging slots in the caller's device buffer `staging` (>=
  * bg_host_staging_size bytes, 256-byte aligned): the copy of chunk c+1 to the
  * device, the kernel on chunk c and the copy of chunk c-1 back to the host
- * overlap on separate streams.  Asynchronous: the host buffers hold the
- * results once `stream` reaches the call.  Host buffers should be page-locked
- * (pageable memory works but the copies serialise).
+ * overlap on separate streams.  When all four host buffers are page-locked
+ * and mapped into the device's address space (cudaHostAlloc/cudaMallocHost
+ * under unified addressing) and the batch's arithmetic per point hides the
+ * host-link traffic -- batches of at most 64 MiB of host data, or heavier
+ * ones such as complex FP64 at n = 8 -- one kernel instead reads the inputs
+ * and writes the results in place, with no copies and the workspace at the
+ * start of `staging`; light, large batches (F_p) keep the copies, which move
+ * data faster than the kernels' scattered loads.  Results are identical on
+ * both paths.  Asynchronous: the host buffers hold the results once `stream`
+ * reaches the call.  Host buffers should be page-locked (pageable memory
+ * works but the copies serialise).
  *
  *   momenta, eps  host arrays with the layouts of bg_eval
  *   out, status   host arrays [E][H] and [E] (status is required here)
