@@ -421,6 +421,21 @@ int bg_version(void);
  */
 bg_status bg_debug_bounds_report(int* checked, uint64_t* first_violation);
 
+/*
+ * bg_debug_in_place_pays -- testing aid (no counterpart in the paper): the
+ * decision bg_eval_host and the server take for a batch of E points of a plan
+ * with (field, n, d, D_s) and H amplitudes per point whose host buffers,
+ * host_bytes in all, are page-locked and mapped.  *in_place = 1 when one
+ * kernel should read and write them over the host link (batches of at most
+ * 64 MiB, or batches whose arithmetic per point hides the link traffic), 0
+ * when copies should move them; *ops = the field multiplications per
+ * amplitude of the literal recursion that the estimate uses.  Pure host
+ * arithmetic: needs no device.  BG_ERR_INVALID_ARG for arguments out of the
+ * ranges of bg_plan_create, H < 1, E < 0 or NULL outputs.
+ */
+bg_status bg_debug_in_place_pays(bg_field field, int n, int d, int D_s, int H, int64_t E,
+                                 size_t host_bytes, int* in_place, double* ops);
+
 typedef enum {
     BG_FAULT_DEVICE_ALLOC = 1,
     BG_FAULT_LAUNCH = 2,

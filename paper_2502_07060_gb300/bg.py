@@ -36,7 +36,7 @@ EXPORTED = ("bg_plan_create", "bg_plan_create_product", "bg_plan_create_mixed", 
             "bg_batch_create", "bg_batch_launch", "bg_batch_describe", "bg_batch_destroy",
             "bg_batch_autotune", "bg_serve_create", "bg_serve_submit", "bg_serve_wait",
             "bg_serve_stats", "bg_serve_destroy", "bg_plan_describe", "bg_strerror", "bg_last_error",
-            "bg_version", "bg_debug_inject_fault", "bg_debug_bounds_report")
+            "bg_version", "bg_debug_inject_fault", "bg_debug_bounds_report", "bg_debug_in_place_pays")
 
 # BG_LIBRARY selects another build of the same library (the bounds-checked
 # one, _build.build(checked=True)); default: the ordinary in-tree build
@@ -124,6 +124,10 @@ def load_library(path=None):
     lib.bg_last_error.restype = ctypes.c_char_p
     lib.bg_debug_bounds_report.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64)]
     lib.bg_debug_bounds_report.restype = ctypes.c_int
+    lib.bg_debug_in_place_pays.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int64, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_double)]
+    lib.bg_debug_in_place_pays.restype = ctypes.c_int
     lib.bg_debug_inject_fault.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.bg_debug_inject_fault.restype = ctypes.c_int
     lib.bg_version.argtypes = []
@@ -476,6 +480,14 @@ def inject_fault(site, skip=0, count=1):
     """bg_debug_inject_fault: operations skip .. skip+count-1 at `site` fail
     as if the CUDA runtime had refused them (count = 0 disarms)."""
     _check(_lib.bg_debug_inject_fault(site, skip, count))
+
+
+def in_place_pays(field, n, d, Ds, H, E, host_bytes):
+    """bg_debug_in_place_pays: (read page-locked buffers in place?, literal
+    multiplications per amplitude of the estimate)."""
+    flag, ops = ctypes.c_int(), ctypes.c_double()
+    _check(_lib.bg_debug_in_place_pays(field, n, d, Ds, H, E, host_bytes, ctypes.byref(flag), ctypes.byref(ops)))
+    return bool(flag.value), ops.value
 
 
 def bounds_report():

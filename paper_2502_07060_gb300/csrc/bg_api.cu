@@ -187,30 +187,29 @@ bool mapped_host(const void* p) {
     return attr.type == cudaMemoryTypeHost && attr.devicePointer == p;
 }
 
-namespace {
-
-// Field operations per amplitude of the recursion counted literally (the
-// three- and four-gluon splits of every range, the propagators and the final
-// contraction; momenta d-, currents D-dimensional): a cost estimate only.
+// Field multiplications per amplitude of the literal recursion (three- and
+// four-gluon splits of every range, propagators, final contraction; momenta
+// d-, currents D-dimensional): C(n,3)(3D+3d) + C(n,4) 6D + (C(n,2)-n)(d+D) + D.
 double ops_per_amplitude(int n, int d, int D) {
-    const double N = n - 1, R = N * (N + 1) / 2;
-    const double s3 = n * (n - 1.0) * (n - 2) / 6, s4 = s3 * (n - 3) / 4;
-    return s3 * (3.0 * D + 3.0 * d) + s4 * 6.0 * D + (R - N) * (d + D) + 3 * (R - N - 1) + D;
+    const double c2 = n * (n - 1.0) / 2, c3 = c2 * (n - 2) / 3, c4 = c3 * (n - 3) / 4;
+    return c3 * (3.0 * D + 3.0 * d) + c4 * 6.0 * D + (c2 - n) * (d + D) + D;
 }
 
-}  // namespace
-
 // The kernels sustain about 4.3e12 (F_p), 2.5e11 (complex, real momenta) and
-// 1.9e11 (complex momenta) of these operations per second (n = 8, d = 6 on a
-// GB300), and their per-thread loads of mapped host memory reach about
+// 1.9e11 (complex momenta) of these multiplications per second (n = 8, d = 6
+// on a GB300), and their per-thread loads of mapped host memory reach about
 // 100 GB/s over the host link: in place pays while the batch needs at most
 // 80 GB/s of it.  At n = 8, d = 6 that keeps F_p batches (about 350 GB/s)
 // on copies and takes complex ones (about 60 GB/s) in place.
-bool in_place_pays(const bg_plan* plan, int64_t E, size_t host_bytes) {
+bool in_place_pays_for(int field, int n, int d, int Ds, int H, int64_t E, size_t host_bytes) {
     if (host_bytes <= kInPlaceBytes) return true;
-    const double rate = plan->field == BG_FIELD_FP ? 4.3e12 : plan->field == BG_FIELD_C64_REAL ? 2.5e11 : 1.9e11;
-    const double seconds = (double)E * plan->H * ops_per_amplitude(plan->n, plan->d, plan->Ds) / rate;
+    const double rate = field == BG_FIELD_FP ? 4.3e12 : field == BG_FIELD_C64_REAL ? 2.5e11 : 1.9e11;
+    const double seconds = (double)E * H * ops_per_amplitude(n, d, Ds) / rate;
     return (double)host_bytes <= 80e9 * seconds;
+}
+
+bool in_place_pays(const bg_plan* plan, int64_t E, size_t host_bytes) {
+    return in_place_pays_for(plan->field, plan->n, plan->d, plan->Ds, plan->H, E, host_bytes);
 }
 
 int round_dim(int x) { return x <= 4 ? 4 : (x <= 6 ? 6 : 8); }
@@ -322,6 +321,16 @@ bg_status bg_debug_bounds_report(int* checked, uint64_t* first_violation) {
     *checked = 1;
     *first_violation = v;
 #endif
+    return BG_OK;
+}
+
+bg_status bg_debug_in_place_pays(bg_field field, int n, int d, int D_s, int H, int64_t E, size_t host_bytes,
+                                 int* in_place, double* ops) {
+    if (!in_place || !ops || n < 4 || n > 12 || d < 4 || D_s < d || D_s > 8 || H < 1 || E < 0 ||
+        (field != BG_FIELD_C64 && field != BG_FIELD_FP && field != BG_FIELD_C64_REAL))
+        return fail(BG_ERR_INVALID_ARG, "bad argument to bg_debug_in_place_pays");
+    *ops = bgi::ops_per_amplitude(n, d, D_s);
+    *in_place = bgi::in_place_pays_for((int)field, n, d, D_s, H, E, host_bytes) ? 1 : 0;
     return BG_OK;
 }
 

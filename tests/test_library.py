@@ -93,3 +93,29 @@ def test_fault_injection_arguments(lib):
     assert lib.bg_debug_inject_fault(2, 0, -1) == 1
     for site in (1, 2, 3):
         assert lib.bg_debug_inject_fault(site, 0, 0) == 0      # disarm
+
+
+def test_in_place_decision_on_host(lib):
+    """The copy-or-in-place decision of the host-buffer paths: its operation
+    estimate is the oracle's literal multiplication tally, and at the
+    benchmark shape it keeps light F_p batches on copies (they would need
+    ~350 GB/s over the host link) and reads complex ones in place (~60 GB/s);
+    batches of at most 64 MiB always go in place."""
+    from oracle.bg_oracle import op_tally
+    from paper_2502_07060_gb300 import bg
+    for n, d, Ds in ((4, 4, 4), (5, 4, 4), (8, 6, 6), (8, 4, 6), (10, 6, 8), (12, 8, 8)):
+        _, ops = bg.in_place_pays(bg.FIELD_FP, n, d, Ds, 1, 1, 0)
+        assert ops == op_tally(n, d, Ds).mul
+    E = 1 << 22
+    fp_bytes = E * (8 * 6 * 4 * 2 + 4 + 1)
+    c64r_bytes = E * (8 * 6 * 8 + 8 * 6 * 16 + 16 + 1)
+    assert bg.in_place_pays(bg.FIELD_FP, 8, 6, 6, 1, E, fp_bytes)[0] is False
+    assert bg.in_place_pays(bg.FIELD_C64_REAL, 8, 6, 6, 1, E, c64r_bytes)[0] is True
+    assert bg.in_place_pays(bg.FIELD_C64, 8, 6, 6, 1, E, E * (8 * 6 * 16 * 2 + 17))[0] is True
+    assert bg.in_place_pays(bg.FIELD_C64, 4, 4, 4, 1, E, E * (4 * 4 * 16 * 2 + 17))[0] is False
+    assert bg.in_place_pays(bg.FIELD_FP, 8, 6, 6, 1, 1 << 16, 64 << 20)[0] is True
+    assert bg.in_place_pays(bg.FIELD_FP, 8, 6, 6, 1, 1 << 16, (64 << 20) + 1)[0] is False
+    # all helicities of a point (H amplitudes) carry H times the arithmetic
+    assert bg.in_place_pays(bg.FIELD_FP, 10, 4, 4, 1024, 1 << 20, (1 << 20) * 4600)[0] is True
+    with pytest.raises(bg.BGError):
+        bg.in_place_pays(bg.FIELD_FP, 3, 4, 4, 1, 1, 0)
