@@ -464,6 +464,9 @@ static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, 
         pl->fpo.r2 = (uint32_t)r2;
         pl->fpo.r3 = (uint32_t)r3;
         pl->fpo.pm2 = p - 2;
+        uint64_t rn3 = r3;                        // R^(n+3): states enter unconverted
+        for (int i = 0; i < n; ++i) rn3 = mulmod64(rn3, r1, p);
+        pl->fpo.rn3 = (uint32_t)rn3;
     }
 
     if (cudaGetDevice(&pl->device) != cudaSuccess) {

@@ -290,10 +290,10 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
         const io_t* ep = ein + ((e * NLEG + l) * a.S + s) * a.ds_in;
         T v[DS];
         if constexpr (F::kIsFp) {
-            uint32_t raw[DS];
-            load_leg_fp<DS>(ep, a.ds_in, vec_eps, raw);
-#pragma unroll
-            for (int mu = 0; mu < DS; ++mu) v[mu] = f.from_io(raw[mu]);
+            // canonical residues kept as they are (level 0, no Montgomery
+            // conversion): each current of length m is then uniformly one
+            // level lower per state, which amplitude_raw undoes at the end
+            load_leg_fp<DS>(ep, a.ds_in, vec_eps, v);
         } else {
 #pragma unroll
             for (int mu = 0; mu < DS; ++mu) v[mu] = (mu < a.ds_in) ? f.from_io(ld_once(ep + mu)) : f.zero();
@@ -483,7 +483,8 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
             Sr[sidx_ok(sidx)] = f.c_to_t(sa);
         } else {
             // a5: contract the top bracket with the last polarisation
-            result = f.template amplitude<DSL, METRIC>(acc, eL);
+            if constexpr (F::kIsFp) result = f.template amplitude_raw<DSL, METRIC>(acc, eL);
+            else result = f.template amplitude<DSL, METRIC>(acc, eL);
         }
     };
 #pragma unroll 1

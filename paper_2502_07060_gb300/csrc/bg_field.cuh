@@ -77,6 +77,7 @@ struct FpOps {
     static constexpr int kField = 1;
 
     uint32_t p, pinv, r2, r3, one, pm2;   // r2 = R^2, r3 = R^3, one = R (mod p)
+    uint32_t rn3;                          // R^(n+3) mod p for the plan's n (amplitude_raw)
 
     __device__ __forceinline__ uint32_t redc(uint64_t t) const {
         const uint32_t m = static_cast<uint32_t>(t) * pinv;
@@ -185,6 +186,20 @@ struct FpOps {
 #pragma unroll
         for (int mu = 0; mu < K; ++mu) r[mu] = mmul(reduce96(acc[mu]), r3);   // level 1
         const C a = dot<K, METRIC>(eps_last, r);                               // level 0 = canonical
+        return a == p ? 0u : a;
+    }
+    // The same contraction when the states were taken as canonical residues
+    // (level 0) instead of level 1: every current is multilinear in the
+    // states of its legs, so a current of length m then sits at level 1 - m
+    // (one level lower per state, uniformly in all its terms), R_top at
+    // level 2 - n.  reduce96 gives level -n, times R^(n+3) level 2, and the
+    // contraction with the level-0 last state level 0 = canonical.
+    template <int K, int METRIC>
+    __device__ __forceinline__ io_t amplitude_raw(const A* acc, const T* eps_last) const {
+        T r[K];
+#pragma unroll
+        for (int mu = 0; mu < K; ++mu) r[mu] = mmul(reduce96(acc[mu]), rn3);
+        const C a = dot<K, METRIC>(eps_last, r);
         return a == p ? 0u : a;
     }
     // P^2 (level 0 coefficient) -> level 1 input of the batched inverse
