@@ -50,7 +50,8 @@ def literal_tally(n, d, Ds):
 def kernel_mults(n, d, Ds):
     """Field multiplications the CUDA kernel performs per amplitude in its
     regrouped form (dots shared between V3 and V4, one scalar-vector product
-    per sub-current, batched inversion), input conversion included."""
+    per sub-current, batched inversion), conversion of the momenta to
+    Montgomery form included (the states enter as canonical residues)."""
     N = n - 1
     tot = 0
     for m in range(2, N + 1):
@@ -66,7 +67,7 @@ def kernel_mults(n, d, Ds):
     ns = N * (N + 1) // 2 - N - 1
     tot += 3 * ns + 45                           # batched inverse + one Fermat power (~45)
     tot += Ds                                    # final contraction
-    tot += N * d + n * Ds                        # conversion to Montgomery form
+    tot += N * d                                 # momenta to Montgomery form
     return tot
 
 
