@@ -111,23 +111,18 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name):
-    """DRAM bytes per 2^22-point launch from the ncu summary profiles/<name>,
-    or None when the kernel sources changed since that capture."""
-    path = os.path.join(ROOT, "profiles", name)
-    vals = {}
+def profiled_traffic(kernel):
+    """DRAM bytes per 2^22-point launch of `kernel` ("fp" or "c64") from
+    bench_traffic.json (ncu counters of a smaller capture scaled by the point
+    count), or None when the kernel sources changed since that capture."""
     try:
-        with open(path) as f:
-            for line in f:
-                if ":" in line and line.split(":")[0].strip() in (
-                        "kernel_source_sha256_16", "traffic_bytes_per_launch_2p22"):
-                    k, v = line.split(":", 1)
-                    vals[k.strip()] = v.strip()
-    except OSError:
+        with open(os.path.join(ROOT, "bench_traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
         return None
-    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+    if not rec or rec.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
-    return float(vals["traffic_bytes_per_launch_2p22"])
+    return float(rec["dram_bytes_per_launch_2p22"])
 
 
 def read_peaks():
@@ -830,8 +825,8 @@ def main():
     ops_c64 = kernel_fp64_ops(N_LEG, D, DS, True)
     ops_c64c = kernel_fp64_ops(N_LEG, D, DS, False)
     kops = kernel_mults(N_LEG, D, DS)
-    traffic_fp = profiled_traffic("fp_compact_n8_d6.md")
-    traffic_c64 = profiled_traffic("c64_real_compact_n8_d6.md")
+    traffic_fp = profiled_traffic("fp")
+    traffic_c64 = profiled_traffic("c64")
     scale = E / float(1 << 22)
     line = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
@@ -847,8 +842,8 @@ def main():
                      "peak_derivation": f"{n_sm} SMs x 32 64-bit products/clk x {sm_max:.0f} MHz, one product "
                                         f"per field multiplication (derived from the IMAD unit: 64 lanes/clk, 64-bit "
                                         f"results at half rate; measured 27/clk/SM for the kernel's accumulation)",
-                     "traffic_source": "profiles/fp_compact_n8_d6.md, ncu capture of 2^19 points "
-                                       "scaled by the point count"},
+                     "traffic_source": "bench_traffic.json: ncu DRAM counters of a 2^19-point "
+                                       "capture scaled by the point count"},
         "c64": None if c64 is None else {
             "value": world * c64["value_per_rank"], "unit": "amplitudes/s",
             "ms_per_step": c64["ms_per_step"], "points_per_step": Ec, "steps": c64_steps,

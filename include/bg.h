@@ -391,24 +391,6 @@ const char* bg_last_error(void);
 int bg_version(void);
 
 /*
- * bg_debug_inject_fault -- testing aid for the failure paths (no counterpart
- * in the paper).  Operations at `site` number 0, 1, 2, ... from this call on;
- * operations skip .. skip+count-1 fail as if the CUDA runtime had refused
- * them, without calling it (nothing reaches the GPU, so nothing can fault
- * there), and every later one runs normally.  count = 0 disarms the site.
- * Process-wide; not meant for production use.
- *   BG_FAULT_DEVICE_ALLOC  device allocations: the assignment table of
- *                          bg_plan_create*, the arena of bg_serve_create ->
- *                          BG_ERR_NOMEM
- *   BG_FAULT_LAUNCH        kernel and graph launches of bg_eval,
- *                          bg_eval_noalloc, bg_batch_launch, bg_cut_trace ->
- *                          BG_ERR_CUDA, outputs untouched
- *   BG_FAULT_COPY          asynchronous copies of bg_eval_host (per chunk)
- *                          and of served requests -> BG_ERR_CUDA (for a
- *                          served request, from its bg_serve_wait)
- * Returns BG_ERR_INVALID_ARG for an unknown site or negative skip / count.
- */
-/*
  * bg_debug_bounds_report -- testing aid for memory safety (no counterpart in
  * the paper).  A library compiled with BG_CHECKED compares every index into
  * the recursion tables with the extent of its region before the access; a
@@ -441,6 +423,25 @@ typedef enum {
     BG_FAULT_LAUNCH = 2,
     BG_FAULT_COPY = 3
 } bg_fault_site;
+
+/*
+ * bg_debug_inject_fault -- testing aid for the failure paths (no counterpart
+ * in the paper).  Operations at `site` number 0, 1, 2, ... from this call on;
+ * operations skip .. skip+count-1 fail as if the CUDA runtime had refused
+ * them, without calling it (nothing reaches the GPU, so nothing can fault
+ * there), and every later one runs normally.  count = 0 disarms the site.
+ * Process-wide; not meant for production use.
+ *   BG_FAULT_DEVICE_ALLOC  device allocations: the assignment table of
+ *                          bg_plan_create*, the arena of bg_serve_create ->
+ *                          BG_ERR_NOMEM
+ *   BG_FAULT_LAUNCH        kernel and graph launches of bg_eval,
+ *                          bg_eval_noalloc, bg_batch_launch, bg_cut_trace ->
+ *                          BG_ERR_CUDA, outputs untouched
+ *   BG_FAULT_COPY          asynchronous copies of bg_eval_host (per chunk)
+ *                          and of served requests -> BG_ERR_CUDA (for a
+ *                          served request, from its bg_serve_wait)
+ * Returns BG_ERR_INVALID_ARG for an unknown site or negative skip / count.
+ */
 bg_status bg_debug_inject_fault(bg_fault_site site, int skip, int count);
 
 #ifdef __cplusplus

@@ -1,9 +1,11 @@
 """Build of the CUDA library ``libbg.so`` (sm_103a) with nvcc.
 
-Every ``csrc/*.cu`` file is compiled to an object in parallel (one per field
-and n, so the large unrolled kernels spread over all cores), then linked
-into ``_build/libbg.so`` with the CUDA runtime linked statically.  Objects
-are rebuilt only when their source or a header is newer.
+Every ``csrc/*.cu`` file is compiled to an object in parallel (one per
+field and dimension pair, so the kernel instances spread over all cores),
+then linked into ``_build/libbg.so`` with the CUDA runtime linked
+statically.  Objects are rebuilt only when their source or a header is
+newer.  The multiply-pipe benchmark behind the roofline peaks is built only
+on request (``build_pipe_benchmark``).
 """
 
 from __future__ import annotations
@@ -71,11 +73,11 @@ def build(jobs=None, verbose=False, force=False, checked=False):
         objs.append(o)
         if force or _stale(o, s, hdr_mtime):
             todo.append((s, o))
-    # the slowest translation units (the two batch kernels, the unrolled
-    # per-n kernels) first, so the pool drains evenly
+    # the slowest translation units (the two batch kernels) first, so the
+    # pool drains evenly
     def weight(src):
         b = os.path.basename(src)
-        return (b.startswith("bg_batch_"), b.startswith("bg_inst_fp_n"), b)
+        return (b.startswith("bg_batch_"), b)
     todo.sort(key=lambda so: weight(so[0]), reverse=True)
     logs = {}
     if todo:
@@ -91,8 +93,6 @@ def build(jobs=None, verbose=False, force=False, checked=False):
     if verbose:
         for s, log in logs.items():
             print(f"== {os.path.basename(s)}\n{log}")
-    if not checked:
-        build_pipe_benchmark()
     return lib
 
 
@@ -102,7 +102,8 @@ PEAKS_BIN = os.path.join(OUT, "pipe_throughput")
 
 def build_pipe_benchmark():
     """The stand-alone multiply-pipe benchmark behind the roofline peaks
-    (run it as _build/pipe_throughput on a GB300)."""
+    (``python -m paper_2502_07060_gb300.build --peaks`` builds it; run it as
+    _build/pipe_throughput on a GB300).  Not part of the library build."""
     if os.path.exists(PEAKS_BIN) and os.path.getmtime(PEAKS_BIN) >= os.path.getmtime(PEAKS_SRC):
         return PEAKS_BIN
     tmp = PEAKS_BIN + f".tmp{os.getpid()}"
@@ -115,4 +116,8 @@ if __name__ == "__main__":
     import sys
     import time
     t0 = time.time()
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv), f"{time.time() - t0:.1f}s")
+    if "--peaks" in sys.argv:
+        os.makedirs(OUT, exist_ok=True)
+        print(build_pipe_benchmark(), f"{time.time() - t0:.1f}s")
+    else:
+        print(build(verbose="-v" in sys.argv, force="-f" in sys.argv), f"{time.time() - t0:.1f}s")

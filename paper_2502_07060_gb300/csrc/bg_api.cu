@@ -15,9 +15,6 @@
 
 #include "bg_internal.h"
 
-#define BG_REG(TAG, N) void bg_register_##TAG##_n##N(std::vector<bgk::KernelEntry>&);
-BG_REG(fp, 5) BG_REG(fp, 6) BG_REG(fp, 7) BG_REG(fp, 8)
-#undef BG_REG
 #define BG_REGC(TAG, D, DS) void bg_register_compact_##TAG##_##D##_##DS(std::vector<bgk::KernelEntry>&);
 BG_REGC(fp, 4, 4) BG_REGC(fp, 4, 6) BG_REGC(fp, 4, 8) BG_REGC(fp, 6, 6) BG_REGC(fp, 6, 8) BG_REGC(fp, 8, 8)
 BG_REGC(c64, 4, 4) BG_REGC(c64, 4, 6) BG_REGC(c64, 4, 8) BG_REGC(c64, 6, 6) BG_REGC(c64, 6, 8)
@@ -87,8 +84,6 @@ const std::vector<bgk::KernelEntry>& registry() {
     static std::vector<bgk::KernelEntry> v;
     static std::once_flag once;
     std::call_once(once, [] {
-#define BG_ADD(TAG, N) bg_register_##TAG##_n##N(v);
-        BG_ADD(fp, 5) BG_ADD(fp, 6) BG_ADD(fp, 7) BG_ADD(fp, 8)
 #define BG_ADDC(TAG, D, DS) bg_register_compact_##TAG##_##D##_##DS(v);
         BG_ADDC(fp, 4, 4) BG_ADDC(fp, 4, 6) BG_ADDC(fp, 4, 8) BG_ADDC(fp, 6, 6) BG_ADDC(fp, 6, 8)
         BG_ADDC(fp, 8, 8) BG_ADDC(c64, 4, 4) BG_ADDC(c64, 4, 6) BG_ADDC(c64, 4, 8) BG_ADDC(c64, 6, 6)
@@ -96,7 +91,6 @@ const std::vector<bgk::KernelEntry>& registry() {
         BG_ADDC(c64r, 4, 4) BG_ADDC(c64r, 4, 6) BG_ADDC(c64r, 4, 8) BG_ADDC(c64r, 6, 6)
         BG_ADDC(c64r, 6, 8) BG_ADDC(c64r, 8, 8)
 #undef BG_ADDC
-#undef BG_ADD
     });
     return v;
 }
@@ -390,30 +384,18 @@ static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, 
                 return fail(BG_ERR_INVALID_ARG, "assign[%lld] = %d >= n_states", (long long)i, assign[i]);
     }
 
-    // Kernel choice: the compact kernel (run-time n) by default; the unrolled
-    // per-n kernel on request (BG_KERNEL=unrolled, F_p only, n <= 8).  Table
-    // placement: shared memory for small tables, else global scratch, or split
-    // (currents global, the rest on chip) (BG_TABLE=shared|global|split
-    // overrides).
-    const char* kenv = getenv("BG_KERNEL");
-    const bool want_unrolled = kenv && strcmp(kenv, "unrolled") == 0;
+    // Kernel choice: the compact kernel (run-time n) for the plan's (D, D_s,
+    // metric).  Table placement: shared memory for small tables, else global
+    // scratch, or split (currents global, the rest on chip)
+    // (BG_TABLE=shared|global|split overrides).
     const char* tenv = getenv("BG_TABLE");
     const int Dk = round_dim(d), DSk = round_dim(D_s);
     // mixed kernels only pay where a current has more than four components
     const bool want_mixed = four_d_legs != 0 && DSk > 4;
     const bgk::KernelEntry* best = nullptr;
-    int words = 0;
-    if (want_unrolled && four_d_legs)
-        return fail(BG_ERR_UNSUPPORTED, "the unrolled kernel has no four-dimensional legs");
-    if (want_unrolled) {
-        const int Du = round_dim(D_s > d ? D_s : d);
-        for (const auto& e : registry())
-            if (!e.compact && e.field == (int)field && e.n == n && e.metric == (int)metric && e.D == Du)
-                best = &e;
-        if (best) words = best->words;
-    } else {
-        const bgk::Geometry geo{n - 1};
-        words = geo.words(Dk, DSk);
+    const bgk::Geometry geo{n - 1};
+    int words = geo.words(Dk, DSk);
+    {
         const size_t elem = value_bytes(field);
         int want = bgk::kPlaceGlobal;
         if (tenv) {
@@ -427,15 +409,15 @@ static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, 
         }
         for (const auto& e : registry()) {
             const int place = e.split ? bgk::kPlaceSplit : e.global_table ? bgk::kPlaceGlobal : bgk::kPlaceShared;
-            if (e.compact && e.field == (int)field && e.D == Dk && e.DS == DSk &&
-                e.metric == (int)metric && place == want && e.mixed == want_mixed)
+            if (e.field == (int)field && e.D == Dk && e.DS == DSk && e.metric == (int)metric && place == want &&
+                e.mixed == want_mixed)
                 best = &e;
         }
         if (best && best->split) words = geo.cur_words(DSk);
         if (!best)      // the complex fields have only the global placement, mixed F_p no split
             for (const auto& e : registry())
-                if (e.compact && e.field == (int)field && e.D == Dk && e.DS == DSk &&
-                    e.metric == (int)metric && e.mixed == want_mixed && !e.split)
+                if (e.field == (int)field && e.D == Dk && e.DS == DSk && e.metric == (int)metric &&
+                    e.mixed == want_mixed && !e.split)
                     best = &e;
     }
     if (!best) return fail(BG_ERR_UNSUPPORTED, "no kernel for n=%d d=%d D_s=%d field=%d metric=%d", n, d,
@@ -453,11 +435,6 @@ static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, 
         const uint64_t r1 = (uint64_t(1) << 32) % p;
         const uint64_t r2 = mulmod64(r1, r1, p);
         const uint64_t r3 = mulmod64(r2, r1, p);
-        pl->fp.p = p;
-        pl->fp.pinv = 0u - inv;
-        pl->fp.one = (uint32_t)r1;
-        pl->fp.r2 = (uint32_t)r2;
-        pl->fp.pm2 = p - 2;
         pl->fpo.p = p;
         pl->fpo.pinv = 0u - inv;
         pl->fpo.one = (uint32_t)r1;
@@ -603,11 +580,10 @@ bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
         return BG_OK;
     }
     int w = snprintf(buf, len,
-                     "field=%s n=%d d=%d D_s=%d kernel=%s kernel_D=%d kernel_D_s=%d metric=%s "
+                     "field=%s n=%d d=%d D_s=%d kernel=compact kernel_D=%d kernel_D_s=%d metric=%s "
                      "table=%s block=%d blocks_per_sm=%d smem=%zu words_per_thread=%d elem_bytes=%d "
                      "four_dim_legs=0x%x",
-                     field_name(plan->field), plan->n, plan->d, plan->Ds,
-                     e->compact ? "compact" : "unrolled", e->D, e->DS,
+                     field_name(plan->field), plan->n, plan->d, plan->Ds, e->D, e->DS,
                      plan->metric == BG_METRIC_MOSTLY_MINUS ? "mostly_minus" : "alternating",
                      e->split ? "split" : e->global_table ? "global" : "shared", e->block, plan->blocks_per_sm,
                      plan->smem_bytes, plan->words, e->elem_bytes, plan->four_d_legs);
@@ -680,24 +656,14 @@ bg_status eval_impl(const bg_plan* plan, int64_t E, const void* momenta, const v
     int64_t blocks = (items + e->block - 1) / e->block;
     const int64_t cap = e->global_table ? resident_blocks(plan) : resident_blocks(plan) * 256;
     if (blocks > cap) blocks = cap;
-    if (e->compact) {
-        bgk::CompactArgs a;
-        a.E = E; a.H = plan->H; a.S = plan->S; a.n = plan->n;
-        a.d_in = plan->d; a.ds_in = plan->Ds;
-        a.k = momenta; a.eps = eps; a.out = out; a.status = status;
-        a.assign = plan->d_assign; a.ws = workspace;
-        a.four_d_legs = plan->four_d_legs;
-        a.violation = bgi::violation_word(dev);
-        e->launch(compact_params(plan), &a, dim3((unsigned)blocks), plan->smem_bytes, stream);
-    } else {
-        bgk::LaunchArgs a;
-        a.E = E; a.H = plan->H; a.S = plan->S;
-        a.d_in = plan->d; a.ds_in = plan->Ds;
-        a.k = momenta; a.eps = eps; a.out = out; a.status = status;
-        a.assign = plan->d_assign; a.ws = workspace;
-        const void* fparams = plan->field == BG_FIELD_FP ? (const void*)&plan->fp : (const void*)&plan->c64;
-        e->launch(fparams, &a, dim3((unsigned)blocks), plan->smem_bytes, stream);
-    }
+    bgk::CompactArgs a;
+    a.E = E; a.H = plan->H; a.S = plan->S; a.n = plan->n;
+    a.d_in = plan->d; a.ds_in = plan->Ds;
+    a.k = momenta; a.eps = eps; a.out = out; a.status = status;
+    a.assign = plan->d_assign; a.ws = workspace;
+    a.four_d_legs = plan->four_d_legs;
+    a.violation = bgi::violation_word(dev);
+    e->launch(compact_params(plan), &a, dim3((unsigned)blocks), plan->smem_bytes, stream);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return fail(BG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(err));
     return BG_OK;

@@ -1,6 +1,7 @@
 // bg_instances.cuh -- compile-time kernel variants and their registry rows.
 //
-// One row per (field, n, D, D_s, metric, table placement).  Momentum and
+// One row per (field, D, D_s, metric, table placement, mixed); n is a
+// run-time parameter of every kernel.  Momentum and
 // polarisation dimensions are compiled for D, D_s in {4, 6, 8}; a request
 // with odd d or D_s runs on the next even instance with zero padding, which
 // leaves the amplitude unchanged (Sec. 2.3: lower-dimensional vectors are
@@ -11,52 +12,22 @@
 #include <vector>
 
 #include "bg_compact.cuh"
-#include "bg_kernel.cuh"
 
 namespace bgk {
 
 struct KernelEntry {
     int field;          // bg_field: 0 = C64, 1 = F_p, 2 = C64 with real momenta
-    int n;              // gluons; 0 for the compact kernel (any n)
     int D, DS, metric;
     bool global_table;  // (part of the) table in global scratch: the workspace is needed
     bool split;         // currents in global scratch, the rest in shared memory
-    bool compact;       // run-time n (bg_compact_kernel) or unrolled per n
     bool mixed;         // evaluates ranges of four-dimensional legs with four components
     int block;          // threads per block
-    int words;          // table elements per thread (unrolled kernels)
     int elem_bytes;     // sizeof(T)
     const void* func;   // the __global__ function
-    // launch(field params, args (LaunchArgs or CompactArgs), grid, smem, stream)
+    // launch(field params, CompactArgs, grid, smem, stream)
     void (*launch)(const void* field_params, const void* args, dim3 grid, size_t smem,
                    cudaStream_t stream);
 };
-
-template <class F, int NLEG, int D, int DS, int M, int B, bool G>
-void launch_impl(const void* fp, const void* args, dim3 grid, size_t smem, cudaStream_t s) {
-    const F& f = *static_cast<const F*>(fp);
-    bg_recursion_kernel<F, NLEG, D, DS, M, B, G><<<grid, B, smem, s>>>(f, *static_cast<const LaunchArgs*>(args));
-}
-
-template <class F, int NLEG, int D, int DS, int M, int B, bool G>
-KernelEntry make_entry() {
-    KernelEntry e;
-    e.field = F::kIsFp ? 1 : 0;
-    e.n = NLEG;
-    e.D = D;
-    e.DS = DS;
-    e.metric = M;
-    e.global_table = G;
-    e.split = false;
-    e.compact = false;
-    e.mixed = false;
-    e.block = B;
-    e.words = Frame<NLEG - 1, D, DS>::WORDS;
-    e.elem_bytes = sizeof(typename F::T);
-    e.func = reinterpret_cast<const void*>(&bg_recursion_kernel<F, NLEG, D, DS, M, B, G>);
-    e.launch = &launch_impl<F, NLEG, D, DS, M, B, G>;
-    return e;
-}
 
 template <class F, int D, int DS, int M, int B, int G, bool X>
 void launch_compact(const void* fp, const void* args, dim3 grid, size_t smem, cudaStream_t s) {
@@ -68,44 +39,17 @@ template <class F, int D, int DS, int M, int B, int G, bool X = false>
 KernelEntry make_compact() {
     KernelEntry e;
     e.field = F::kField;
-    e.n = 0;
     e.D = D;
     e.DS = DS;
     e.metric = M;
     e.global_table = G != kPlaceShared;
     e.split = G == kPlaceSplit;
-    e.compact = true;
     e.mixed = X;
     e.block = B;
-    e.words = 0;
     e.elem_bytes = sizeof(typename F::T);
     e.func = reinterpret_cast<const void*>(&bg_compact_kernel<F, D, DS, M, B, G, X>);
     e.launch = &launch_compact<F, D, DS, M, B, G, X>;
     return e;
-}
-
-// Thread-block sizes: F_p with the table in shared memory uses 64 threads
-// (n = 8, D_s = 6: 1000 B per thread, three blocks per SM); global-table
-// variants use 128 (F_p) and 64 (C64) threads.
-constexpr int kBlockFpSmem = 64;
-constexpr int kBlockFpGlobal = 128;
-constexpr int kBlockC64 = 64;
-
-// Unrolled kernels (one per n) are built for F_p with the table in shared
-// memory; they are kept to compare against the compact kernel.
-template <int NLEG, int D, int M>
-void add_unrolled(std::vector<KernelEntry>& v) {
-    v.push_back(make_entry<FieldFp, NLEG, D, D, M, kBlockFpSmem, false>());
-}
-
-template <int NLEG>
-void register_unrolled(std::vector<KernelEntry>& v) {
-    add_unrolled<NLEG, 4, 0>(v);
-    add_unrolled<NLEG, 6, 0>(v);
-    add_unrolled<NLEG, 8, 0>(v);
-    add_unrolled<NLEG, 4, 1>(v);
-    add_unrolled<NLEG, 6, 1>(v);
-    add_unrolled<NLEG, 8, 1>(v);
 }
 
 // Compact kernels: every (D, D_s) pair with D <= D_s in {4, 6, 8}, both
@@ -141,11 +85,6 @@ void register_compact(std::vector<KernelEntry>& v) {
 }
 
 }  // namespace bgk
-
-#define BG_DEFINE_REGISTRY(NLEG, FP, TAG)                                     \
-    void bg_register_##TAG##_n##NLEG(std::vector<bgk::KernelEntry>& v) {      \
-        bgk::register_unrolled<NLEG>(v);                                      \
-    }
 
 #define BG_DEFINE_COMPACT(D, DS, OPS, TAG)                                    \
     void bg_register_compact_##TAG##_##D##_##DS(std::vector<bgk::KernelEntry>& v) { \

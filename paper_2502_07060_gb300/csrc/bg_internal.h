@@ -22,10 +22,9 @@ struct bg_plan {
     uint8_t* d_assign = nullptr;      // device copy when H > 1
     int device = -1;                  // device of d_assign / attribute setup
     const bgk::KernelEntry* entry = nullptr;
-    int words = 0;                    // table elements per thread
-    bgk::FieldFp fp{};                // unrolled kernels
-    bgk::FieldC64 c64{};
-    bgk::FpOps fpo{};                 // compact kernels
+    int words = 0;                    // table elements per thread (or per thread in global
+                                      // scratch for the split placement)
+    bgk::FpOps fpo{};                 // field constants of the kernels
     bgk::C64Ops c64o{};
     bgk::C64ROps c64ro{};
     int sm_count = 0;

@@ -91,7 +91,7 @@ extern "C" bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void*
     const int D = bgi::round_dim(plan->d), DS = bgi::round_dim(plan->Ds);
     const bgk::KernelEntry* e = nullptr;
     for (const auto& k : bgi::registry())
-        if (k.compact && k.global_table && !k.split && k.field == (int)plan->field && k.D == D &&
+        if (k.global_table && !k.split && k.field == (int)plan->field && k.D == D &&
             k.DS == DS && k.metric == (int)plan->metric && k.mixed == plan->entry->mixed)
             e = &k;
     if (!e) return bgi::fail(BG_ERR_UNSUPPORTED, "no global-table kernel for this plan");

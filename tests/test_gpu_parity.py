@@ -41,7 +41,7 @@ def _dev_c(a):
 
 
 class _env:
-    """Temporarily set BG_TABLE / BG_KERNEL (read at plan creation)."""
+    """Temporarily set BG_TABLE (read at plan creation)."""
 
     def __init__(self, **kv):
         self.kv = {k: v for k, v in kv.items() if v is not None}
@@ -58,11 +58,11 @@ class _env:
                 os.environ[k] = v
 
 
-def run_fp(k, eps, p, metric, n_states=1, assign=None, table=None, kernel=None):
+def run_fp(k, eps, p, metric, n_states=1, assign=None, table=None):
     bg = _bg()
     E, n, d = k.shape
     Ds = eps.shape[-1]
-    with _env(BG_TABLE=table, BG_KERNEL=kernel):
+    with _env(BG_TABLE=table):
         plan = bg.Plan(n, d, Ds, bg.FIELD_FP, p, metric, n_states, assign)
     out, st = plan.eval(_dev_u32(k), _dev_u32(eps))
     import torch
@@ -118,18 +118,6 @@ def test_fp_split_placement_bit_exact(n, d, Ds, metric, p):
     out, st, plan = run_fp(k, eps, p, metric, table="split")
     assert "table=split" in plan.describe()
     assert np.array_equal(st, rst) and np.array_equal(out, ref)
-
-
-@pytest.mark.parametrize("n,d,metric", [(5, 4, 0), (6, 6, 1), (7, 8, 0), (8, 6, 0), (8, 4, 1)])
-def test_fp_unrolled_kernel_bit_exact(n, d, metric):
-    """The per-n unrolled kernel (kept for comparison) is bit-exact too."""
-    E = 2 * 64 + 13
-    p = P if metric == 0 else PM
-    k, eps = G.fp_batch(300 + n, E, n, d, d, p, metric)
-    ref, _ = C.amp_fp(k, eps, p, metric)
-    out, _, plan = run_fp(k, eps, p, metric, kernel="unrolled")
-    assert "kernel=unrolled" in plan.describe()
-    assert np.array_equal(out, ref)
 
 
 def c64_tolerance(k, eps, metric, hi, lo, spt=None):
