@@ -11,9 +11,12 @@ the launching stream; max over ranks.  The printed JSON line's headline
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Multi-GPU (torchrun): each rank evaluates its own independent batch (weak
-scaling, no data-path collective); the process group only provides the
-barrier and the max over ranks of the elapsed time.
+Multi-GPU: ``--gpus N`` started as a plain process re-runs itself as N ranks
+under torch.distributed.run (started by torchrun, it reads RANK, LOCAL_RANK
+and WORLD_SIZE from the environment).  Each rank evaluates its own
+independent batch on its own GPU (weak scaling, no data-path collective); the
+process group only provides the barrier and the max over ranks of the elapsed
+time.
 """
 
 from __future__ import annotations
@@ -45,6 +48,32 @@ def literal_tally(n, d, Ds):
     mul = comb(n, 3) * (3 * Ds + 3 * d) + comb(n, 4) * 6 * Ds + (comb(n, 2) - n) * (d + Ds) + Ds
     add = None
     return mul, add
+
+
+def literal_flops(n, d, Ds, real_k):
+    """FP64 operations of the literal recursion at (n, d, D_s) over complex
+    FP64 (the oracle's FLOP tally, a closed formula): products real x real 1,
+    real x complex 2, complex x complex 6; sums 1 with a real operand, 2 with
+    two complex ones; reciprocal 1 (real) or 6 (complex); nothing for
+    negations and for sums that start from zero.  real_k: real momenta (the
+    physical points)."""
+    N = n - 1
+    tot = 0
+    for m in range(2, N + 1):
+        s3, s4 = m - 1, (m - 1) * (m - 2) // 2
+        per = s4 * (48 * Ds - 4) - 2 * Ds
+        if real_k:
+            per += s3 * (24 * Ds + 13 * d - 2)
+            if m < N:
+                per += 2 * d + 2 * Ds                  # P^2, reciprocal, J = R / P^2
+        else:
+            per += s3 * (24 * Ds + 26 * d - 2)
+            if m < N:
+                per += 8 * d + 4 + 6 * Ds
+        tot += (N - m + 1) * per
+    tot += 8 * Ds - 2                                   # final contraction
+    tot += (1 if real_k else 2) * d * N * (N - 1) // 2  # range momenta
+    return tot
 
 
 def kernel_mults(n, d, Ds):
@@ -216,6 +245,44 @@ def max_over_ranks(x, dist, device):
     return float(t.item())
 
 
+def launch_ranks(n):
+    """Re-run this command as n replica ranks (one process per GPU) under
+    torch.distributed.run on this node; returns the launcher's exit code."""
+    import socket
+    with socket.socket() as sock:
+        sock.bind(("127.0.0.1", 0))
+        port = sock.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
+def launch_check(args, rank, world):
+    """The multi-rank path without a GPU (gloo): every rank builds its own
+    seeded batch of the metric's workload, times that as its step, and rank 0
+    prints the aggregated line with each rank's seed and input digest."""
+    import hashlib
+    import torch
+    dist = init_dist(world, "gloo")
+    E = 1 << args.log2_points
+    seed = rank_seed(1000, rank)
+    t0 = time.perf_counter()
+    k, e = G.fp_batch(seed, E, N_LEG, D, DS, P, 0, workers=1)
+    ms = (time.perf_counter() - t0) * 1e3
+    ms_max = max_over_ranks(ms, dist, torch.device("cpu"))
+    mine = {"rank": rank, "seed": seed, "points": E,
+            "digest": hashlib.sha256(k.tobytes() + e.tobytes()).hexdigest()[:16]}
+    ranks = [mine]
+    if dist is not None:
+        ranks = [None] * world
+        dist.all_gather_object(ranks, mine)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "launch_check": True, "n_gpus": world, "ms_per_step": ms_max,
+                          "value": job_value(E, world, ms_max), "scaling": "weak", "ranks": ranks}))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def rank_seed(base, rank):
     """Each rank evaluates its own independent batch (weak scaling)."""
     return base + rank
@@ -249,8 +316,8 @@ def cpu_baseline(field, target_s=10.0):
         m = int(m * min(16.0, max(2.0, target_s / max(dt, 1e-3))))
         m = 1 << max(12, min(20, m.bit_length() - 1))
     return {"value": m / dt, "unit": "amplitudes/s", "cores": threads, "kind": "oracle",
-            "sample": f"{m} points of the n=8 d=D_s=6 {field} workload, C oracle (gcc -O2, OpenMP, "
-                      f"one point per iteration), {dt:.2f} s"}
+            "sample": f"{m} points of the n=8 d=D_s=6 {field} workload, C oracle (gcc -O3 "
+                      f"-ffp-contract=off, OpenMP, one point per iteration), {dt:.2f} s"}
 
 
 # --------------------------------------------------------------------------
@@ -711,13 +778,15 @@ def main():
                          "points through the complex-momentum plan)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving latency leg")
-    ap.add_argument("--workload", choices=["metric", "mixed", "serve", "helicity", "sweep", "fourdim"],
+    ap.add_argument("--workload", choices=["metric", "mixed", "serve", "helicity", "sweep", "fourdim",
+                                           "launchcheck"],
                     default="metric",
                     help="metric: n=8 d=6 headline line; mixed: uneven-batch comparison; "
                          "serve: p50/p99 latency of the request server; helicity: all 2^n "
                          "helicities with shared sub-currents against one recursion per assignment; "
                          "sweep: time against points, gluons and dimension; fourdim: cut trees with "
-                         "four-dimensional legs, ordinary against mixed-dimension plans")
+                         "four-dimensional legs, ordinary against mixed-dimension plans; launchcheck: "
+                         "the multi-rank launch on CPU (gloo), no GPU work")
     ap.add_argument("--log2-points-helicity", type=int, default=20,
                     help="points per n of the helicity workload")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
@@ -727,7 +796,15 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # started as a plain process: become N replica ranks (one per GPU)
+        sys.exit(launch_ranks(args.gpus))
     rank, world, local = dist_env()
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    if args.workload == "launchcheck":
+        launch_check(args, rank, world)
+        return
     E = 1 << args.log2_points
     Ec = 1 << args.log2_points_c64
     config = {"workload": f"n={N_LEG} gluons, d=D_s={D}, mostly-minus metric, F_p p=2^31-19 and "
@@ -736,31 +813,32 @@ def main():
               "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"}
 
     if args.impl == "reference":
+        # the oracle as it stands, on the host cores: every step evaluates a
+        # bounded sample (2^14 points) of the same n=8, d=D_s=6 F_p workload
         if rank != 0:
             return
-        steps = args.steps
-        t_all = 0.0
-        done = 0
         from oracle import coracle
         m = 1 << 14
         k, e = G.fp_batch(4242, m, N_LEG, D, DS, P, 0)
-        for _ in range(min(args.warmup, 1)):
+        for _ in range(args.warmup):
             coracle.amp_fp(k[:1024], e[:1024], P, 0)
-        for _ in range(min(steps, 10)):
+        t_all = 0.0
+        for _ in range(args.steps):
             t0 = time.perf_counter()
             coracle.amp_fp(k, e, P, 0)
             t_all += time.perf_counter() - t0
-            done += m
-        val = done / t_all
+        val = args.steps * m / t_all
         cores = coracle.max_threads()
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "amplitudes/s",
-                "n_gpus": world, "steps": min(steps, 10), "warmup": args.warmup,
-                "ms_per_step": 1e3 * t_all / min(steps, 10), "higher_is_better": True,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": dict(config, reference_points_per_step=m),
+                "config": config,
                 "cpu_baseline": {"value": val, "unit": "amplitudes/s", "cores": cores,
                                  "kind": "oracle",
-                                 "sample": f"{m} points per step of the F_p workload, C oracle"},
+                                 "sample": f"{m} points per step of the n=8 d=D_s=6 F_p workload (of "
+                                           f"{E} per GPU step), C oracle (gcc -O3 -ffp-contract=off, "
+                                           f"OpenMP, one point per iteration) on {cores} host threads"},
                 "e2e": {"value": val, "unit": "amplitudes/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -819,7 +897,8 @@ def main():
     # four-product accumulation 27 field multiplications/clk/SM).
     peak_mulmod = n_sm * 32 * sm_max * 1e6
     achieved = fp["value_per_rank"] * tally
-    c64_flops = 6 * tally + 2 * 5348
+    c64_flops = literal_flops(N_LEG, D, DS, True)        # real momenta (the c64 leg)
+    c64c_flops = literal_flops(N_LEG, D, DS, False)      # complex momenta
     peak_fp64 = n_sm * 2 * 2 * sm_max * 1e6
     peak_fp64_instr = n_sm * 2 * sm_max * 1e6
     ops_c64 = kernel_fp64_ops(N_LEG, D, DS, True)
@@ -850,10 +929,15 @@ def main():
             "dtype": "f64",
             "momenta": "real (physical points; BG_FIELD_C64_REAL plan)",
             "roofline": {"bound": "alu", "achieved": c64["value_per_rank"] * c64_flops,
-                         "peak": peak_fp64, "unit": "FP64 FLOP/s (literal tally of complex operations)",
+                         "peak": peak_fp64, "unit": "FP64 FLOP/s (literal tally, real momenta)",
                          "frac": c64["value_per_rank"] * c64_flops / peak_fp64,
+                         "ops_per_unit": c64_flops,
                          "kernel_fp64_instr_per_unit": ops_c64,
                          "frac_kernel_ops": c64["value_per_rank"] * ops_c64 / peak_fp64_instr,
+                         "frac_note": "frac counts the literal recursion's FP64 work (oracle tally); the "
+                                      "kernel's regrouped recursion issues fewer FP64 operations than the "
+                                      "literal one, so frac can exceed 1; frac_kernel_ops is the FP64 pipe's "
+                                      "share of its instruction peak",
                          "traffic": None if traffic_c64 is None else traffic_c64 * Ec / float(1 << 22),
                          "peak_derivation": f"{n_sm} SMs x 2 DFMA/clk x 2 x {sm_max:.0f} MHz "
                                             f"(kernel ops: FP64 instructions at 2/clk/SM)"},
@@ -863,6 +947,8 @@ def main():
             "value": world * c64c["value_per_rank"], "unit": "amplitudes/s",
             "ms_per_step": c64c["ms_per_step"], "points_per_step": Ec, "steps": c64_steps,
             "kernel_fp64_instr_per_unit": ops_c64c,
+            "literal_flops_per_unit": c64c_flops,
+            "frac": c64c["value_per_rank"] * c64c_flops / peak_fp64,
             "frac_kernel_ops": c64c["value_per_rank"] * ops_c64c / peak_fp64_instr,
             "clocks": c64c["clocks"], "plan": c64c["plan"]},
         "e2e": None if not e2e else {

@@ -32,7 +32,10 @@
  * on the host before any launch (BG_ERR_INVALID_ARG / BG_ERR_UNSUPPORTED) and
  * leave all buffers untouched; CUDA launch errors return BG_ERR_CUDA.
  * Data-dependent failures never trap: a singular propagator (P_{i,j}^2 = 0 for
- * an internal range) sets status[e] = 1 and out = 0 for that point.
+ * an internal range) sets status[e] = 1 and out = 0 for that point.  A library
+ * built with BG_CHECKED also tests each point's inputs against the
+ * preconditions of bg_eval and sets status[e] = 2 and out = 0 for a point
+ * that breaks one.
  * bg_last_error() returns a thread-local message for the last failure.
  */
 #ifndef BG_H
@@ -170,20 +173,28 @@ bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes);
  *   eps        device [E][n][S][D_s]: uint32 (FP) or double2 (complex
  *              fields) (S = n_states)
  *   out        device [E][H]: uint32 in [0,p) (FP) or double2 (complex)
- *   status     device [E] uint8 or NULL: 0 ok, 1 singular propagator
+ *   status     device [E] uint8 or NULL: 0 ok, 1 singular propagator,
+ *              2 precondition broken (checked builds only, see below)
  *   workspace  device buffer of >= bg_workspace_size(plan, E) bytes, 256-byte
  *              aligned, or NULL when that size is 0; concurrent calls need
  *              distinct workspaces
  *   stream     CUDA stream (0 = legacy default stream)
  *
  * Buffers must be on the device that is current at the call, and momenta,
- * eps and out must be aligned to their element size.  Preconditions not
- * checked on the device: canonical F_p inputs (< p), sum k = 0, k_i^2 = 0,
- * eps_i . k_i = 0 for every state.  The kernels use the current conservation
- * that on-shell, transverse inputs imply (P_X . J_X = 0 for every internal
- * current, so the three-gluon coefficients are formed with the range
- * momentum); on inputs that violate the preconditions the numbers are
- * well-defined but not the literal recursion's.
+ * eps and out must be aligned to their element size.
+ *
+ * Preconditions of the inputs (Sec. 2.2: currents of on-shell legs, momentum
+ * conservation imposed at the amplitude): canonical F_p residues (< p),
+ * sum k = 0, k_i^2 = 0, and eps_i . k_i = 0 for every state slot of every
+ * leg.  The kernels use the current conservation these imply (P_X . J_X = 0
+ * for every internal current, so the three-gluon coefficients are formed
+ * with the range momentum).  The ordinary build does not test them: on inputs
+ * that break them the results are unspecified (non-canonical F_p states can
+ * also overflow the kernels' unreduced sums), though every access stays
+ * inside the caller's buffers.  A build with BG_CHECKED tests every point
+ * (exactly over F_p; for the complex fields within 1e-8 of the point's
+ * momentum scale) and reports a point that breaks one with status 2 and
+ * amplitude 0.
  */
 bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta,
                   const void* eps, void* out, uint8_t* status,
@@ -241,9 +252,12 @@ bg_status bg_eval_host(const bg_plan* plan, int64_t E, const void* momenta,
  * device array of 64 MiB inside libbg.so, present on every device that loads
  * the library until the process exits.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.  All calls share
- * the array: calls whose kernels overlap on the GPU race, so order them on
- * one stream.  Nothing in the array needs to start at zero.
+ * current); make that first call before any stream capture.  The address is
+ * kept for the life of the process, so it goes stale if the device's primary
+ * context is torn down (cudaDeviceReset): do not call this entry point after
+ * such a reset in the same process.  All calls share the array: calls whose
+ * kernels overlap on the GPU race, so order them on one stream.  Nothing in
+ * the array needs to start at zero.
  *
  *   plan, E, momenta, eps, out, status, stream: as for bg_eval (buffers on
  *   the current device, caller-owned).  Returns BG_ERR_INVALID_ARG when

@@ -306,6 +306,90 @@ def op_tally(n, d, Ds):
     return r.tally
 
 
+class _FlopValue:
+    """Stand-in number that records FP64 work instead of a value.
+
+    Only its kind is tracked: REAL (a double), COMPLEX (a pair of doubles) or
+    ZERO (the exact zero every sum of the recursion starts from).  Each
+    arithmetic operation adds its cost in FP64 operations to ``counter[0]``:
+    a product real x real 1, real x complex 2, complex x complex 6 (four
+    products and two sums); a sum or difference with a real operand 1, of two
+    complex operands 2; the reciprocal of a real 1, of a complex 6
+    (conj(z) / |z|^2: three for |z|^2, one division, two products).
+    Operations with the exact zero and negations cost nothing, since no
+    floating-point instruction is needed for them."""
+
+    REAL, COMPLEX, ZERO = 0, 1, 2
+    __slots__ = ("kind", "counter")
+
+    def __init__(self, kind, counter):
+        self.kind = kind
+        self.counter = counter
+
+    def _new(self, kind, cost):
+        self.counter[0] += cost
+        return _FlopValue(kind, self.counter)
+
+    def _kind_of(self, o):
+        if isinstance(o, _FlopValue):
+            return o.kind
+        return self.ZERO if o == 0 else self.REAL
+
+    def __add__(self, o):
+        a, b = self.kind, self._kind_of(o)
+        if a == self.ZERO:
+            return _FlopValue(b, self.counter)
+        if b == self.ZERO:
+            return _FlopValue(a, self.counter)
+        both_c = a == self.COMPLEX and b == self.COMPLEX
+        kind = self.COMPLEX if self.COMPLEX in (a, b) else self.REAL
+        return self._new(kind, 2 if both_c else 1)
+
+    __radd__ = __add__
+    __sub__ = __add__
+    __rsub__ = __add__
+
+    def __mul__(self, o):
+        a, b = self.kind, self._kind_of(o)
+        if self.ZERO in (a, b):
+            return _FlopValue(self.ZERO, self.counter)
+        if a == self.COMPLEX and b == self.COMPLEX:
+            return self._new(self.COMPLEX, 6)
+        if self.COMPLEX in (a, b):
+            return self._new(self.COMPLEX, 2)
+        return self._new(self.REAL, 1)
+
+    __rmul__ = __mul__
+
+    def __neg__(self):
+        return _FlopValue(self.kind, self.counter)
+
+    def __rtruediv__(self, o):          # 1 / x, the propagator's reciprocal
+        if self.kind == self.ZERO:
+            raise ZeroDivisionError("reciprocal of the exact zero")
+        return self._new(self.kind, 1 if self.kind == self.REAL else 6)
+
+    def __eq__(self, o):                # only the singular-propagator test
+        return self.kind == self.ZERO and self._kind_of(o) == self.ZERO
+
+    __hash__ = object.__hash__
+
+
+def flop_tally(n, d, Ds, real_momenta=True):
+    """FP64 operations of one literal evaluation of the recursion above over
+    complex FP64, counted by running it on ``_FlopValue`` stand-ins: momenta
+    real (the physical points of Sec. 3) or complex, polarisations complex.
+    The count depends only on (n, d, D_s) and the kinds of the inputs."""
+    counter = [0]
+    kk = _FlopValue.REAL if real_momenta else _FlopValue.COMPLEX
+    k = [[_FlopValue(kk, counter) for _ in range(d)] for _ in range(n)]
+    eps = [[_FlopValue(_FlopValue.COMPLEX, counter) for _ in range(Ds)] for _ in range(n)]
+    r = bg_recursion(k, eps, MOSTLY_MINUS, zero=_FlopValue(_FlopValue.ZERO, counter))
+    if r.status != OK:
+        raise RuntimeError("flop tally hit the exact zero as a propagator")
+    return counter[0]
+
+
 # --------------------------------------------------------------------------
 # Brute-force Feynman-diagram sum with the explicit vertex tensors
 # --------------------------------------------------------------------------

@@ -74,6 +74,108 @@ __device__ __forceinline__ int checked_slot(unsigned long long* violation, int i
     return idx;
 }
 
+// Input preconditions of the boundary (builds compiled with BG_CHECKED;
+// ordinary builds never call this): every F_p value canonical (< p), momentum
+// conservation sum_l k_l = 0, on-shell legs k_l^2 = 0 and transverse states
+// eps_{l,s} . k_l = 0 for every state s (Sec. 2.2 builds the currents from
+// on-shell legs and imposes momentum conservation at the amplitude; the
+// kernels rely on the current conservation these imply).  Exact over F_p
+// (plain modular arithmetic on the canonical inputs); for the complex fields
+// within kPreconditionTol relative to the point's momentum scale kmax (the
+// largest Euclidean norm of its momenta): |sum k| <= tol kmax,
+// |k_l^2| <= tol kmax^2, |eps . k_l| <= tol |eps| kmax.
+constexpr double kPreconditionTol = 1e-8;
+
+template <int METRIC>
+__device__ inline bool fp_preconditions(uint32_t p, const uint32_t* k, const uint32_t* eps, int n, int d, int ds,
+                                        int S, const int* used) {
+    const uint64_t P = p;
+    for (int i = 0; i < n * d; ++i)
+        if (k[i] >= p) return false;
+    for (int l = 0; l < n; ++l)
+        for (int i = 0; i < (used ? used[l] : S) * ds; ++i)
+            if (eps[l * S * ds + i] >= p) return false;
+    for (int mu = 0; mu < d; ++mu) {
+        uint64_t sum = 0;
+        for (int l = 0; l < n; ++l) sum = (sum + k[l * d + mu]) % P;
+        if (sum != 0) return false;
+    }
+    for (int l = 0; l < n; ++l) {
+        const uint32_t* kl = k + l * d;
+        uint64_t k2 = 0;
+        for (int mu = 0; mu < d; ++mu) {
+            const uint64_t t = static_cast<uint64_t>(kl[mu]) * kl[mu] % P;
+            k2 = (k2 + (msign<METRIC>(mu) > 0 ? t : P - t)) % P;
+        }
+        if (k2 != 0) return false;
+        for (int s = 0; s < (used ? used[l] : S); ++s) {
+            const uint32_t* es = eps + (l * S + s) * ds;
+            uint64_t ek = 0;
+            for (int mu = 0; mu < d; ++mu) {
+                const uint64_t t = static_cast<uint64_t>(es[mu]) * kl[mu] % P;
+                ek = (ek + (msign<METRIC>(mu) > 0 ? t : P - t)) % P;
+            }
+            if (ek != 0) return false;
+        }
+    }
+    return true;
+}
+
+// complex FP64 (KC = double2: complex momenta, double: real momenta)
+template <int METRIC, class KC>
+__device__ inline bool c64_preconditions(const KC* k, const double2* eps, int n, int d, int ds, int S,
+                                         const int* used) {
+    auto re = [](const KC& x) -> double { if constexpr (sizeof(KC) == 16) return x.x; else return x; };
+    auto im = [](const KC& x) -> double { if constexpr (sizeof(KC) == 16) return x.y; else return 0.0; };
+    double kmax = 0.0;
+    for (int l = 0; l < n; ++l) {
+        double nk = 0.0;
+        for (int mu = 0; mu < d; ++mu) nk += re(k[l * d + mu]) * re(k[l * d + mu]) + im(k[l * d + mu]) * im(k[l * d + mu]);
+        kmax = fmax(kmax, sqrt(nk));
+    }
+    for (int mu = 0; mu < d; ++mu) {
+        double sr = 0.0, si = 0.0;
+        for (int l = 0; l < n; ++l) { sr += re(k[l * d + mu]); si += im(k[l * d + mu]); }
+        if (sqrt(sr * sr + si * si) > kPreconditionTol * kmax) return false;
+    }
+    for (int l = 0; l < n; ++l) {
+        const KC* kl = k + l * d;
+        double k2r = 0.0, k2i = 0.0;
+        for (int mu = 0; mu < d; ++mu) {
+            const double g = msign<METRIC>(mu);
+            k2r += g * (re(kl[mu]) * re(kl[mu]) - im(kl[mu]) * im(kl[mu]));
+            k2i += g * 2.0 * re(kl[mu]) * im(kl[mu]);
+        }
+        if (sqrt(k2r * k2r + k2i * k2i) > kPreconditionTol * kmax * kmax) return false;
+        for (int s = 0; s < (used ? used[l] : S); ++s) {
+            const double2* es = eps + (l * S + s) * ds;
+            double er = 0.0, ei = 0.0, ne = 0.0;
+            for (int mu = 0; mu < ds; ++mu) ne += es[mu].x * es[mu].x + es[mu].y * es[mu].y;
+            for (int mu = 0; mu < d; ++mu) {
+                const double g = msign<METRIC>(mu);
+                er += g * (es[mu].x * re(kl[mu]) - es[mu].y * im(kl[mu]));
+                ei += g * (es[mu].x * im(kl[mu]) + es[mu].y * re(kl[mu]));
+            }
+            if (sqrt(er * er + ei * ei) > kPreconditionTol * sqrt(ne) * kmax) return false;
+        }
+    }
+    return true;
+}
+
+// The preconditions for point e of a batch in the boundary layouts
+// (momenta [E][n][d], polarisations [E][n][S][D_s]); used[l] (or all S when
+// used is null) is the number of leg l's state slots that are evaluated.
+template <class F, int METRIC>
+__device__ inline bool inputs_meet_preconditions(const F& f, const void* k, const void* eps, int64_t e, int n,
+                                                 int d, int ds, int S, const int* used = nullptr) {
+    using kio_t = typename F::kio_t;
+    using io_t = typename F::io_t;
+    const kio_t* kp = static_cast<const kio_t*>(k) + e * n * d;
+    const io_t* ep = static_cast<const io_t*>(eps) + e * n * S * ds;
+    if constexpr (F::kIsFp) return fp_preconditions<METRIC>(f.p, kp, ep, n, d, ds, S, used);
+    else return c64_preconditions<METRIC>(kp, ep, n, d, ds, S, used);
+}
+
 // Table geometry for N = n - 1 recursion legs (host and device), in table
 // elements per thread.  Region starts are rounded up to 4 elements so that
 // vector accesses stay aligned.
@@ -253,6 +355,12 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
         e = u / a.H;
         h = static_cast<int>(u - e * a.H);
     }
+#ifdef BG_CHECKED
+    // every item of a point checks all of its states, so all items agree
+    const bool violated = !inputs_meet_preconditions<F, METRIC>(f, a.k, a.eps, e, NLEG, a.d_in, a.ds_in, a.S);
+#else
+    constexpr bool violated = false;
+#endif
     // a1: momenta -> prefix sums K_0 = 0, K_{l+1} = K_l + k_l (leg n unused:
     // P_{1,n-1} = -k_n never enters); polarisations -> currents of length 1.
     {
@@ -506,8 +614,8 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
             range(std::integral_constant<int, D>{}, std::integral_constant<int, DS>{}, m, i);
         }
     }
-    st_once(out + u, singular ? f.zero_io() : result);
-    if (a.status != nullptr && h == 0) a.status[e] = singular ? 1 : 0;
+    st_once(out + u, (singular || violated) ? f.zero_io() : result);
+    if (a.status != nullptr && h == 0) a.status[e] = violated ? 2 : singular ? 1 : 0;
 }
 
 // bg_point with the whole table at `tab` (one region, as in the batch kernel).

@@ -16,7 +16,9 @@
 // object, not device memory): its device address is obtained once per device
 // with cudaGetSymbolAddress, with that device current, during the first call
 // on that device.  That first call should therefore come before any stream
-// capture begins.  All calls share the array and it keeps the previous call's
+// capture begins.  The cached address belongs to the device's primary
+// context: after cudaDeviceReset it is stale, and the library must not be
+// used again in that process.  All calls share the array and it keeps the previous call's
 // contents; the kernel writes every table entry before reading it, so nothing
 // needs clearing, but calls whose kernels overlap on the GPU (different
 // streams, or without ordering between them) race on the array.

@@ -207,7 +207,15 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
             if (l < N) tp[at(g.cur[1][l] + t * DS + mu, 1, 11)] = v;
             else tp[at(g.off_el + t * DS + mu, 1, 12)] = v;
         }
-        for (int p = lane; p < np; p += 32) *flag(p) = 0;
+        for (int p = lane; p < np; p += 32) {
+            int fl = 0;
+#ifdef BG_CHECKED
+            // bit 1: the point's inputs break a precondition of the boundary
+            if (!inputs_meet_preconditions<F, METRIC>(f, a.k, a.eps, e0 + p, n, a.d_in, a.ds_in, S, g.radix))
+                fl = 2;
+#endif
+            *flag(p) = fl;
+        }
     }
     __threadfence_block();
     __syncwarp();
@@ -226,7 +234,7 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) Pv[mu] = f.ksub(Kb[mu], Ka[mu]);
         const T xv = f.inv_input(f.template kkdot<D, METRIC>(Pv, Pv));
-        if (f.is_zero(xv)) *flag(p) = 1;
+        if (f.is_zero(xv)) *flag(p) |= 1;    // bit 0: singular propagator
         tab[p * W + at(g.off_inv + r, 1, 13)] = f.inv_store(f.inv_scalar(xv));
     }
     __threadfence_block();
@@ -347,7 +355,7 @@ __device__ __forceinline__ void states_group(const F& f, const StatesArgs& a, co
         __syncwarp();
     }
     if (a.status != nullptr)
-        for (int p = lane; p < np; p += 32) a.status[e0 + p] = *flag(p) ? 1 : 0;
+        for (int p = lane; p < np; p += 32) a.status[e0 + p] = (*flag(p) & 2) ? 2 : (*flag(p) ? 1 : 0);
     __syncwarp();
 }
 

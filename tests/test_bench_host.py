@@ -1,6 +1,7 @@
 """Host logic of bench.py that needs no GPU: the reference arm (the oracle
 timed on the host cores) prints the contract's JSON line, and the algorithmic
-work per amplitude behind the roofline is the oracle's counted tally."""
+work per amplitude behind the rooflines (field multiplications over F_p, FP64
+operations over complex FP64) is the oracle's counted tally."""
 
 import json
 import os
@@ -36,3 +37,11 @@ def test_literal_tally_is_the_oracle_count(n, d, Ds):
     import bench
     from oracle.bg_oracle import op_tally
     assert bench.literal_tally(n, d, Ds)[0] == op_tally(n, d, Ds).mul
+
+
+@pytest.mark.parametrize("n,d,Ds", [(4, 4, 4), (5, 4, 4), (8, 6, 6), (8, 4, 8), (10, 6, 6), (12, 8, 8)])
+@pytest.mark.parametrize("real_k", [True, False])
+def test_literal_flops_are_the_oracle_count(n, d, Ds, real_k):
+    import bench
+    from oracle.bg_oracle import flop_tally
+    assert bench.literal_flops(n, d, Ds, real_k) == flop_tally(n, d, Ds, real_momenta=real_k)

@@ -42,7 +42,7 @@ def test_c64_real_within_tolerance(n, d, Ds, metric):
     out, st, plan = run_c64r(k, eps, metric)
     assert "field=c64_real" in plan.describe()
     assert np.array_equal(st, rst)
-    check_c64(out, k, eps, metric, max_widened=0.05)
+    check_c64(out, k, eps, metric, max_widened=0.02)   # measured: at most 2 of 157 points
 
 
 def test_c64_real_metric_workload_strict():
@@ -67,7 +67,7 @@ def test_c64_real_singular_status():
     assert st[77] == 1 and out[77] == 0 and rst[77] == 1
     assert np.array_equal(st, rst)
     keep = np.arange(len(k)) != 77
-    check_c64(out[keep], k[keep], eps[keep], 0, max_widened=0.05)
+    check_c64(out[keep], k[keep], eps[keep], 0, max_widened=0.01)   # measured: none
 
 
 def test_c64_real_state_assignment_table():
@@ -82,7 +82,7 @@ def test_c64_real_state_assignment_table():
     his = np.stack([C.amp_c64dd(k, e_h, 1)[0] for e_h in e_hs], axis=1)
     spt = np.abs(his).max(axis=1)
     for h in range(H):
-        check_c64(out[:, h], k, e_hs[h], 1, spt=spt, max_widened=0.05)
+        check_c64(out[:, h], k, e_hs[h], 1, spt=spt, max_widened=0.0)   # measured: none
 
 
 def test_c64_real_other_entry_points_match_eval():

@@ -102,7 +102,7 @@ def test_product_plan_complex(field):
     his = np.stack([C.amp_c64dd(k, np.ascontiguousarray(e), 0)[0] for e in e_h], axis=1)
     spt = np.abs(his).max(axis=1)
     for h in range(len(table)):
-        check_c64(out[:, h], k, np.ascontiguousarray(e_h[h]), 0, spt=spt, max_widened=0.05)
+        check_c64(out[:, h], k, np.ascontiguousarray(e_h[h]), 0, spt=spt, max_widened=0.0)   # measured: none
 
 
 @pytest.mark.parametrize("k_ring,S", [(1, 3), (2, 4), (4, 4), (5, 2), (3, 8)])

@@ -87,7 +87,7 @@ def test_c64_mixed_within_tolerance(field, n, d, Ds, metric):
     out, st = _run(_plan(n, d, Ds, f, 0, metric, mask), kd, ed)
     out_plain, st_plain = _run(bg.Plan(n, d, Ds, f, 0, metric), kd, ed)
     assert np.array_equal(st, st_plain)
-    check_c64(out, k, eps, metric, max_widened=0.05)
+    check_c64(out, k, eps, metric, max_widened=0.02)   # measured: at most 1 of 157 points
     # separately compiled kernels: the same values up to FP64 rounding (FMA
     # contraction may differ), measured below 1e-11 relative
     rel = np.abs(out - out_plain) / np.abs(out_plain)

@@ -158,7 +158,7 @@ def test_c64_within_tolerance(n, d, Ds, metric):
     _, rst = C.amp_c64(k, eps, metric)
     out, st, plan = run_c64(k, eps, metric)
     assert np.array_equal(st, rst)
-    check_c64(out, k, eps, metric, max_widened=0.05)
+    check_c64(out, k, eps, metric, max_widened=0.02)   # measured: at most 2 of 157 points
 
 
 def test_c64_metric_workload_strict():
@@ -227,7 +227,7 @@ def test_state_assignment_table(field):
         his = np.stack([C.amp_c64dd(k, e_h, 0)[0] for e_h in refs], axis=1)
         spt = np.abs(his).max(axis=1)
         for h in range(H):
-            check_c64(out[:, h], k, refs[h], 0, spt=spt, max_widened=0.05)
+            check_c64(out[:, h], k, refs[h], 0, spt=spt, max_widened=0.0)   # measured: none
 
 
 def test_ward_identity_on_gpu_full_batch():

@@ -113,7 +113,7 @@ def test_states_c64_within_tolerance(field, n, d, Ds, metric, S, E):
     his = np.stack([C.amp_c64dd(k, np.ascontiguousarray(e), metric)[0] for e in e_h], axis=1)
     spt = np.abs(his).max(axis=1)
     for h in range(len(assign)):
-        check_c64(out[:, h], k, np.ascontiguousarray(e_h[h]), metric, spt=spt, max_widened=0.05)
+        check_c64(out[:, h], k, np.ascontiguousarray(e_h[h]), metric, spt=spt, max_widened=0.0)   # measured: none
     assert not st.any()
 
 

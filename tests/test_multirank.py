@@ -57,3 +57,34 @@ def test_two_rank_replicas_gloo(tmp_path):
         k, e = G.fp_batch(bench.rank_seed(1000, r), 64, 6, 6, 6, G.P_DEFAULT, 0, workers=1)
         ref, _ = C.amp_fp(k, e, G.P_DEFAULT, 0)
         assert np.array_equal(res[r], ref.astype(np.int64))
+
+
+def test_bench_launches_two_ranks_itself():
+    """`bench.py --gpus 2` started as a plain process re-runs itself as two
+    ranks under torch.distributed.run (the launch the scaling run uses); the
+    launch check (gloo, no GPU work) reports n_gpus = 2, each rank's own
+    seeded batch and the whole-job value over the slowest rank's time."""
+    import json
+    import subprocess
+    import sys
+    import hashlib
+    import bench
+    from paper_2502_07060_gb300 import inputs as G
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--workload",
+                        "launchcheck", "--log2-points", "8"], capture_output=True, text=True, timeout=600,
+                       cwd=root, env=env)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1                            # rank 0 alone prints
+    line = json.loads(lines[0])
+    assert line["n_gpus"] == 2 and line["scaling"] == "weak"
+    assert line["value"] == pytest.approx(bench.job_value(256, 2, line["ms_per_step"]))
+    ranks = sorted(line["ranks"], key=lambda x: x["rank"])
+    assert [x["rank"] for x in ranks] == [0, 1]
+    for x in ranks:
+        assert x["seed"] == bench.rank_seed(1000, x["rank"]) and x["points"] == 256
+        k, e = G.fp_batch(x["seed"], 256, bench.N_LEG, bench.D, bench.DS, bench.P, 0, workers=1)
+        assert x["digest"] == hashlib.sha256(k.tobytes() + e.tobytes()).hexdigest()[:16]
+    assert ranks[0]["digest"] != ranks[1]["digest"]

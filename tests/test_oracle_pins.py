@@ -86,6 +86,26 @@ def test_op_tally_matches_combinatorics():
         assert t.inv == math.comb(n, 2) - n
 
 
+def test_flop_tally_agrees_with_the_operation_tally():
+    """With complex momenta every product costs 6 FP64 operations and every sum
+    2, except the sums that start from zero (one per dot product, one per
+    component of each range's bracket, one per component of each range-momentum
+    row), which cost nothing; a complex reciprocal costs 6.  So the FLOP
+    tally, counted by a different mechanism (stand-in numbers instead of the
+    operation counters), must equal 6 mul + 2 (add - Z) + 6 inv."""
+    for n, d, Ds in [(4, 4, 4), (5, 4, 6), (8, 6, 6), (9, 5, 7), (12, 8, 8)]:
+        t = O.op_tally(n, d, Ds)
+        N = n - 1
+        ranges = N * (N - 1) // 2                      # lengths 2..N
+        internal = ranges - 1
+        s3, s4 = math.comb(n, 3), math.comb(n, 4)
+        dots = 3 * s3 + 3 * s4 + internal + 1
+        Z = dots + Ds * ranges + d * N
+        assert O.flop_tally(n, d, Ds, real_momenta=False) == 6 * t.mul + 2 * (t.add - Z) + 6 * t.inv
+        # real momenta: strictly less work, and no more than the complex count
+        assert O.flop_tally(n, d, Ds, real_momenta=True) < O.flop_tally(n, d, Ds, real_momenta=False)
+
+
 # ----------------------------------------------------------- gauge invariance
 
 @pytest.mark.parametrize("n,d,Ds,metric,p", [

@@ -46,6 +46,26 @@ def test_noalloc_matches_bg_eval_on_two_calls(field, n, d, E):
             assert (np.abs(a - b) <= 1e-10 * np.abs(b)).all()
 
 
+def test_noalloc_with_an_assignment_table_matches_bg_eval():
+    """Several state assignments per point (H = 3 rows of an explicit table,
+    two states per leg): the table and H reach the kernel the same way as in
+    bg_eval; two calls in a row, bit-exact over F_p."""
+    import torch
+    from paper_2502_07060_gb300 import bg
+    n, d, S = 6, 4, 2
+    table = np.array([[0] * n, [1] * n, [0, 1, 1, 0, 1, 0]], dtype=np.uint8)
+    plan = bg.Plan(n, d, d, bg.FIELD_FP, G.P_DEFAULT, bg.MOSTLY_MINUS, S, table)
+    for seed in (21, 22):
+        k, e = G.fp_batch(seed, 2000, n, d, d, S=S, workers=1)
+        kd = torch.from_numpy(k.view(np.int32)).cuda()
+        ed = torch.from_numpy(e.view(np.int32)).cuda()
+        out, st = plan.eval_noalloc(kd, ed)
+        ref, rst = plan.eval(kd, ed)
+        torch.cuda.synchronize()
+        assert out.shape == (2000, 3)
+        assert torch.equal(st, rst) and torch.equal(out, ref)
+
+
 def test_noalloc_rejects_sizes_beyond_the_maximum():
     from paper_2502_07060_gb300 import bg
     import torch
