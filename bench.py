@@ -626,20 +626,25 @@ def fourdim_workload(args, device):
 
 
 def serve_workload(args, device):
-    """Poisson arrivals (mean rate --serve-rate per second) of requests with
-    log-uniform sizes 1..65536 points, n uniform in 4..12, d = D_s uniform in
-    {4, 6, 8}, field uniform; latency = completion - arrival.  Served by
-    (a) bg_server (continuous admission, 8 stream slots) with host buffers
-    staged through its arena, (c) the same server with the momenta and states
-    resident on the device (a pool uploaded once; results still returned to
-    host memory), and (b) plain per-request evaluation, one request at a time
-    (copy in, bg_eval, copy out, synchronise), in arrival order."""
+    """Poisson arrivals (mean rate per second from --serve-rates) of requests
+    with log-uniform sizes 1..65536 points, n uniform in 4..12, d = D_s
+    uniform in {4, 6, 8}, field uniform; latency = completion - arrival.
+    Arms, each on the same request sequence:
+      server           bg_server (continuous admission, 8 stream slots) with
+                       page-locked host buffers (used in place or staged);
+      server_resident  the same server with the momenta and states resident
+                       on the device (a pool uploaded once; results still
+                       returned to host memory), first rate only;
+      plain_1          plain per-request evaluation by one thread in arrival
+                       order (copy in, bg_eval, copy out, synchronise);
+      plain_8          the same by 8 threads, each on its own stream, without
+                       admission control (a request waits only for a free
+                       thread)."""
     import queue
     import threading
 
     import torch
     from paper_2502_07060_gb300 import bg
-    rng = np.random.default_rng(args.serve_seed)
     configs = [(f, n, d) for f in ("fp", "c64") for n in range(4, 13) for d in (4, 6, 8)]
     pool_pts = 1 << 16
     pools, plans = {}, {}
@@ -653,30 +658,33 @@ def serve_workload(args, device):
             k, e = G.c64_batch(7000 + i, pool_pts, n, d, d, 0)
             pools[(f, n, d)] = (torch.from_numpy(k).pin_memory(), torch.from_numpy(e).pin_memory())
             plans[(f, n, d)] = bg.Plan(n, d, d, bg.FIELD_C64, 0)
-    n_req = int(args.serve_rate * args.serve_seconds)
-    gaps = rng.exponential(1.0 / args.serve_rate, n_req)
-    arrivals = np.cumsum(gaps)
-    reqs = []
-    placement = []
-    for i in range(n_req):
-        cfg = configs[rng.integers(len(configs))]
-        E = int(np.clip(np.exp(rng.uniform(0, np.log(65536))), 1, 65536))
-        off = int(rng.integers(0, pool_pts - E + 1))
-        hk, he = pools[cfg]
-        out = torch.empty(E, dtype=hk.dtype).pin_memory()
-        st = torch.empty(E, dtype=torch.uint8).pin_memory()
-        reqs.append((plans[cfg], hk[off:off + E], he[off:off + E], out, st, E))
-        placement.append((cfg, off))
-    total_pts = sum(r[5] for r in reqs)
 
-    def summarise(lat, t0, t_end):
+    def requests(rate, seed):
+        rng = np.random.default_rng(seed)
+        n_req = int(rate * args.serve_seconds)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        reqs, placement = [], []
+        for _ in range(n_req):
+            cfg = configs[rng.integers(len(configs))]
+            E = int(np.clip(np.exp(rng.uniform(0, np.log(65536))), 1, 65536))
+            off = int(rng.integers(0, pool_pts - E + 1))
+            hk, he = pools[cfg]
+            out = torch.empty(E, dtype=hk.dtype).pin_memory()
+            st = torch.empty(E, dtype=torch.uint8).pin_memory()
+            reqs.append((plans[cfg], hk[off:off + E], he[off:off + E], out, st, E))
+            placement.append((cfg, off))
+        return arrivals, reqs, placement
+
+    def summarise(lat, t0, t_end, total_pts):
         lat = np.array(lat) * 1e3
+        n_req = len(lat)
         return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
                 "throughput_points_per_s": total_pts / (t_end - t0),
                 "throughput_requests_per_s": n_req / (t_end - t0)}
 
-    def run_server(req_list):
+    def run_server(arrivals, req_list):
+        n_req = len(req_list)
         srv = bg.Server(8 << 30, max_inflight=8)
         done_at = [0.0] * n_req
         tickets = queue.Queue()
@@ -708,60 +716,70 @@ def serve_workload(args, device):
             tickets.put(None)
         for w in waiters:
             w.join()
-        res = summarise([done_at[i] - (t0 + arrivals[i]) for i in range(n_req)], t0, max(done_at))
+        res = summarise([done_at[i] - (t0 + arrivals[i]) for i in range(n_req)], t0, max(done_at),
+                        sum(r[5] for r in req_list))
         res["peak_arena_bytes"] = srv.stats()["peak_bytes"]
         res["failed_requests"] = len(failed)
         srv.close()
         return res
 
-    # (a) server, host buffers staged through its arena
-    served = run_server(reqs)
-    # (c) server, momenta and states resident on the device (a pool uploaded
-    # once), results returned to host memory
-    dpools = {cfg: (hk.to(device), he.to(device)) for cfg, (hk, he) in pools.items()}
-    torch.cuda.synchronize(device)
-    resident = [(r[0], dpools[cfg][0][off:off + r[5]], dpools[cfg][1][off:off + r[5]], r[3], r[4], r[5])
-                for r, (cfg, off) in zip(reqs, placement)]
-    served_resident = run_server(resident)
-    del resident, dpools
-    torch.cuda.empty_cache()
+    def run_plain(arrivals, req_list, threads):
+        n_req = len(req_list)
+        work = queue.Queue()
+        done_at = [0.0] * n_req
 
-    # (b) plain per-request launches, one at a time in arrival order
-    stream = torch.cuda.current_stream(device)
-    work = queue.Queue()
-    done_plain = [0.0] * n_req
+        def worker():
+            stream = torch.cuda.Stream(device)
+            while True:
+                i = work.get()
+                if i is None:
+                    return
+                plan, hk, he, out, st, E = req_list[i]
+                with torch.cuda.stream(stream):
+                    dk = hk.to(device, non_blocking=True)
+                    de = he.to(device, non_blocking=True)
+                    o, s_ = plan.eval(dk, de, stream=stream)
+                    out.copy_(o, non_blocking=True)
+                    st.copy_(s_, non_blocking=True)
+                stream.synchronize()
+                done_at[i] = time.perf_counter()
 
-    def worker():
-        while True:
-            item = work.get()
-            if item is None:
-                return
-            i = item
-            plan, hk, he, out, st, E = reqs[i]
-            dk = hk.to(device, non_blocking=True)
-            de = he.to(device, non_blocking=True)
-            o, s_ = plan.eval(dk, de, stream=stream)
-            out.copy_(o, non_blocking=True)
-            st.copy_(s_, non_blocking=True)
+        ws = [threading.Thread(target=worker) for _ in range(threads)]
+        for w in ws:
+            w.start()
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            delay = t0 + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            work.put(i)
+        for _ in ws:
+            work.put(None)
+        for w in ws:
+            w.join()
+        return summarise([done_at[i] - (t0 + arrivals[i]) for i in range(n_req)], t0, max(done_at),
+                         sum(r[5] for r in req_list))
+
+    rates = [float(x) for x in args.serve_rates.split(",")]
+    rows = []
+    for ri, rate in enumerate(rates):
+        arrivals, reqs, placement = requests(rate, args.serve_seed + ri)
+        row = {"rate_per_s": rate, "requests": len(reqs), "points": sum(r[5] for r in reqs),
+               "server": run_server(arrivals, reqs)}
+        if ri == 0:
+            dpools = {cfg: (hk.to(device), he.to(device)) for cfg, (hk, he) in pools.items()}
             torch.cuda.synchronize(device)
-            done_plain[i] = time.perf_counter()
-
-    wt = threading.Thread(target=worker)
-    wt.start()
-    t0 = time.perf_counter()
-    for i in range(n_req):
-        delay = t0 + arrivals[i] - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        work.put(i)
-    work.put(None)
-    wt.join()
-    plain = summarise([done_plain[i] - (t0 + arrivals[i]) for i in range(n_req)], t0, max(done_plain))
-    return {"workload": f"Poisson arrivals at {args.serve_rate}/s for {args.serve_seconds} s, "
-                        f"{n_req} requests (seed {args.serve_seed}), sizes log-uniform 1..65536 "
-                        f"(total {total_pts} points), "
-                        "n uniform 4..12, d = D_s uniform {4, 6, 8}, F_p or C64",
-            "server": served, "server_resident_inputs": served_resident, "plain_per_request": plain}
+            resident = [(r[0], dpools[cfg][0][off:off + r[5]], dpools[cfg][1][off:off + r[5]], r[3], r[4], r[5])
+                        for r, (cfg, off) in zip(reqs, placement)]
+            row["server_resident"] = run_server(arrivals, resident)
+            del resident, dpools
+            torch.cuda.empty_cache()
+            row["plain_1"] = run_plain(arrivals, reqs, 1)
+        row["plain_8"] = run_plain(arrivals, reqs, 8)
+        rows.append(row)
+    return {"workload": f"Poisson arrivals for {args.serve_seconds} s per rate (seed {args.serve_seed}), "
+                        "sizes log-uniform 1..65536, n uniform 4..12, d = D_s uniform {4, 6, 8}, F_p or C64",
+            "rows": rows}
 
 
 def main():
@@ -789,8 +807,9 @@ def main():
                          "the multi-rank launch on CPU (gloo), no GPU work")
     ap.add_argument("--log2-points-helicity", type=int, default=20,
                     help="points per n of the helicity workload")
-    ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-rates", default="2000,1000",
+                    help="comma list of mean request rates per second; the first is the metric's")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-seed", type=int, default=2026,
                     help="seed of the arrival times, sizes, configurations and pool offsets")
     args = ap.parse_args()
@@ -965,17 +984,24 @@ def main():
         # server against plain per-request launches (the serve workload)
         try:
             sv = serve_workload(args, device)
+            r0 = sv["rows"][0]
             line["serving"] = {
-                "workload": sv["workload"], "unit": "ms",
-                "p50_ms": sv["server"]["p50_ms"], "p99_ms": sv["server"]["p99_ms"],
-                "throughput_points_per_s": sv["server"]["throughput_points_per_s"],
-                "failed_requests": sv["server"]["failed_requests"] + sv["server_resident_inputs"]["failed_requests"],
-                "resident_inputs_p50_ms": sv["server_resident_inputs"]["p50_ms"],
-                "resident_inputs_p99_ms": sv["server_resident_inputs"]["p99_ms"],
-                "plain_per_request_p50_ms": sv["plain_per_request"]["p50_ms"],
-                "plain_per_request_p99_ms": sv["plain_per_request"]["p99_ms"],
-                "plain_per_request_throughput_points_per_s":
-                    sv["plain_per_request"]["throughput_points_per_s"]}
+                "workload": sv["workload"], "unit": "ms", "rate_per_s": r0["rate_per_s"],
+                "p50_ms": r0["server"]["p50_ms"], "p99_ms": r0["server"]["p99_ms"],
+                "throughput_points_per_s": r0["server"]["throughput_points_per_s"],
+                "failed_requests": sum(r["server"]["failed_requests"] for r in sv["rows"])
+                + r0["server_resident"]["failed_requests"],
+                "resident_inputs_p50_ms": r0["server_resident"]["p50_ms"],
+                "resident_inputs_p99_ms": r0["server_resident"]["p99_ms"],
+                "plain_per_request_p50_ms": r0["plain_1"]["p50_ms"],
+                "plain_per_request_p99_ms": r0["plain_1"]["p99_ms"],
+                "plain_per_request_throughput_points_per_s": r0["plain_1"]["throughput_points_per_s"],
+                "plain_8_streams_p50_ms": r0["plain_8"]["p50_ms"],
+                "plain_8_streams_p99_ms": r0["plain_8"]["p99_ms"],
+                "other_rates": [{"rate_per_s": r["rate_per_s"], "server_p50_ms": r["server"]["p50_ms"],
+                                 "server_p99_ms": r["server"]["p99_ms"],
+                                 "plain_8_streams_p50_ms": r["plain_8"]["p50_ms"],
+                                 "plain_8_streams_p99_ms": r["plain_8"]["p99_ms"]} for r in sv["rows"][1:]]}
         except Exception as exc:                    # noqa: BLE001 -- keep the throughput line
             line["serving"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:

@@ -157,15 +157,25 @@ bg_status bg_plan_destroy(bg_plan* plan);
 
 /*
  * bg_workspace_size -- device workspace bytes bg_eval needs for E points
- * (0 when the plan's kernel keeps its current table in shared memory).  The
- * size is at most the value for E = INT64_MAX and is independent of E once E
- * exceeds the number of resident threads.
+ * (0 when the plan's kernel keeps its current table in shared memory, or when
+ * the batch is small enough for the lane-group kernel described at bg_eval).
+ * The size is at most the value for E = INT64_MAX and is independent of E
+ * once E exceeds the number of resident threads.
  */
 bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes);
 
 /*
  * bg_eval -- evaluate E points on `stream` (asynchronous, one kernel launch;
- * the results are valid once the stream reaches the call).
+ * the results are valid once the stream reaches the call).  The data-parallel
+ * evaluation of Sec. 3: one independent recursion (Sec. 2.2) per point and
+ * state assignment.  Large batches run one work item (point x assignment)
+ * per thread; small ones -- at most a quarter of that kernel's resident
+ * threads, see bg_plan_describe's lanes_max_items -- run each item on a
+ * group of 4 or 8 lanes, one vector component per lane, which shortens the
+ * call when most of the GPU would otherwise idle (the flat part of the
+ * time-against-points curve of Sec. 3.2).  Both give the same F_p residues;
+ * complex results agree to rounding.  The environment variable BG_LANES=0
+ * (never) or 1 (always) read at plan creation overrides the choice.
  *
  *   E          number of phase-space points, E >= 0 (E == 0: no launch)
  *   momenta    device [E][n][d]: uint32 residues (FP), double2 (C64) or
@@ -320,7 +330,12 @@ bg_status bg_batch_destroy(bg_batch* batch);
  * residency caps of the two kernels) on this batch, `reps` launches each on
  * `stream`, and return the fastest in *best (and its time per launch in
  * *best_ms if non-NULL).  Needs bg_batch_workspace_size(groups, n, NULL)
- * bytes of workspace.  Synchronises the stream. */
+ * bytes of workspace.  Synchronises the stream.  When the environment
+ * variable BG_AUTOTUNE_CACHE names a file, a result stored there for the same
+ * device, library version and group mix (each group's configuration and its
+ * size rounded up to a power of two) is returned without timing, and a newly
+ * timed result is appended to the file.  Setting BG_LOG (to anything but 0)
+ * logs plan choices and autotune results to stderr. */
 bg_status bg_batch_autotune(const bg_group* groups, int n_groups, void* workspace,
                             size_t workspace_bytes, int reps, cudaStream_t stream,
                             bg_batch_config* best, double* best_ms);
@@ -362,7 +377,12 @@ bg_status bg_serve_submit(bg_server* srv, const bg_plan* plan, int64_t E, const 
 
 /* bg_serve_wait -- block until the ticket's results are in its host buffers
  * (BG_OK, the ticket is then retired), or until timeout_ms elapsed
- * (BG_ERR_TIMEOUT, the ticket stays valid); timeout_ms < 0 waits forever. */
+ * (BG_ERR_TIMEOUT, the ticket stays valid); timeout_ms < 0 waits forever.
+ * BG_ERR_CUDA when the request's copies or kernel failed, including an
+ * asynchronous error raised on the device after they were enqueued.  Several
+ * threads may wait on the same ticket at once: each returns the request's
+ * result; a wait that starts after the ticket was retired returns
+ * BG_ERR_INVALID_ARG (unknown ticket). */
 bg_status bg_serve_wait(bg_server* srv, uint64_t ticket, int64_t timeout_ms);
 
 /* bg_serve_stats -- counters (any pointer may be NULL). */

@@ -22,6 +22,9 @@ BG_REGC(c64, 8, 8)
 BG_REGC(c64r, 4, 4) BG_REGC(c64r, 4, 6) BG_REGC(c64r, 4, 8) BG_REGC(c64r, 6, 6) BG_REGC(c64r, 6, 8)
 BG_REGC(c64r, 8, 8)
 #undef BG_REGC
+void bg_register_lanes_fp(std::vector<bgk::LanesEntry>&);
+void bg_register_lanes_c64(std::vector<bgk::LanesEntry>&);
+void bg_register_lanes_c64r(std::vector<bgk::LanesEntry>&);
 #define BG_REGS(TAG, D) void bg_register_states_##TAG##_##D(std::vector<bgk::StatesEntry>&);
 BG_REGS(fp, 4) BG_REGS(fp, 6) BG_REGS(fp, 8) BG_REGS(c64, 4) BG_REGS(c64, 6) BG_REGS(c64, 8)
 BG_REGS(c64r, 4) BG_REGS(c64r, 6) BG_REGS(c64r, 8)
@@ -80,6 +83,20 @@ bg_status fail(bg_status s, const char* fmt, ...) {
     return s;
 }
 
+void log(const char* fmt, ...) {
+    static const bool on = [] {
+        const char* v = getenv("BG_LOG");
+        return v && *v && strcmp(v, "0") != 0;
+    }();
+    if (!on) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    fprintf(stderr, "bg: %s\n", buf);
+}
+
 const std::vector<bgk::KernelEntry>& registry() {
     static std::vector<bgk::KernelEntry> v;
     static std::once_flag once;
@@ -102,6 +119,17 @@ const std::vector<bgk::StatesEntry>& states_registry() {
         bg_register_states_fp_4(v); bg_register_states_fp_6(v); bg_register_states_fp_8(v);
         bg_register_states_c64_4(v); bg_register_states_c64_6(v); bg_register_states_c64_8(v);
         bg_register_states_c64r_4(v); bg_register_states_c64r_6(v); bg_register_states_c64r_8(v);
+    });
+    return v;
+}
+
+const std::vector<bgk::LanesEntry>& lanes_registry() {
+    static std::vector<bgk::LanesEntry> v;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        bg_register_lanes_fp(v);
+        bg_register_lanes_c64(v);
+        bg_register_lanes_c64r(v);
     });
     return v;
 }
@@ -277,6 +305,40 @@ bg_status setup_states(bg_plan* pl, const int* radix, const char* tenv) {
         return fail(BG_ERR_UNSUPPORTED, "all-assignment kernel cannot be resident (%s)", cudaGetErrorString(err));
     }
     pl->blocks_per_sm = occ;
+    return BG_OK;
+}
+
+// The lane-group kernel of a plan with one recursion per work item, and the
+// batch sizes it takes.  A batch of E H work items on the compact kernel
+// runs one item per thread: while E H is far below the kernel's resident
+// threads most of the GPU idles and the call lasts as long as one thread's
+// whole recursion.  The lanes kernel spreads each item over L lanes.
+// BG_LANES=0 never uses it, BG_LANES=1 always (when the plan has one),
+// otherwise batches of at most a quarter of the compact kernel's resident
+// threads take it (the crossover measured on GB300 lies near there for
+// n = 4..12, both number types).
+bg_status setup_lanes(bg_plan* pl) {
+    const int L = round_dim(pl->Ds) <= 4 ? 4 : 8;
+    for (const auto& e : bgi::lanes_registry())
+        if (e.field == (int)pl->field && e.L == L && e.metric == (int)pl->metric) pl->lentry = &e;
+    if (!pl->lentry) return BG_OK;
+    const size_t smem = (size_t)bgk::LaneGeometry{pl->n - 1}.words() * pl->lentry->block * pl->lentry->elem_bytes;
+    int occ = 0;
+    if (smem > 227 * 1024 || bgi::ensure_smem_limit(pl->lentry->func, pl->device, smem) != BG_OK ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pl->lentry->func, pl->lentry->block, smem) !=
+            cudaSuccess ||
+        occ < 1) {
+        cudaGetLastError();
+        g_last_error.clear();
+        pl->lentry = nullptr;            // the compact kernel serves every size
+        return BG_OK;
+    }
+    pl->lanes_smem = smem;
+    pl->lanes_blocks_per_sm = occ;
+    const char* env = getenv("BG_LANES");
+    if (env && strcmp(env, "0") == 0) pl->lanes_max_items = 0;
+    else if (env && strcmp(env, "1") == 0) pl->lanes_max_items = INT64_MAX;
+    else pl->lanes_max_items = (int64_t)pl->blocks_per_sm * pl->sm_count * pl->entry->block / 4;
     return BG_OK;
 }
 
@@ -480,6 +542,7 @@ static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, 
             return st;
         }
     }
+    if (!all_states) setup_lanes(pl);
     if (n_assign > 1 && !all_states) {
         size_t bytes = pl->assign.size();
         if (bgi::fault(BG_FAULT_DEVICE_ALLOC) || cudaMalloc(&pl->d_assign, bytes) != cudaSuccess) {
@@ -495,6 +558,13 @@ static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, 
         }
     }
     *out = pl;
+    if (pl->all_states)
+        bgi::log("plan n=%d d=%d D_s=%d field=%d: all-assignment kernel, %s table, %d blocks/SM", n, d, D_s,
+                 (int)field, pl->states_global ? "global" : "shared", pl->blocks_per_sm);
+    else
+        bgi::log("plan n=%d d=%d D_s=%d field=%d: compact kernel D=%d D_s=%d, %s table, block %d, %d blocks/SM",
+                 n, d, D_s, (int)field, best->D, best->DS,
+                 best->split ? "split" : best->global_table ? "global" : "shared", best->block, pl->blocks_per_sm);
     return BG_OK;
 }
 
@@ -557,6 +627,7 @@ bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes) {
     }
     if (!plan->entry->global_table) return BG_OK;
     const int64_t items = E * plan->H;
+    if (plan->lentry && items <= plan->lanes_max_items) return BG_OK;     // lanes kernel: no workspace
     const int B = plan->entry->block;
     int64_t blocks = (items + B - 1) / B;
     if (blocks > resident_blocks(plan)) blocks = resident_blocks(plan);
@@ -582,11 +653,12 @@ bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
     int w = snprintf(buf, len,
                      "field=%s n=%d d=%d D_s=%d kernel=compact kernel_D=%d kernel_D_s=%d metric=%s "
                      "table=%s block=%d blocks_per_sm=%d smem=%zu words_per_thread=%d elem_bytes=%d "
-                     "four_dim_legs=0x%x",
+                     "four_dim_legs=0x%x lanes=%d lanes_max_items=%lld",
                      field_name(plan->field), plan->n, plan->d, plan->Ds, e->D, e->DS,
                      plan->metric == BG_METRIC_MOSTLY_MINUS ? "mostly_minus" : "alternating",
                      e->split ? "split" : e->global_table ? "global" : "shared", e->block, plan->blocks_per_sm,
-                     plan->smem_bytes, plan->words, e->elem_bytes, plan->four_d_legs);
+                     plan->smem_bytes, plan->words, e->elem_bytes, plan->four_d_legs,
+                     plan->lentry ? plan->lentry->L : 0, (long long)plan->lanes_max_items);
     if (w < 0 || (size_t)w >= len) return fail(BG_ERR_INVALID_ARG, "buffer too small");
     return BG_OK;
 }
@@ -653,6 +725,26 @@ bg_status eval_impl(const bg_plan* plan, int64_t E, const void* momenta, const v
     }
     if (bgi::fault(BG_FAULT_LAUNCH)) return fail(BG_ERR_CUDA, "launch failed: injected fault");
     const int64_t items = E * plan->H;
+    if (plan->lentry && items <= plan->lanes_max_items) {
+        // small batch: one item per group of L lanes
+        const bgk::LanesEntry* le = plan->lentry;
+        if (dev != plan->device && (st = bgi::ensure_smem_limit(le->func, dev, plan->lanes_smem)) != BG_OK) return st;
+        const int64_t ppb = le->block / le->L;
+        int64_t lblocks = (items + ppb - 1) / ppb;
+        const int64_t lcap = (int64_t)plan->lanes_blocks_per_sm * plan->sm_count;
+        if (lblocks > lcap) lblocks = lcap;
+        bgk::CompactArgs a;
+        a.E = E; a.H = plan->H; a.S = plan->S; a.n = plan->n;
+        a.d_in = plan->d; a.ds_in = plan->Ds;
+        a.k = momenta; a.eps = eps; a.out = out; a.status = status;
+        a.assign = plan->d_assign; a.ws = nullptr;
+        a.four_d_legs = 0;
+        a.violation = bgi::violation_word(dev);
+        le->launch(compact_params(plan), &a, dim3((unsigned)lblocks), plan->lanes_smem, stream);
+        cudaError_t lerr = cudaGetLastError();
+        if (lerr != cudaSuccess) return fail(BG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(lerr));
+        return BG_OK;
+    }
     int64_t blocks = (items + e->block - 1) / e->block;
     const int64_t cap = e->global_table ? resident_blocks(plan) : resident_blocks(plan) * 256;
     if (blocks > cap) blocks = cap;

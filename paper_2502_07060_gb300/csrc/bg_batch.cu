@@ -13,8 +13,10 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "bg_batch.cuh"
@@ -305,13 +307,99 @@ bg_status bg_batch_destroy(bg_batch* batch) {
     return BG_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Key of a batch's group mix for the autotune cache: the device, the library
+// version and, for every non-empty group in a canonical order, its
+// configuration and its size rounded up to a power of two (FNV-1a, 64 bit).
+std::string tune_key(const bg_group* groups, int n_groups, int dev) {
+    std::vector<std::string> parts;
+    for (int g = 0; g < n_groups; ++g) {
+        const bg_plan* pl = groups[g].plan;
+        if (!pl || groups[g].E <= 0) continue;
+        int lg = 0;
+        while ((int64_t(1) << lg) < groups[g].E) ++lg;
+        char buf[128];
+        snprintf(buf, sizeof buf, "%d:%d:%d:%d:%d:%u:%d:%d:%x:%d", (int)pl->field, pl->n, pl->d, pl->Ds,
+                 (int)pl->metric, pl->p, pl->S, pl->H, pl->four_d_legs, lg);
+        parts.push_back(buf);
+    }
+    std::sort(parts.begin(), parts.end());
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    std::string all = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "/v" +
+                      std::to_string(BG_VERSION);
+    for (const auto& x : parts) all += "|" + x;
+    uint64_t h = 1469598103934665603ull;
+    for (unsigned char c : all) {
+        h ^= c;
+        h *= 1099511628211ull;
+    }
+    char hex[17];
+    snprintf(hex, sizeof hex, "%016llx", (unsigned long long)h);
+    return hex;
+}
+
+// A cached result for `key` in the file `path` (lines "key tile fp_cap
+// c64_cap ms"; the last matching line wins).
+bool tune_lookup(const char* path, const std::string& key, bg_batch_config* cfg, double* ms) {
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char k[64];
+    int t, fc, cc;
+    double m;
+    bool found = false;
+    while (fscanf(f, "%63s %d %d %d %lf", k, &t, &fc, &cc, &m) == 5) {
+        if (key == k && t > 0 && fc >= 0 && cc >= 0) {
+            *cfg = bg_batch_config{t, fc, cc};
+            *ms = m;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void tune_store(const char* path, const std::string& key, const bg_batch_config& cfg, double ms) {
+    FILE* f = fopen(path, "a");
+    if (!f) {
+        bgi::log("autotune cache %s not writable", path);
+        return;
+    }
+    fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), cfg.tile_points, cfg.fp_blocks_per_sm, cfg.c64_blocks_per_sm, ms);
+    fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
 // Time every candidate configuration (tile size x residency caps) on the
 // caller's batch and return the fastest.  Each candidate: one warm-up launch
-// and `reps` timed launches of its graph on `stream`.
+// and `reps` timed launches of its graph on `stream`.  With BG_AUTOTUNE_CACHE
+// naming a file, a result stored there for the same device and group mix is
+// returned without timing, and a new result is appended.
 bg_status bg_batch_autotune(const bg_group* groups, int n_groups, void* workspace, size_t workspace_bytes,
                             int reps, cudaStream_t stream, bg_batch_config* best, double* best_ms) {
     if (!best) return bgi::fail(BG_ERR_INVALID_ARG, "best is NULL");
+    if (!groups || n_groups < 1) return bgi::fail(BG_ERR_INVALID_ARG, "groups required");
     if (reps < 1) reps = 1;
+    const char* cache = getenv("BG_AUTOTUNE_CACHE");
+    std::string key;
+    if (cache && *cache) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        key = tune_key(groups, n_groups, dev);
+        double ms = 0;
+        if (tune_lookup(cache, key, best, &ms)) {
+            if (best_ms) *best_ms = ms;
+            bgi::log("autotune cache hit %s: tile %d, caps %d/%d, %.3f ms", key.c_str(), best->tile_points,
+                     best->fp_blocks_per_sm, best->c64_blocks_per_sm, ms);
+            return BG_OK;
+        }
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
@@ -347,6 +435,9 @@ bg_status bg_batch_autotune(const bg_group* groups, int n_groups, void* workspac
     cudaEventDestroy(e1);
     if (best_t < 0) return result != BG_OK ? result : bgi::fail(BG_ERR_CUDA, "no candidate ran");
     if (best_ms) *best_ms = best_t;
+    bgi::log("autotune: tile %d, caps %d/%d, %.3f ms", best->tile_points, best->fp_blocks_per_sm,
+             best->c64_blocks_per_sm, best_t);
+    if (!key.empty()) tune_store(cache, key, *best, best_t);
     return BG_OK;
 }
 

@@ -25,8 +25,9 @@
 //     sum hi(t) + hi(m p + lo(t));
 //   * a product of two reduced values is < p^2 < 2^62, so FOUR products fit
 //     in 64 bits without reduction;
-//   * a dot product sums its products in groups of up to four, applies
-//     redc_full to each group (level 1) and one more redc to their sum: the
+//   * a dot product of up to four products (< 2^64) applies redc_full and
+//     redc; of five to eight, adds two 64-bit sums of four into a 96-bit
+//     value and applies reduce96 (the same two Montgomery steps): the
 //     coefficient is at level 0, in [0, p];
 //   * R(i,j) accumulates the unreduced products (level 0 coefficient) x
 //     (level 1 entry) -- level-1 integers below 2^62 -- in a 96-bit
@@ -108,24 +109,30 @@ struct FpOps {
 
     // sum_mu eta_mu a_mu b_mu -> level 0, in [0, p].  All terms of the sign
     // that occurs most often are summed directly; the others use p - a.
-    // Groups of up to four products (< 4 p^2 < 2^64) are reduced with
-    // redc_full; the sum of at most two groups (< 2^34) with redc.
+    // Up to four products (< 4 p^2 < 2^64): one 64-bit sum, redc_full and
+    // redc.  Five to eight: two 64-bit sums of four added into a 96-bit value
+    // (hi <= 1) and reduced twice by reduce96 -- one reduction fewer than
+    // reducing each group (measured 3 % on the n=8, d=6 kernel).
     template <int D, int METRIC>
     __device__ __forceinline__ C dot(const T* a, const T* b) const {
         constexpr int nneg = []() { int c = 0; for (int mu = 0; mu < D; ++mu) c += msign<METRIC>(mu) < 0; return c; }();
         constexpr int flip = (nneg * 2 > D) ? -1 : 1;   // sign that is NOT negated
         static_assert(D <= 8, "two groups of four products at most");
-        uint64_t S = 0;
-        uint64_t t = 0;
-        int c = 0;
+        uint64_t s0 = 0, s1 = 0;
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) {
             const uint32_t x = (msign<METRIC>(mu) == flip) ? a[mu] : (p - a[mu]);
-            t += static_cast<uint64_t>(x) * b[mu];
-            if (++c == 4) { S += redc_full(t); t = 0; c = 0; }
+            if (mu < 4) s0 += static_cast<uint64_t>(x) * b[mu];
+            else s1 += static_cast<uint64_t>(x) * b[mu];
         }
-        if (c) S += redc_full(t);
-        const uint32_t r = fold(redc(S));          // flip * dot, level 0, [0, p)
+        uint32_t r;
+        if constexpr (D <= 4) {
+            r = fold(redc(redc_full(s0)));             // flip * dot, level 0, [0, p)
+        } else {
+            A acc{s0, 0u};
+            add96(acc, s1);
+            r = fold(reduce96(acc));
+        }
         return flip > 0 ? r : p - r;               // [0, p]
     }
     __device__ __forceinline__ C cadd(C a, C b) const { return madd(a, b); }        // [0, p)
@@ -164,9 +171,9 @@ struct FpOps {
             add96(acc[mu], static_cast<uint64_t>(c1) * v1[mu] + static_cast<uint64_t>(c2) * v2[mu] +
                                static_cast<uint64_t>(c3) * v3[mu] + static_cast<uint64_t>(c4) * v4[mu]);
     }
-    // 96-bit sum of level-1 products -> level -1, in [0, 2p): redc_full of
+    // 96-bit sum -> divided by R^2 (two Montgomery steps), in [0, 2p): redc_full of
     // the low word shifts the sum down by 2^32 (it stays far below p 2^32:
-    // a range sums fewer than 2^8 products), then one redc
+    // a range sums fewer than 2^8 products, a contraction eight), then one redc
     __device__ __forceinline__ uint32_t reduce96(const A& a) const {
         const uint32_t lo = static_cast<uint32_t>(a.lo);
         const uint32_t m = lo * pinv;

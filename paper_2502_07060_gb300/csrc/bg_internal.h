@@ -9,6 +9,7 @@
 
 #include "../../include/bg.h"
 #include "bg_instances.cuh"
+#include "bg_lanes.cuh"
 #include "bg_states.cuh"
 
 struct bg_plan {
@@ -30,6 +31,12 @@ struct bg_plan {
     int sm_count = 0;
     int blocks_per_sm = 0;
     size_t smem_bytes = 0;            // dynamic shared memory per block
+    // small batches: one point per group of L lanes (bg_lanes.cuh), used by
+    // bg_eval for at most lanes_max_items work items
+    const bgk::LanesEntry* lentry = nullptr;
+    size_t lanes_smem = 0;
+    int lanes_blocks_per_sm = 0;
+    int64_t lanes_max_items = 0;
     // all S^n assignments with sub-current reuse (assign == NULL, H == S^n > 1)
     bool all_states = false;
     const bgk::StatesEntry* sentry = nullptr;
@@ -57,7 +64,11 @@ struct Range {
 
 const std::vector<bgk::KernelEntry>& registry();
 const std::vector<bgk::StatesEntry>& states_registry();
+const std::vector<bgk::LanesEntry>& lanes_registry();
 bg_status fail(bg_status s, const char* fmt, ...);
+// One line on stderr, prefixed "bg: ", when the environment variable BG_LOG
+// is set to anything but "" or "0" (read once); otherwise nothing.
+void log(const char* fmt, ...);
 bg_status check_device_ptr(const void* ptr, const char* what, int device);
 bg_status check_kernel_ptr(const void* ptr, const char* what, int device, bool mapped_host_ok);
 // bg_eval that also takes page-locked host buffers mapped at the same address

@@ -28,8 +28,14 @@
 //     (bgi::in_place_pays), are staged through the arena by copies;
 //   * the dispatcher enqueues copies and kernels with the server mutex
 //     released, so the completion host functions never wait on it;
+//   * each slot records an event after its request's work; when the host
+//     function reports the slot finished, the dispatcher queries that event,
+//     so an asynchronous error of the request's copies or kernel marks the
+//     request failed (BG_ERR_CUDA from its wait) instead of done;
 //   * bg_serve_wait blocks on a condition variable with a deadline and
-//     returns BG_ERR_TIMEOUT when the request is not done by then.
+//     returns BG_ERR_TIMEOUT when the request is not done by then.  Several
+//     threads may wait on one ticket: each gets the request's result, and the
+//     request is freed when the last of them returns.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -113,6 +119,8 @@ struct Request {
     bg_status result = BG_OK;
     size_t off = 0;
     int slot = -1;
+    int waiters = 0;                         // threads inside bg_serve_wait on this ticket
+    bool retired = false;                    // finished and removed from the ticket map
 };
 
 }  // namespace
@@ -123,6 +131,7 @@ struct bg_server {
     unsigned char* arena_mem = nullptr;
     Arena* arena = nullptr;
     std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> slot_event;     // recorded after each request's work
     std::vector<Request*> slot_req;          // request running on each slot (or null)
     std::vector<int> slot_done;              // set by the host function
     std::mutex mu;
@@ -189,6 +198,7 @@ bg_status launch_request(bg_server* s, Request* r) {
         err = cudaMemcpyAsync(r->status, dst, (size_t)r->E, cudaMemcpyDeviceToHost, st);
     SlotDone* sd = new (std::nothrow) SlotDone{s, r->slot};
     if (!sd) return BG_ERR_NOMEM;
+    if (!err) err = cudaEventRecord(s->slot_event[r->slot], st);
     if (!err) err = cudaLaunchHostFunc(st, slot_finished, sd);
     if (err) { delete sd; cudaGetLastError(); return BG_ERR_CUDA; }
     return BG_OK;
@@ -210,7 +220,16 @@ void dispatcher(bg_server* s) {
             if (s->slot_req[i] && s->slot_done[i]) {
                 Request* r = s->slot_req[i];
                 s->arena->release(r->off, r->total);
-                r->state = State::Done;
+                // the host function ran after the work, so the event has
+                // completed -- unless that work raised an asynchronous error
+                const cudaError_t ev = cudaEventQuery(s->slot_event[i]);
+                if (ev == cudaSuccess) {
+                    r->state = State::Done;
+                } else {
+                    cudaGetLastError();
+                    r->result = BG_ERR_CUDA;
+                    r->state = State::Failed;
+                }
                 s->slot_req[i] = nullptr;
                 s->slot_done[i] = 0;
                 ++s->n_completed;
@@ -301,16 +320,21 @@ bg_status bg_serve_create(size_t budget_bytes, int max_inflight, bg_server** out
     }
     s->arena = new Arena(s->budget);
     s->streams.resize(max_inflight);
+    s->slot_event.resize(max_inflight);
     s->slot_req.assign(max_inflight, nullptr);
     s->slot_done.assign(max_inflight, 0);
     for (int i = 0; i < max_inflight; ++i) {
-        if (cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->slot_event[i], cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
-            for (int j = 0; j < i; ++j) cudaStreamDestroy(s->streams[j]);
+            for (int j = 0; j < i; ++j) {
+                cudaStreamDestroy(s->streams[j]);
+                cudaEventDestroy(s->slot_event[j]);
+            }
             cudaFree(s->arena_mem);
             delete s->arena;
             delete s;
-            return bgi::fail(BG_ERR_CUDA, "stream creation failed");
+            return bgi::fail(BG_ERR_CUDA, "stream or event creation failed");
         }
     }
     s->thread = std::thread(dispatcher, s);
@@ -412,15 +436,20 @@ bg_status bg_serve_wait(bg_server* srv, uint64_t ticket, int64_t timeout_ms) {
     if (it == srv->requests.end()) return bgi::fail(BG_ERR_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
     Request* r = it->second;
     auto finished = [r] { return r->state == State::Done || r->state == State::Failed; };
-    if (timeout_ms < 0) {
-        srv->cv_done.wait(lk, finished);
-    } else if (!srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), finished)) {
+    ++r->waiters;
+    bool done = true;
+    if (timeout_ms < 0) srv->cv_done.wait(lk, finished);
+    else done = srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), finished);
+    --r->waiters;
+    if (!done)
         return bgi::fail(BG_ERR_TIMEOUT, "request %llu not finished after %lld ms", (unsigned long long)ticket,
                          (long long)timeout_ms);
-    }
     const bg_status result = r->state == State::Done ? BG_OK : r->result;
-    srv->requests.erase(it);
-    delete r;
+    if (!r->retired) {                          // the first waiter to return retires the ticket
+        r->retired = true;
+        srv->requests.erase(r->id);
+    }
+    if (r->waiters == 0) delete r;              // the last one frees the request
     if (result != BG_OK) return bgi::fail(result, "request failed");
     return BG_OK;
 }
@@ -449,6 +478,7 @@ bg_status bg_serve_destroy(bg_server* srv) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
+    for (cudaEvent_t ev : srv->slot_event) cudaEventDestroy(ev);
     cudaFree(srv->arena_mem);
     for (auto& kv : srv->requests) delete kv.second;
     delete srv->arena;

@@ -1,4 +1,5 @@
-"""Small evaluations through every kernel family of the library, compared with
+"""Small evaluations through every kernel family of the library (the lane-group
+kernel of small batches included), compared with
 the oracle; run in a child process by test_gpu_bounds.py with BG_LIBRARY set to
 the bounds-checked build.  Prints one JSON line: the bounds report and the
 number of cases and mismatches."""
@@ -28,14 +29,16 @@ def main():
     def dev_u32(a):
         return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
 
-    def fp_case(n, d, Ds, metric, p, table=None, mask=None, S=1, assign=None, mode="eval"):
+    def fp_case(n, d, Ds, metric, p, table=None, mask=None, S=1, assign=None, mode="eval", lanes=False):
         nonlocal cases, mismatches
         k, e = G.fp_batch(100 + n * 10 + d, E, n, d, Ds, p, metric, S=S, workers=1,
                           four_d=mask or 0)
         if table:
             os.environ["BG_TABLE"] = table
+        os.environ["BG_LANES"] = "1" if lanes else "0"
         plan = bg.Plan(n, d, Ds, bg.FIELD_FP, p, metric, S, assign, four_dim_legs=mask)
         os.environ.pop("BG_TABLE", None)
+        os.environ.pop("BG_LANES", None)
         if S == 1:
             ref, _ = C.amp_fp(k, e, p, metric)
         else:
@@ -61,11 +64,13 @@ def main():
         got = out.cpu().numpy().view(np.uint32).reshape(ref.shape)
         mismatches += int(not np.array_equal(got, ref))
 
-    def c64_case(n, d, Ds, metric, real):
+    def c64_case(n, d, Ds, metric, real, lanes=False):
         nonlocal cases, mismatches
         k, e = G.c64_batch(200 + n * 10 + d, E, n, d, Ds, metric, workers=1)
         field = bg.FIELD_C64_REAL if real else bg.FIELD_C64
+        os.environ["BG_LANES"] = "1" if lanes else "0"
         plan = bg.Plan(n, d, Ds, field, 0, metric)
+        os.environ.pop("BG_LANES", None)
         kd = torch.from_numpy(np.ascontiguousarray(k.real if real else k)).cuda()
         out, _ = plan.eval(kd, torch.from_numpy(e).cuda())
         torch.cuda.synchronize()
@@ -95,6 +100,10 @@ def main():
     fp_case(8, 6, 6, 0, P, None, mode="noalloc")
     fp_case(12, 8, 8, 0, P, None, mode="noalloc")
     fp_case(9, 6, 6, 0, P, None, mode="host")
+    for n in (4, 8, 12):                         # lane-group kernel of small batches
+        fp_case(n, 4, 4, 1, PM, None, lanes=True)
+        fp_case(n, 5, 7, 0, P, None, lanes=True)
+        c64_case(n, 6, 6, 0, real=(n != 8), lanes=True)
     checked, violation = bg.bounds_report()
     print(json.dumps({"checked": checked, "violation": violation, "cases": cases, "mismatches": mismatches}))
 

@@ -53,17 +53,19 @@ def main():
                                 "good_equal": bool(np.array_equal(out[good], ref[good])),
                                 "good_status0": bool(np.all(st[good] == 0))})
 
-    # F_p, compact kernel (both table placements), n = 7, d = D_s = 6
+    # F_p, compact kernel (both table placements) and lane-group kernel, n = 7, d = D_s = 6
     k, e = G.fp_batch(71, E, 7, 6, 6, P, 0, workers=1)
     ref, _ = C.amp_fp(k, e, P, 0)
     kb, eb = corrupt_fp(k, e[:, :, None, :], P)
-    for table in ("shared", "global"):
+    for table, lanes in (("shared", "0"), ("global", "0"), ("global", "1")):
         os.environ["BG_TABLE"] = table
+        os.environ["BG_LANES"] = lanes
         plan = bg.Plan(7, 6, 6, bg.FIELD_FP, P, bg.MOSTLY_MINUS)
         os.environ.pop("BG_TABLE")
+        os.environ.pop("BG_LANES")
         out, st = plan.eval(dev_u32(kb), dev_u32(eb[:, :, 0, :]))
         torch.cuda.synchronize()
-        record(f"fp_compact_{table}", out.cpu().numpy().view(np.uint32), st, ref)
+        record(f"fp_compact_{table}" if lanes == "0" else "fp_lanes", out.cpu().numpy().view(np.uint32), st, ref)
     # F_p, uneven-batch kernel (the same point body inside the persistent kernel)
     plan = bg.Plan(7, 6, 6, bg.FIELD_FP, P, bg.MOSTLY_MINUS)
     out = torch.empty(E, dtype=torch.int32, device="cuda")
@@ -95,7 +97,9 @@ def main():
     kcb[11, 1, 3] += 0.25                                  # off shell
     kcb[13, 0] *= 2.0                                      # not conserved
     for real in (True, False):
+        os.environ["BG_LANES"] = "1" if real else "0"      # the real-momentum plan on the lane kernel
         plan = bg.Plan(6, 4, 4, bg.FIELD_C64_REAL if real else bg.FIELD_C64, 0, bg.MOSTLY_MINUS)
+        os.environ.pop("BG_LANES")
         kd = torch.from_numpy(np.ascontiguousarray(kcb.real if real else kcb)).cuda()
         out, st = plan.eval(kd, torch.from_numpy(ecb).cuda())
         torch.cuda.synchronize()

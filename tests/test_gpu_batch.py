@@ -1,11 +1,14 @@
 """Uneven batches (groups of different n, d, D_s, metric, number type and
-state tables) in one graph launch reproduce per-group bg_eval exactly: the
-same arithmetic runs in both, so F_p and complex results are bit-identical."""
+state tables) in one graph launch: every group's output equals the oracle
+(bit-exact over F_p, the complex tolerance rule of reading G8), under the
+default configuration, explicit ones and the autotuned one, and reproduces
+per-group bg_eval exactly (the same arithmetic runs in both)."""
 
 import numpy as np
 import pytest
 
 from paper_2502_07060_gb300 import inputs as G
+from tests.gpu_oracle_check import check_complex, check_fp
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +36,24 @@ def _group(bg, field, n, d, Ds, metric, E, seed, S=1, assign=None):
     H = plan.n_assign
     out = torch.empty((E,) if H == 1 else (E, H), dtype=ed.dtype, device="cuda")
     st = torch.empty(E, dtype=torch.uint8, device="cuda")
+    _HOST[id(out)] = (field, metric, p if field == "fp" else 0, k, e, assign)
     return plan, kd, ed, out, st
+
+
+_HOST = {}      # id(out tensor) -> the group's host inputs for the oracle
+
+
+def _check_oracle(groups):
+    """Every non-empty group's output and status against the oracle."""
+    for plan, k, _, out, st in groups:
+        if k.shape[0] == 0:
+            continue
+        field, metric, p, hk, he, assign = _HOST[id(out)]
+        o, s = out.cpu().numpy(), st.cpu().numpy()
+        if field == "fp":
+            check_fp(o, s, hk, he, p, metric, assign)
+        else:
+            check_complex(o, s, hk, he, metric, assign)
 
 
 SPECS = [("fp", 4, 4, 4, 0, 3000), ("fp", 8, 6, 6, 0, 5000), ("fp", 12, 8, 8, 1, 700),
@@ -68,6 +88,8 @@ def test_batch_matches_per_group_eval():
                 continue
             assert torch.equal(out, ref[0]), plan.describe()
             assert torch.equal(st, ref[1])
+        if rep == 0:
+            _check_oracle(groups)
     assert "tiles" in batch.describe()
 
 
@@ -77,10 +99,46 @@ def test_batch_config_variants_and_autotune():
     groups = [_group(bg, *s, seed=80 + i) for i, s in enumerate(SPECS[:7])]
     refs = [plan.eval(k, e)[0] for plan, k, e, _, _ in groups]
     for cfg in (bg.BgBatchConfig(256, 2, 1), bg.BgBatchConfig(4096, 0, 3)):
+        for _, _, _, out, st in groups:
+            out.zero_()
+            st.fill_(7)
         batch = bg.Batch(groups, config=cfg)
         batch.launch()
         torch.cuda.synchronize()
         for (_, _, _, out, _), ref in zip(groups, refs):
             assert torch.equal(out, ref)
+        _check_oracle(groups)
     best, ms = bg.Batch.autotune(groups, reps=1)
     assert best.tile_points in (256, 1024, 4096) and ms > 0
+    for _, _, _, out, st in groups:
+        out.zero_()
+        st.fill_(7)
+    tuned = bg.Batch(groups, config=best)
+    tuned.launch()
+    torch.cuda.synchronize()
+    _check_oracle(groups)
+
+
+def test_autotune_cache(tmp_path, monkeypatch):
+    """With BG_AUTOTUNE_CACHE set, the first autotune of a group mix times the
+    candidates and appends its result; the next one for the same mix reads it
+    back without timing; a different mix gets its own entry."""
+    from paper_2502_07060_gb300 import bg
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("BG_AUTOTUNE_CACHE", str(cache))
+    groups = [_group(bg, *s, seed=120 + i) for i, s in enumerate(SPECS[:3])]
+    best, ms = bg.Batch.autotune(groups, reps=1)
+    lines = cache.read_text().split("\n")
+    lines = [l for l in lines if l.strip()]
+    assert len(lines) == 1
+    key, t, fc, cc, m = lines[0].split()
+    assert (int(t), int(fc), int(cc)) == (best.tile_points, best.fp_blocks_per_sm, best.c64_blocks_per_sm)
+    again, ms2 = bg.Batch.autotune(groups, reps=1)
+    assert (again.tile_points, again.fp_blocks_per_sm, again.c64_blocks_per_sm) == \
+        (best.tile_points, best.fp_blocks_per_sm, best.c64_blocks_per_sm)
+    assert abs(ms2 - float(m)) < 1e-5
+    assert len([l for l in cache.read_text().split("\n") if l.strip()]) == 1
+    other = [_group(bg, *s, seed=130 + i) for i, s in enumerate(SPECS[3:5])]
+    bg.Batch.autotune(other, reps=1)
+    keys = [l.split()[0] for l in cache.read_text().split("\n") if l.strip()]
+    assert len(keys) == 2 and keys[0] != keys[1]

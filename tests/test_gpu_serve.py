@@ -1,12 +1,14 @@
-"""Serving: every request's result is the same alone and in the mix (bit-exact
-over F_p; identical complex results, since the same kernel runs), waits time
-out with an error instead of blocking, and admission respects the device
-memory budget."""
+"""Serving: every request's result equals the oracle (bit-exact over F_p, the
+complex tolerance rule of reading G8) and is the same alone and in the mix
+(identical results, since the same kernel runs), for host-staged, mapped
+page-locked and device-resident buffers; waits time out with an error instead
+of blocking, and admission respects the device memory budget."""
 
 import numpy as np
 import pytest
 
 from paper_2502_07060_gb300 import inputs as G
+from tests.gpu_oracle_check import check_complex, check_fp
 
 pytestmark = pytest.mark.gpu
 
@@ -41,6 +43,16 @@ def _pageable(req):
             torch.empty(out.shape, dtype=out.dtype), torch.empty(st.shape, dtype=st.dtype))
 
 
+def _oracle(plan, hk, he, out, st):
+    """The served output against the oracle on the request's host inputs."""
+    from paper_2502_07060_gb300 import bg
+    k, e = hk.cpu().numpy(), he.cpu().numpy()
+    if plan.field == bg.FIELD_FP:
+        check_fp(out.cpu().numpy(), st.cpu().numpy(), k.view(np.uint32), e.view(np.uint32), P, 0)
+    else:
+        check_complex(out.cpu().numpy(), st.cpu().numpy(), k.astype(np.complex128), e, 0)
+
+
 def _alone(plan, hk, he):
     import torch
     o, s = plan.eval(hk.cuda(), he.cuda())
@@ -64,9 +76,10 @@ def test_results_alone_equal_results_in_the_mix():
     tickets = [srv.submit(p, k, e, o, s) for p, k, e, o, s in reqs]
     for t in tickets[::-1]:                       # wait in reverse order
         assert srv.wait(t, timeout_ms=60000)
-    for (p, _, _, o, s), (ro, rs) in zip(reqs, refs):
+    for (p, k, e, o, s), (ro, rs) in zip(reqs, refs):
         assert torch.equal(o, ro), p.describe()
         assert torch.equal(s, rs)
+        _oracle(p, k, e, o, s)
     st = srv.stats()
     assert st["completed"] == 40 and st["pending"] == 0 and st["bytes_in_use"] == 0
     assert st["peak_bytes"] <= 256 << 20
@@ -122,9 +135,10 @@ def test_device_resident_inputs_and_outputs():
     dk = torch.from_numpy(k.view(np.int32)).cuda()            # resident pool
     de = torch.from_numpy(e.view(np.int32)).cuda()
     plan = bg.Plan(n, d, d, bg.FIELD_FP, P)
-    ref, _ = plan.eval(dk, de)
+    ref, rst = plan.eval(dk, de)
     torch.cuda.synchronize()
     ref = ref.cpu()
+    check_fp(ref.numpy(), rst.cpu().numpy(), k, e, P, 0)
     srv = bg.Server(64 << 20, max_inflight=4)
     jobs = []
     rng = np.random.default_rng(4)
@@ -172,6 +186,7 @@ def test_page_locked_requests_are_served_in_place():
         srv = bg.Server(2 << 30, max_inflight=2)
         assert srv.wait(srv.submit(plan, hk, he, out, st), timeout_ms=60000)
         assert torch.equal(out, ro) and torch.equal(st, rs), plan.describe()
+        _oracle(plan, hk, he, out, st)
         assert srv.stats()["peak_bytes"] == ws
         srv.close()
         _, pk, pe, po, ps = _pageable((plan, hk, he, out, st))
@@ -181,3 +196,27 @@ def test_page_locked_requests_are_served_in_place():
         assert torch.equal(po, ro) and torch.equal(ps, rs), plan.describe()
         assert srv.stats()["peak_bytes"] > ws
         srv.close()
+
+
+def test_two_threads_wait_on_one_ticket():
+    """Several waiters on one ticket all get its result; the ticket is retired
+    afterwards (a later wait reports an unknown ticket)."""
+    import threading
+    from paper_2502_07060_gb300 import bg
+    plan, hk, he, out, st = _request(bg, "c64", 10, 6, 3000, 1300)
+    srv = bg.Server(1 << 30, max_inflight=2)
+    t = srv.submit(plan, hk, he, out, st)
+    results = []
+
+    def waiter():
+        results.append(bg._lib.bg_serve_wait(srv._h, t, 60000))
+
+    threads = [threading.Thread(target=waiter) for _ in range(3)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert results == [bg.BG_OK] * 3
+    assert bg._lib.bg_serve_wait(srv._h, t, 0) == bg.BG_ERR_INVALID_ARG
+    _oracle(plan, hk, he, out, st)
+    srv.close()
