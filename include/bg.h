@@ -169,13 +169,15 @@ bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes);
  * the results are valid once the stream reaches the call).  The data-parallel
  * evaluation of Sec. 3: one independent recursion (Sec. 2.2) per point and
  * state assignment.  Large batches run one work item (point x assignment)
- * per thread; small ones -- at most a quarter of that kernel's resident
- * threads, see bg_plan_describe's lanes_max_items -- run each item on a
+ * per thread; small ones -- up to 16 (complex) or 24 (F_p, n >= 7) work
+ * items per SM, bg_plan_describe's lanes_max_items -- run each item on a
  * group of 4 or 8 lanes, one vector component per lane, which shortens the
  * call when most of the GPU would otherwise idle (the flat part of the
  * time-against-points curve of Sec. 3.2).  Both give the same F_p residues;
  * complex results agree to rounding.  The environment variable BG_LANES=0
  * (never) or 1 (always) read at plan creation overrides the choice.
+ * bg_eval_host and bg_eval_noalloc take the same kernel as bg_eval for the
+ * same batch (bg_eval_host chooses by the whole batch, not by chunk).
  *
  *   E          number of phase-space points, E >= 0 (E == 0: no launch)
  *   momenta    device [E][n][d]: uint32 residues (FP), double2 (C64) or

@@ -312,11 +312,15 @@ bg_status setup_states(bg_plan* pl, const int* radix, const char* tenv) {
 // batch sizes it takes.  A batch of E H work items on the compact kernel
 // runs one item per thread: while E H is far below the kernel's resident
 // threads most of the GPU idles and the call lasts as long as one thread's
-// whole recursion.  The lanes kernel spreads each item over L lanes.
-// BG_LANES=0 never uses it, BG_LANES=1 always (when the plan has one),
-// otherwise batches of at most a quarter of the compact kernel's resident
-// threads take it (the crossover measured on GB300 lies near there for
-// n = 4..12, both number types).
+// whole recursion.  The lanes kernel spreads each item over L lanes, which
+// shortens that recursion for the complex fields (FP64 vector updates split
+// over the lanes: 2.1x at n = 8, 2.8x at n = 12, d = 8, up to 2048 points)
+// and less over F_p, where the shuffled contractions lengthen its dependency
+// chains (1.17x at n = 8, 1.4x at n = 12; none at n <= 5).  Measured on
+// GB300, the lanes kernel stops paying between 16 and 32 items per SM for
+// the complex fields and between 24 and 48 for F_p: BG_LANES unset takes it
+// up to 16 (complex) or 24 (F_p, n >= 7) items per SM; BG_LANES=0 never,
+// BG_LANES=1 always (when the plan has one).
 bg_status setup_lanes(bg_plan* pl) {
     const int L = round_dim(pl->Ds) <= 4 ? 4 : 8;
     for (const auto& e : bgi::lanes_registry())
@@ -338,7 +342,8 @@ bg_status setup_lanes(bg_plan* pl) {
     const char* env = getenv("BG_LANES");
     if (env && strcmp(env, "0") == 0) pl->lanes_max_items = 0;
     else if (env && strcmp(env, "1") == 0) pl->lanes_max_items = INT64_MAX;
-    else pl->lanes_max_items = (int64_t)pl->blocks_per_sm * pl->sm_count * pl->entry->block / 4;
+    else if (pl->field == BG_FIELD_FP) pl->lanes_max_items = pl->n >= 7 ? (int64_t)24 * pl->sm_count : 0;
+    else pl->lanes_max_items = (int64_t)16 * pl->sm_count;
     return BG_OK;
 }
 
@@ -615,25 +620,62 @@ static int64_t resident_blocks(const bg_plan* pl) { return (int64_t)pl->blocks_p
 
 bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes) {
     if (!plan || !bytes || E < 0) return fail(BG_ERR_INVALID_ARG, "bad argument to bg_workspace_size");
-    *bytes = 0;
-    if (E == 0) return BG_OK;
+    *bytes = bgi::workspace_bytes(plan, E, E * plan->H);
+    return BG_OK;
+}
+
+}  // extern "C"
+
+namespace bgi {
+
+bool uses_lanes(const bg_plan* plan, int64_t select_items) {
+    return !plan->all_states && plan->lentry && select_items <= plan->lanes_max_items;
+}
+
+bg_status launch_lanes(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
+                       uint8_t* status, int dev, cudaStream_t stream) {
+    const bgk::LanesEntry* le = plan->lentry;
+    bg_status st;
+    if (dev != plan->device && (st = ensure_smem_limit(le->func, dev, plan->lanes_smem)) != BG_OK) return st;
+    const int64_t items = E * plan->H;
+    const int64_t ppb = le->block / le->L;
+    int64_t blocks = (items + ppb - 1) / ppb;
+    const int64_t cap = (int64_t)plan->lanes_blocks_per_sm * plan->sm_count;
+    if (blocks > cap) blocks = cap;
+    bgk::CompactArgs a;
+    a.E = E; a.H = plan->H; a.S = plan->S; a.n = plan->n;
+    a.d_in = plan->d; a.ds_in = plan->Ds;
+    a.k = momenta; a.eps = eps; a.out = out; a.status = status;
+    a.assign = plan->d_assign; a.ws = nullptr;
+    a.four_d_legs = 0;
+    a.violation = violation_word(dev);
+    le->launch(compact_params(plan), &a, dim3((unsigned)blocks), plan->lanes_smem, stream);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(BG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(err));
+    return BG_OK;
+}
+
+size_t workspace_bytes(const bg_plan* plan, int64_t E, int64_t select_items) {
+    if (E <= 0) return 0;
     if (plan->all_states) {
-        if (!plan->states_global) return BG_OK;
+        if (!plan->states_global) return 0;
         const int64_t per_block = (int64_t)bgk::kStatesWarps * plan->sgeo.P;
         int64_t blocks = (E + per_block - 1) / per_block;
         if (blocks > resident_blocks(plan)) blocks = resident_blocks(plan);
-        *bytes = (size_t)blocks * per_block * plan->sgeo.words * plan->sentry->elem_bytes;
-        return BG_OK;
+        return (size_t)blocks * per_block * plan->sgeo.words * plan->sentry->elem_bytes;
     }
-    if (!plan->entry->global_table) return BG_OK;
+    if (!plan->entry->global_table) return 0;
+    if (uses_lanes(plan, select_items)) return 0;      // lanes kernel: shared memory only
     const int64_t items = E * plan->H;
-    if (plan->lentry && items <= plan->lanes_max_items) return BG_OK;     // lanes kernel: no workspace
     const int B = plan->entry->block;
     int64_t blocks = (items + B - 1) / B;
     if (blocks > resident_blocks(plan)) blocks = resident_blocks(plan);
-    *bytes = (size_t)blocks * B * plan->words * plan->entry->elem_bytes;
-    return BG_OK;
+    return (size_t)blocks * B * plan->words * plan->entry->elem_bytes;
 }
+
+}  // namespace bgi
+
+extern "C" {
 
 bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
     if (!plan || !buf) return fail(BG_ERR_INVALID_ARG, "bad argument to bg_plan_describe");
@@ -667,7 +709,7 @@ namespace {
 
 bg_status eval_impl(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
                     uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream,
-                    bool mapped_host_ok) {
+                    bool mapped_host_ok, int64_t select_items) {
     g_last_error.clear();
     if (!plan) return fail(BG_ERR_INVALID_ARG, "plan is NULL");
     if (E < 0) return fail(BG_ERR_INVALID_ARG, "E = %lld < 0", (long long)E);
@@ -692,8 +734,7 @@ bg_status eval_impl(const bg_plan* plan, int64_t E, const void* momenta, const v
     if (status && (st = bgi::check_kernel_ptr(status, "status", dev, mapped_host_ok)) != BG_OK) return st;
 
     const bgk::KernelEntry* e = plan->entry;
-    size_t need = 0;
-    bg_workspace_size(plan, E, &need);
+    const size_t need = bgi::workspace_bytes(plan, E, select_items);
     if (need > 0) {
         if (!workspace || workspace_bytes < need)
             return fail(BG_ERR_INVALID_ARG, "workspace of %zu B needed, %zu B given", need, workspace_bytes);
@@ -725,26 +766,7 @@ bg_status eval_impl(const bg_plan* plan, int64_t E, const void* momenta, const v
     }
     if (bgi::fault(BG_FAULT_LAUNCH)) return fail(BG_ERR_CUDA, "launch failed: injected fault");
     const int64_t items = E * plan->H;
-    if (plan->lentry && items <= plan->lanes_max_items) {
-        // small batch: one item per group of L lanes
-        const bgk::LanesEntry* le = plan->lentry;
-        if (dev != plan->device && (st = bgi::ensure_smem_limit(le->func, dev, plan->lanes_smem)) != BG_OK) return st;
-        const int64_t ppb = le->block / le->L;
-        int64_t lblocks = (items + ppb - 1) / ppb;
-        const int64_t lcap = (int64_t)plan->lanes_blocks_per_sm * plan->sm_count;
-        if (lblocks > lcap) lblocks = lcap;
-        bgk::CompactArgs a;
-        a.E = E; a.H = plan->H; a.S = plan->S; a.n = plan->n;
-        a.d_in = plan->d; a.ds_in = plan->Ds;
-        a.k = momenta; a.eps = eps; a.out = out; a.status = status;
-        a.assign = plan->d_assign; a.ws = nullptr;
-        a.four_d_legs = 0;
-        a.violation = bgi::violation_word(dev);
-        le->launch(compact_params(plan), &a, dim3((unsigned)lblocks), plan->lanes_smem, stream);
-        cudaError_t lerr = cudaGetLastError();
-        if (lerr != cudaSuccess) return fail(BG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(lerr));
-        return BG_OK;
-    }
+    if (bgi::uses_lanes(plan, select_items)) return bgi::launch_lanes(plan, E, momenta, eps, out, status, dev, stream);
     int64_t blocks = (items + e->block - 1) / e->block;
     const int64_t cap = e->global_table ? resident_blocks(plan) : resident_blocks(plan) * 256;
     if (blocks > cap) blocks = cap;
@@ -766,7 +788,8 @@ bg_status eval_impl(const bg_plan* plan, int64_t E, const void* momenta, const v
 bg_status bg_eval(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
                   uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream) {
     bgi::Range nvtx("bg_eval");
-    return eval_impl(plan, E, momenta, eps, out, status, workspace, workspace_bytes, stream, false);
+    return eval_impl(plan, E, momenta, eps, out, status, workspace, workspace_bytes, stream, false,
+                     plan ? E * plan->H : 0);
 }
 
 }  // extern "C"
@@ -776,7 +799,14 @@ namespace bgi {
 bg_status eval_mapped(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
                       uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream) {
     Range nvtx("bg_eval_mapped");
-    return eval_impl(plan, E, momenta, eps, out, status, workspace, workspace_bytes, stream, true);
+    return eval_impl(plan, E, momenta, eps, out, status, workspace, workspace_bytes, stream, true,
+                     plan ? E * plan->H : 0);
+}
+
+bg_status eval_part(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
+                    uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream,
+                    int64_t batch_items) {
+    return eval_impl(plan, E, momenta, eps, out, status, workspace, workspace_bytes, stream, false, batch_items);
 }
 
 }  // namespace bgi

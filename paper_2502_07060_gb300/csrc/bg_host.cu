@@ -23,6 +23,8 @@
 // results in place instead: no copies, no chunk boundaries.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include <mutex>
 
 #include "bg_internal.h"
@@ -80,9 +82,9 @@ Slot slot_sizes(const bg_plan* pl, int64_t chunk) {
 
 extern "C" bg_status bg_host_staging_size(const bg_plan* plan, int64_t chunk, size_t* bytes) {
     if (!plan || !bytes || chunk < 1) return bgi::fail(BG_ERR_INVALID_ARG, "bad argument to bg_host_staging_size");
-    size_t ws = 0;
-    bg_status st = bg_workspace_size(plan, chunk, &ws);
-    if (st != BG_OK) return st;
+    // a chunk of a large batch runs the kernel of the whole batch, which may
+    // need a workspace even where a batch of `chunk` points alone would not
+    const size_t ws = bgi::workspace_bytes(plan, chunk, INT64_MAX);
     *bytes = 2 * slot_sizes(plan, chunk).total() + up256(ws);
     return BG_OK;
 }
@@ -173,7 +175,8 @@ extern "C" bg_status bg_eval_host(const bg_plan* plan, int64_t E, const void* mo
             cudaGetLastError();
             return drained(bgi::fail(BG_ERR_CUDA, "enqueueing chunk %lld: %s", (long long)c, cudaGetErrorString(err)));
         }
-        if ((st = bg_eval(plan, m, dk, de, dout, dst, ws, ws_bytes, stream)) != BG_OK) return drained(st);
+        if ((st = bgi::eval_part(plan, m, dk, de, dout, dst, ws, ws_bytes, stream, E * plan->H)) != BG_OK)
+            return drained(st);
         err = cudaEventRecord(hp->k_done[s], stream);
         if (!err) err = cudaStreamWaitEvent(hp->s_out, hp->k_done[s], 0);
         if (!err) err = cudaMemcpyAsync(oh + start * o_pt, dout, m * o_pt, cudaMemcpyDeviceToHost, hp->s_out);

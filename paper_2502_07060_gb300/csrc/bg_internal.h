@@ -76,6 +76,20 @@ bg_status check_kernel_ptr(const void* ptr, const char* what, int device, bool m
 // reads and writes them over the host link.
 bg_status eval_mapped(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
                       uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream);
+// bg_eval on part of a larger batch of batch_items work items (a chunk of
+// bg_eval_host): the kernel is the one bg_eval takes for the whole batch, so
+// every chunk gives the whole batch's values.
+bg_status eval_part(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
+                    uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream,
+                    int64_t batch_items);
+// Whether a batch of select_items work items runs on the plan's lane-group
+// kernel, and the device workspace for E points when the kernel is chosen by
+// select_items (bg_workspace_size: select_items = E * H).
+bool uses_lanes(const bg_plan* plan, int64_t select_items);
+// One launch of the plan's lane-group kernel on E points (checked arguments).
+bg_status launch_lanes(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
+                       uint8_t* status, int dev, cudaStream_t stream);
+size_t workspace_bytes(const bg_plan* plan, int64_t E, int64_t select_items);
 // True when `p` is page-locked host memory mapped into the device's address
 // space at the same address (the kernels can read and write it directly).
 bool mapped_host(const void* p);

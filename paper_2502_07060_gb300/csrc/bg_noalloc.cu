@@ -88,6 +88,12 @@ extern "C" bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void*
     if ((st = bgi::check_device_ptr(out, "out", dev)) != BG_OK) return st;
     if (status && (st = bgi::check_device_ptr(status, "status", dev)) != BG_OK) return st;
 
+    // Small batches take the lane-group kernel as bg_eval does; its table is
+    // in shared memory, so it needs no scratch at all.
+    if (bgi::uses_lanes(plan, E * plan->H)) {
+        if (bgi::fault(BG_FAULT_LAUNCH)) return bgi::fail(BG_ERR_CUDA, "launch failed: injected fault");
+        return bgi::launch_lanes(plan, E, momenta, eps, out, status, dev, stream);
+    }
     // The compact kernel with its table in global memory, same dimensions and
     // metric as the plan's own kernel.
     const int D = bgi::round_dim(plan->d), DS = bgi::round_dim(plan->Ds);

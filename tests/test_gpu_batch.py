@@ -17,7 +17,12 @@ PM = G.P_MERSENNE
 
 
 def _group(bg, field, n, d, Ds, metric, E, seed, S=1, assign=None):
+    """A group and its plan; the plan's own bg_eval runs one point per thread
+    at every size (BG_LANES=0), the arithmetic the batch kernels share, so the
+    batch reproduces it bit for bit."""
+    import os
     import torch
+    os.environ["BG_LANES"] = "0"
     if field == "fp":
         p = P if metric == 0 else PM
         k, e = G.fp_batch(seed, E, n, d, Ds, p, metric, S=S, workers=1)
@@ -33,6 +38,7 @@ def _group(bg, field, n, d, Ds, metric, E, seed, S=1, assign=None):
         ed = torch.from_numpy(e).cuda()
         fid = bg.FIELD_C64_REAL if field == "c64r" else bg.FIELD_C64
         plan = bg.Plan(n, d, Ds, fid, 0, metric, S, assign)
+    os.environ.pop("BG_LANES", None)
     H = plan.n_assign
     out = torch.empty((E,) if H == 1 else (E, H), dtype=ed.dtype, device="cuda")
     st = torch.empty(E, dtype=torch.uint8, device="cuda")
