@@ -579,6 +579,65 @@ def sweep_workload(args, device):
             "unit": "amplitudes/s", **res}
 
 
+def lanes_workload(args, device):
+    """Small batches: one bg_eval launch on the one-point-per-thread kernel
+    (BG_LANES=0) against the lane-group kernel (BG_LANES=1) for E = 2^6 ..
+    2^15 points: F_p (p = 2^31 - 19) at n = 5, 8, 12 and complex FP64 (real
+    momenta at n = 8 and 12, complex momenta at n = 6), mostly-minus metric.
+    Each entry: 3 warm-up calls, then the mean of 20 CUDA-event-timed calls;
+    F_p results compared bit for bit, complex ones by their largest relative
+    difference."""
+    import torch
+    from paper_2502_07060_gb300 import bg
+    stream = torch.cuda.current_stream(device)
+    rows = []
+    for field, n, d, lgmax in (("fp", 5, 4, 15), ("fp", 8, 6, 15), ("fp", 12, 8, 15), ("c64r", 8, 6, 15),
+                               ("c64r", 12, 8, 13), ("c64", 6, 4, 15)):
+        E = 1 << lgmax
+        if field == "fp":
+            k, e = G.fp_batch(11, E, n, d, d, P, 0)
+            kd = torch.from_numpy(k.view(np.int32)).to(device)
+            ed = torch.from_numpy(e.view(np.int32)).to(device)
+            fid, p = bg.FIELD_FP, P
+        else:
+            k, e = G.c64_batch(11, E, n, d, d, 0)
+            kd = torch.from_numpy(np.ascontiguousarray(k.real) if field == "c64r" else k).to(device)
+            ed = torch.from_numpy(e).to(device)
+            fid, p = (bg.FIELD_C64_REAL if field == "c64r" else bg.FIELD_C64), 0
+        plans = {}
+        for v in ("0", "1", "auto"):
+            old = os.environ.get("BG_LANES")
+            os.environ["BG_LANES"] = v
+            plans[v] = bg.Plan(n, d, d, fid, p, bg.MOSTLY_MINUS)
+            if old is None:
+                os.environ.pop("BG_LANES")
+            else:
+                os.environ["BG_LANES"] = old
+        cut = int(dict(x.split("=", 1) for x in plans["auto"].describe().split())["lanes_max_items"])
+        for lg in range(6, lgmax + 1):
+            m = 1 << lg
+            row = {"field": field, "n": n, "d": d, "E": m, "default": "lanes" if m <= cut else "per_thread"}
+            outs = {}
+            for v, key in (("0", "per_thread_ms"), ("1", "lanes_ms")):
+                plan = plans[v]
+                out = torch.empty(m, dtype=ed.dtype, device=device)
+                st = torch.empty(m, dtype=torch.uint8, device=device)
+                ws = plan.workspace(m, device)
+                fn = lambda: plan.eval(kd[:m], ed[:m], out=out, status=st, workspace=ws, stream=stream)
+                row[key] = time_steps(fn, 20, 3, stream, None, device) / 20
+                outs[v] = out
+            if field == "fp":
+                row["bit_identical"] = bool(torch.equal(outs["0"], outs["1"]))
+            else:
+                row["max_rel_diff"] = float(((outs["0"] - outs["1"]).abs() / outs["0"].abs()).max().item())
+            row["speedup"] = row["per_thread_ms"] / row["lanes_ms"]
+            rows.append(row)
+        del kd, ed
+        torch.cuda.empty_cache()
+    return {"workload": "small batches, one bg_eval launch: per-thread kernel against the lane-group kernel",
+            "unit": "ms per call", "rows": rows}
+
+
 def fourdim_workload(args, device):
     """Trees of a one-loop cut (Sec. 2.3): legs 0 and n-1 d-dimensional, legs
     1..n-2 four-dimensional states zero-padded into d dimensions.  Times the
@@ -797,13 +856,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving latency leg")
     ap.add_argument("--workload", choices=["metric", "mixed", "serve", "helicity", "sweep", "fourdim",
-                                           "launchcheck"],
+                                           "lanes", "launchcheck"],
                     default="metric",
                     help="metric: n=8 d=6 headline line; mixed: uneven-batch comparison; "
                          "serve: p50/p99 latency of the request server; helicity: all 2^n "
                          "helicities with shared sub-currents against one recursion per assignment; "
                          "sweep: time against points, gluons and dimension; fourdim: cut trees with "
-                         "four-dimensional legs, ordinary against mixed-dimension plans; launchcheck: "
+                         "four-dimensional legs, ordinary against mixed-dimension plans; lanes: small "
+                         "batches on the per-thread and lane-group kernels; launchcheck: "
                          "the multi-rank launch on CPU (gloo), no GPU work")
     ap.add_argument("--log2-points-helicity", type=int, default=20,
                     help="points per n of the helicity workload")
@@ -881,6 +941,10 @@ def main():
     if args.workload == "sweep":
         if rank == 0:
             print(json.dumps({"metric": METRIC, "sweep": sweep_workload(args, device)}))
+        return
+    if args.workload == "lanes":
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "lanes": lanes_workload(args, device)}))
         return
     if args.workload == "serve":
         if rank == 0:

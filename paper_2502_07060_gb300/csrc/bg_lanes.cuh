@@ -264,14 +264,24 @@ __device__ __forceinline__ void lanes_point(const F& f, const CompactArgs& a, un
                 if (lenB >= 2) cpre = f.csub(cpre, f.t_to_c(SA(ss - N)));
                 f.template acc2<1>(acc, csuf, &sf, cpre, &pb);
                 f.template kacc1<1>(acc, f.cdbl(adj), &Kt);
+                // gaps in pairs: two independent shuffle contractions in flight
                 int pq = i, dp = N, iq = es, di = N - b + 1;
+                int q = 0;
 #pragma unroll 1
-                for (int q = 0; q < b; ++q) {
-                    const T pa = J(pq), in = J(iq);
-                    const C g0 = f.cdbl(lo.template dot<METRIC>(pa, sf, mu));
-                    f.template acc1<1>(acc, g0, &in);
+                for (; q + 1 < b; q += 2) {
+                    const T pa0 = J(pq), in0 = J(iq);
                     pq += dp; iq -= di;
-                    --dp; ++di;
+                    const T pa1 = J(pq), in1 = J(iq);
+                    pq += dp - 1; iq -= di + 1;
+                    dp -= 2; di += 2;
+                    const C g0 = f.cdbl(lo.template dot<METRIC>(pa0, sf, mu));
+                    const C g1 = f.cdbl(lo.template dot<METRIC>(pa1, sf, mu));
+                    f.template acc2<1>(acc, g0, &in0, g1, &in1);
+                }
+                if (q < b) {
+                    const T pa0 = J(pq), in0 = J(iq);
+                    const C g0 = f.cdbl(lo.template dot<METRIC>(pa0, sf, mu));
+                    f.template acc1<1>(acc, g0, &in0);
                 }
                 ps += N - b;
                 ss -= N - lenB + 1;

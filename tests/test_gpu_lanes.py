@@ -116,7 +116,8 @@ def test_lanes_singular_point():
 def test_default_choice_and_switch_over(field):
     """Without BG_LANES the plan takes the lanes kernel up to lanes_max_items
     work items and needs no workspace there; at and just above that size the
-    two kernels give the same residues (F_p) or agree to 1e-12 (complex)."""
+    two kernels give the same residues (F_p), or both meet the oracle's
+    complex tolerance (their sums run in different orders)."""
     import torch
     from paper_2502_07060_gb300 import bg
     n, d = 7, 6
@@ -141,7 +142,8 @@ def test_default_choice_and_switch_over(field):
         if field == "fp":
             assert np.array_equal(out, ref)
         else:
-            assert (np.abs(out - ref) <= 1e-12 * np.abs(ref)).all()
+            check_complex(out, st, k, e, 0)
+            check_complex(ref, rst, k, e, 0)
     sample = np.arange(0, cut, max(1, cut // 300))
     if field == "fp":
         k, e = G.fp_batch(1800, cut, n, d, d, workers=1)
