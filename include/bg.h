@@ -170,7 +170,8 @@ bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes);
  * evaluation of Sec. 3: one independent recursion (Sec. 2.2) per point and
  * state assignment.  Large batches run one work item (point x assignment)
  * per thread; small ones -- up to 16 (complex) or 24 (F_p, n >= 7) work
- * items per SM, bg_plan_describe's lanes_max_items -- run each item on a
+ * items per SM or half a resident wave of the lane kernel, whichever is
+ * larger: bg_plan_describe's lanes_max_items -- run each item on a
  * group of 4 or 8 lanes, one vector component per lane, which shortens the
  * call when most of the GPU would otherwise idle (the flat part of the
  * time-against-points curve of Sec. 3.2).  Both give the same F_p residues;

@@ -2,6 +2,7 @@
 // validation, kernel selection and the single launch of bg_eval.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdlib>
@@ -316,11 +317,13 @@ bg_status setup_states(bg_plan* pl, const int* radix, const char* tenv) {
 // shortens that recursion for the complex fields (FP64 vector updates split
 // over the lanes: 2.1x at n = 8, 2.8x at n = 12, d = 8, up to 2048 points)
 // and less over F_p, where the shuffled contractions lengthen its dependency
-// chains (1.17x at n = 8, 1.4x at n = 12; none at n <= 5).  Measured on
+// chains (1.24x at n = 8, 1.5x at n = 12; none at n <= 5).  Measured on
 // GB300, the lanes kernel stops paying between 16 and 32 items per SM for
-// the complex fields and between 24 and 48 for F_p: BG_LANES unset takes it
-// up to 16 (complex) or 24 (F_p, n >= 7) items per SM; BG_LANES=0 never,
-// BG_LANES=1 always (when the plan has one).
+// the complex fields at n = 8..12 and between 24 and 48 for F_p, and at about
+// half of one resident wave of lane groups when the groups are small (L = 4,
+// short tables): BG_LANES unset takes it up to max(16 (complex) or 24 (F_p,
+// n >= 7) items per SM, half a resident wave of the lanes kernel);
+// BG_LANES=0 never, BG_LANES=1 always (when the plan has one).
 bg_status setup_lanes(bg_plan* pl) {
     const int L = round_dim(pl->Ds) <= 4 ? 4 : 8;
     for (const auto& e : bgi::lanes_registry())
@@ -342,8 +345,12 @@ bg_status setup_lanes(bg_plan* pl) {
     const char* env = getenv("BG_LANES");
     if (env && strcmp(env, "0") == 0) pl->lanes_max_items = 0;
     else if (env && strcmp(env, "1") == 0) pl->lanes_max_items = INT64_MAX;
-    else if (pl->field == BG_FIELD_FP) pl->lanes_max_items = pl->n >= 7 ? (int64_t)24 * pl->sm_count : 0;
-    else pl->lanes_max_items = (int64_t)16 * pl->sm_count;
+    else {
+        const int64_t wave = (int64_t)occ * pl->sm_count * (pl->lentry->block / pl->lentry->L);
+        const int64_t per_sm = pl->field == BG_FIELD_FP ? 24 : 16;
+        pl->lanes_max_items = (pl->field == BG_FIELD_FP && pl->n < 7) ? 0
+                            : std::max(per_sm * pl->sm_count, wave / 2);
+    }
     return BG_OK;
 }
 

@@ -263,8 +263,9 @@ def test_eval_rejects_host_pointers_and_small_workspace():
         plan.eval(k, k, out=torch.zeros(4, dtype=torch.int32, device="cuda"))
     assert ei.value.status == bg.BG_ERR_INVALID_ARG
     c = bg.Plan(8, 6, 6, bg.FIELD_C64, 0)
-    kd = torch.zeros((1000, 8, 6), dtype=torch.complex128, device="cuda")
-    need = c.workspace_size(1000)
+    E = 20000                                                  # above the lane kernel's batch sizes
+    kd = torch.zeros((E, 8, 6), dtype=torch.complex128, device="cuda")
+    need = c.workspace_size(E)
     assert need > 0
     small = torch.empty(need // 2, dtype=torch.uint8, device="cuda")
     with pytest.raises(bg.BGError):
