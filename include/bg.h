@@ -449,7 +449,8 @@ bg_status bg_debug_bounds_report(int* checked, uint64_t* first_violation);
  * 64 MiB, or batches whose arithmetic per point hides the link traffic), 0
  * when copies should move them; *ops = the field multiplications per
  * amplitude of the literal recursion that the estimate uses.  Pure host
- * arithmetic: needs no device.  BG_ERR_INVALID_ARG for arguments out of the
+ * arithmetic for a 152-SM GB300 (the library's own decision scales the
+ * kernels' rates by the plan device's SM count): needs no device.  BG_ERR_INVALID_ARG for arguments out of the
  * ranges of bg_plan_create, H < 1, E < 0 or NULL outputs.
  */
 bg_status bg_debug_in_place_pays(bg_field field, int n, int d, int D_s, int H, int64_t E,

@@ -224,15 +224,18 @@ double ops_per_amplitude(int n, int d, int D) {
 // 100 GB/s over the host link: in place pays while the batch needs at most
 // 80 GB/s of it.  At n = 8, d = 6 that keeps F_p batches (about 350 GB/s)
 // on copies and takes complex ones (about 60 GB/s) in place.
-bool in_place_pays_for(int field, int n, int d, int Ds, int H, int64_t E, size_t host_bytes) {
+bool in_place_pays_for(int field, int n, int d, int Ds, int H, int64_t E, size_t host_bytes, double sm_scale) {
     if (host_bytes <= kInPlaceBytes) return true;
-    const double rate = field == BG_FIELD_FP ? 4.3e12 : field == BG_FIELD_C64_REAL ? 2.5e11 : 1.9e11;
+    const double rate = sm_scale * (field == BG_FIELD_FP ? 4.3e12 : field == BG_FIELD_C64_REAL ? 2.5e11 : 1.9e11);
     const double seconds = (double)E * H * ops_per_amplitude(n, d, Ds) / rate;
     return (double)host_bytes <= 80e9 * seconds;
 }
 
+// The rates above were measured on a 152-SM GB300; a device with another SM
+// count scales them (the kernels are bound by per-SM pipes).
 bool in_place_pays(const bg_plan* plan, int64_t E, size_t host_bytes) {
-    return in_place_pays_for(plan->field, plan->n, plan->d, plan->Ds, plan->H, E, host_bytes);
+    const double sm_scale = plan->sm_count > 0 ? plan->sm_count / 152.0 : 1.0;
+    return in_place_pays_for(plan->field, plan->n, plan->d, plan->Ds, plan->H, E, host_bytes, sm_scale);
 }
 
 int round_dim(int x) { return x <= 4 ? 4 : (x <= 6 ? 6 : 8); }
@@ -398,7 +401,7 @@ bg_status bg_debug_in_place_pays(bg_field field, int n, int d, int D_s, int H, i
         (field != BG_FIELD_C64 && field != BG_FIELD_FP && field != BG_FIELD_C64_REAL))
         return fail(BG_ERR_INVALID_ARG, "bad argument to bg_debug_in_place_pays");
     *ops = bgi::ops_per_amplitude(n, d, D_s);
-    *in_place = bgi::in_place_pays_for((int)field, n, d, D_s, H, E, host_bytes) ? 1 : 0;
+    *in_place = bgi::in_place_pays_for((int)field, n, d, D_s, H, E, host_bytes, 1.0) ? 1 : 0;
     return BG_OK;
 }
 
