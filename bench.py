@@ -416,24 +416,30 @@ def run_field(field, E, steps, warmup, rank, dist, device, seed, e2e=True):
 
 
 def mixed_workload(args, device):
-    """Uneven batch: 2^22 points spread evenly over n = 4..12, d = D_s in
-    {4, 6, 8} and both number types (54 groups).  Times (a) 54 plain
-    per-group bg_eval launches, (b) one graph launch of the batch with the
-    default configuration and (c) with the autotuned configuration."""
+    """Uneven batches over n = 4..12, d = D_s in {4, 6, 8} and both number
+    types (54 groups): 2^22 points spread evenly (about 78 k per group), and
+    54 small groups of 512 points (the request mix of a serving step).  Each
+    times (a) 54 plain per-group bg_eval launches (which take the lane-group
+    kernel for small groups), (b) one graph launch of the batch with the
+    default configuration and (c) with the autotuned configuration (tile size,
+    residency caps, lane groups for small groups)."""
+    return {"large": _mixed(args, device, (1 << args.log2_points) // 54, 3000),
+            "small": _mixed(args, device, 512, 3100)}
+
+
+def _mixed(args, device, per, seed0):
     import torch
     from paper_2502_07060_gb300 import bg
-    total = 1 << args.log2_points
     specs = [(f, n, d) for f in ("fp", "c64") for n in range(4, 13) for d in (4, 6, 8)]
-    per = total // len(specs)
     groups = []
     for i, (f, n, d) in enumerate(specs):
         if f == "fp":
-            k, e = G.fp_batch(3000 + i, per, n, d, d, P, 0)
+            k, e = G.fp_batch(seed0 + i, per, n, d, d, P, 0)
             kd = torch.from_numpy(k.view(np.int32)).to(device)
             ed = torch.from_numpy(e.view(np.int32)).to(device)
             plan = bg.Plan(n, d, d, bg.FIELD_FP, P, bg.MOSTLY_MINUS)
         else:
-            k, e = G.c64_batch(3000 + i, per, n, d, d, 0)
+            k, e = G.c64_batch(seed0 + i, per, n, d, d, 0)
             kd = torch.from_numpy(k).to(device)
             ed = torch.from_numpy(e).to(device)
             plan = bg.Plan(n, d, d, bg.FIELD_C64, 0, bg.MOSTLY_MINUS)
@@ -467,7 +473,8 @@ def mixed_workload(args, device):
             "batch_autotuned": {"ms_per_step": ms_tuned / steps, "value": n_pts / (ms_tuned / steps / 1e3),
                                 "config": {"tile_points": best.tile_points,
                                            "fp_blocks_per_sm": best.fp_blocks_per_sm,
-                                           "c64_blocks_per_sm": best.c64_blocks_per_sm},
+                                           "c64_blocks_per_sm": best.c64_blocks_per_sm,
+                                           "lanes_max_items": best.lanes_max_items},
                                 "describe": tuned.describe()},
             "unit": "amplitudes/s", "steps": steps}
 

@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define BG_VERSION 1
+#define BG_VERSION 2
 
 typedef enum {
     BG_OK = 0,
@@ -303,6 +303,9 @@ typedef struct {
     int tile_points;          /* work items per tile; 0 = 1024                     */
     int fp_blocks_per_sm;     /* residency cap of the F_p kernel; 0 = all that fit */
     int c64_blocks_per_sm;    /* residency cap of the complex kernel; 0 = all      */
+    int lanes_max_items;      /* groups of at most this many work items run one
+                                 item per group of 4 or 8 lanes (the lane-group
+                                 body of bg_eval's small batches); 0 = none       */
 } bg_batch_config;
 
 typedef struct bg_batch bg_batch;   /* opaque: tables in the workspace + a graph */
@@ -330,7 +333,8 @@ bg_status bg_batch_describe(const bg_batch* batch, char* buf, size_t len);
 bg_status bg_batch_destroy(bg_batch* batch);
 
 /* bg_batch_autotune -- time every candidate configuration (tile size x
- * residency caps of the two kernels) on this batch, `reps` launches each on
+ * residency caps of the two kernels x lane groups for small groups or not)
+ * on this batch, `reps` launches each on
  * `stream`, and return the fastest in *best (and its time per launch in
  * *best_ms if non-NULL).  Needs bg_batch_workspace_size(groups, n, NULL)
  * bytes of workspace.  Synchronises the stream.  When the environment

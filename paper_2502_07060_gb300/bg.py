@@ -52,7 +52,7 @@ class BgGroup(ctypes.Structure):
 class BgBatchConfig(ctypes.Structure):
     """bg_batch_config of include/bg.h."""
     _fields_ = [("tile_points", ctypes.c_int), ("fp_blocks_per_sm", ctypes.c_int),
-                ("c64_blocks_per_sm", ctypes.c_int)]
+                ("c64_blocks_per_sm", ctypes.c_int), ("lanes_max_items", ctypes.c_int)]
 
 
 def load_library(path=None):

@@ -29,6 +29,7 @@ using bgk::kBlockFpBatch;
 constexpr int kTuneTiles[] = {256, 1024, 4096};     // autotune candidates (points per tile)
 constexpr int kTuneFpCaps[] = {0, 4, 2};            // F_p blocks per SM (0 = all that fit)
 constexpr int kTuneC64Caps[] = {0, 3, 2, 1};        // C64 blocks per SM
+constexpr int kTuneLanes[] = {0, 2048};             // lane groups for groups of at most this many items
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -104,9 +105,12 @@ bg_status build_layout(const bg_group* groups, int n_groups, const bg_batch_conf
         bgd.variant = 2 * bgk::batch_pair_index(D, DS) + (int)pl->metric +
                       (pl->field == BG_FIELD_C64_REAL ? bgk::kBatchVariants : 0);
         bgd.fp = pl->fpo;
+        const int64_t items_g = g.E * pl->H;
+        bgd.lanes = (cfg && cfg->lanes_max_items > 0 && items_g <= cfg->lanes_max_items) ? (DS <= 4 ? 4 : 8) : 0;
         const int gidx = (int)fpart.groups.size();
         fpart.groups.push_back(bgd);
         fpart.words = std::max(fpart.words, bgk::Geometry{pl->n - 1}.words(D, DS));
+        fpart.words = std::max(fpart.words, bgk::LaneGeometry{pl->n - 1}.words());
         const int64_t items = g.E * pl->H;
         for (int64_t first = 0; first < items; first += tile) {
             bgk::BatchTile t;
@@ -343,17 +347,17 @@ std::string tune_key(const bg_group* groups, int n_groups, int dev) {
 }
 
 // A cached result for `key` in the file `path` (lines "key tile fp_cap
-// c64_cap ms"; the last matching line wins).
+// c64_cap lanes_max_items ms"; the last matching line wins).
 bool tune_lookup(const char* path, const std::string& key, bg_batch_config* cfg, double* ms) {
     FILE* f = fopen(path, "r");
     if (!f) return false;
     char k[64];
-    int t, fc, cc;
+    int t, fc, cc, ln;
     double m;
     bool found = false;
-    while (fscanf(f, "%63s %d %d %d %lf", k, &t, &fc, &cc, &m) == 5) {
-        if (key == k && t > 0 && fc >= 0 && cc >= 0) {
-            *cfg = bg_batch_config{t, fc, cc};
+    while (fscanf(f, "%63s %d %d %d %d %lf", k, &t, &fc, &cc, &ln, &m) == 6) {
+        if (key == k && t > 0 && fc >= 0 && cc >= 0 && ln >= 0) {
+            *cfg = bg_batch_config{t, fc, cc, ln};
             *ms = m;
             found = true;
         }
@@ -368,7 +372,8 @@ void tune_store(const char* path, const std::string& key, const bg_batch_config&
         bgi::log("autotune cache %s not writable", path);
         return;
     }
-    fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), cfg.tile_points, cfg.fp_blocks_per_sm, cfg.c64_blocks_per_sm, ms);
+    fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), cfg.tile_points, cfg.fp_blocks_per_sm, cfg.c64_blocks_per_sm,
+            cfg.lanes_max_items, ms);
     fclose(f);
 }
 
@@ -395,8 +400,8 @@ bg_status bg_batch_autotune(const bg_group* groups, int n_groups, void* workspac
         double ms = 0;
         if (tune_lookup(cache, key, best, &ms)) {
             if (best_ms) *best_ms = ms;
-            bgi::log("autotune cache hit %s: tile %d, caps %d/%d, %.3f ms", key.c_str(), best->tile_points,
-                     best->fp_blocks_per_sm, best->c64_blocks_per_sm, ms);
+            bgi::log("autotune cache hit %s: tile %d, caps %d/%d, lanes %d, %.3f ms", key.c_str(), best->tile_points,
+                     best->fp_blocks_per_sm, best->c64_blocks_per_sm, best->lanes_max_items, ms);
             return BG_OK;
         }
     }
@@ -409,8 +414,9 @@ bg_status bg_batch_autotune(const bg_group* groups, int n_groups, void* workspac
     bg_status result = BG_OK;
     for (int t : kTuneTiles)
         for (int fc : kTuneFpCaps)
-            for (int cc : kTuneC64Caps) {
-                bg_batch_config cfg{t, fc, cc};
+            for (int cc : kTuneC64Caps)
+              for (int ln : kTuneLanes) {
+                bg_batch_config cfg{t, fc, cc, ln};
                 bg_batch* b = nullptr;
                 bg_status st = bg_batch_create(groups, n_groups, &cfg, workspace, workspace_bytes, &b);
                 if (st != BG_OK) { result = st; continue; }
@@ -430,13 +436,13 @@ bg_status bg_batch_autotune(const bg_group* groups, int n_groups, void* workspac
                     best_t = per;
                     *best = cfg;
                 }
-            }
+              }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best_t < 0) return result != BG_OK ? result : bgi::fail(BG_ERR_CUDA, "no candidate ran");
     if (best_ms) *best_ms = best_t;
-    bgi::log("autotune: tile %d, caps %d/%d, %.3f ms", best->tile_points, best->fp_blocks_per_sm,
-             best->c64_blocks_per_sm, best_t);
+    bgi::log("autotune: tile %d, caps %d/%d, lanes %d, %.3f ms", best->tile_points, best->fp_blocks_per_sm,
+             best->c64_blocks_per_sm, best->lanes_max_items, best_t);
     if (!key.empty()) tune_store(cache, key, *best, best_t);
     return BG_OK;
 }

@@ -1,7 +1,10 @@
 // bg_batch.cuh -- persistent kernel for a batch of uneven groups: points of
 // different n, d, D_s and metric (one number type per kernel) in one launch.
 //
-// The batch is cut into tiles of consecutive work items of one group.  Tiles
+// The batch is cut into tiles of consecutive work items of one group.  A
+// group runs one work item per thread, or -- when the configuration asks for
+// it and the group is small -- one per group of 4 or 8 lanes (the lane-group
+// body of bg_lanes.cuh, on the same table region).  Tiles
 // are ordered by decreasing cost per point (longest-processing-time first, so
 // the cheap tiles fill the tail) and handed out by one atomic counter: each
 // resident block takes the next tile, runs the recursion of bg_compact.cuh on
@@ -12,6 +15,7 @@
 #include <cstdint>
 
 #include "bg_compact.cuh"
+#include "bg_lanes.cuh"
 
 namespace bgk {
 
@@ -27,6 +31,7 @@ __host__ __device__ constexpr int batch_pair_index(int D, int DS) {
 struct BatchGroup {
     CompactArgs args;       // n, E, H, S, dims, device buffers (ws unused)
     int variant;            // 2 * batch_pair_index(D, D_s) + metric (+ kBatchVariants)
+    int lanes;              // 0: one work item per thread; 4 or 8: per group of lanes
     FpOps fp;               // Montgomery constants (F_p groups)
 };
 
@@ -90,6 +95,37 @@ __device__ __forceinline__ void batch_item(const F& f, const CompactArgs& a, int
     batch_dims<F, BLOCK>(f, a, variant, tab, u);
 }
 
+// The lane-group body (bg_lanes.cuh) for a group of small size: one work
+// item per group of L lanes, the lane table in the block's global region.
+template <class F, int L, int M, int BLOCK>
+__device__ __noinline__ void batch_lanes_point(const F f, const CompactArgs* a, unsigned char* tab, int64_t u) {
+    lanes_point<F, L, M, BLOCK>(f, *a, tab, u);
+}
+
+template <class F, int BLOCK>
+__device__ __forceinline__ void batch_lanes_dims(const F& f, const CompactArgs& a, int L, int metric,
+                                                 unsigned char* tab, int64_t u) {
+    if (L == 4) {
+        if (metric) batch_lanes_point<F, 4, 1, BLOCK>(f, &a, tab, u);
+        else batch_lanes_point<F, 4, 0, BLOCK>(f, &a, tab, u);
+    } else {
+        if (metric) batch_lanes_point<F, 8, 1, BLOCK>(f, &a, tab, u);
+        else batch_lanes_point<F, 8, 0, BLOCK>(f, &a, tab, u);
+    }
+}
+
+template <class F, int BLOCK>
+__device__ __forceinline__ void batch_lanes_item(const F& f, const CompactArgs& a, int variant, int L,
+                                                 unsigned char* tab, int64_t u) {
+    if constexpr (!F::kIsFp) {
+        if (variant >= kBatchVariants) {
+            batch_lanes_dims<C64ROps, BLOCK>(C64ROps{}, a, L, (variant - kBatchVariants) & 1, tab, u);
+            return;
+        }
+    }
+    batch_lanes_dims<F, BLOCK>(f, a, L, variant & 1, tab, u);
+}
+
 template <class F, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1) bg_batch_kernel(const BatchArgs a) {
     using T = typename F::T;
@@ -105,8 +141,15 @@ __global__ void __launch_bounds__(BLOCK, 1) bg_batch_kernel(const BatchArgs a) {
         const BatchGroup& gd = a.groups[td.group];
         const F f = batch_field<F>(gd);
         const int variant = gd.variant;
-        for (int k = threadIdx.x; k < td.count; k += BLOCK)
-            batch_item<F, BLOCK>(f, gd.args, variant, tab, td.first + k);
+        if (gd.lanes) {                        // groups of L lanes share one work item
+            const int L = gd.lanes;
+            for (int k = threadIdx.x / L; k < td.count; k += BLOCK / L)
+                batch_lanes_item<F, BLOCK>(f, gd.args, variant, L, reinterpret_cast<unsigned char*>(tab),
+                                           td.first + k);
+        } else {
+            for (int k = threadIdx.x; k < td.count; k += BLOCK)
+                batch_item<F, BLOCK>(f, gd.args, variant, tab, td.first + k);
+        }
     }
 }
 

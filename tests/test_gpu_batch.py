@@ -104,7 +104,8 @@ def test_batch_config_variants_and_autotune():
     from paper_2502_07060_gb300 import bg
     groups = [_group(bg, *s, seed=80 + i) for i, s in enumerate(SPECS[:7])]
     refs = [plan.eval(k, e)[0] for plan, k, e, _, _ in groups]
-    for cfg in (bg.BgBatchConfig(256, 2, 1), bg.BgBatchConfig(4096, 0, 3)):
+    # explicit configurations: caps, tile sizes, and every group on lane groups
+    for cfg in (bg.BgBatchConfig(256, 2, 1, 0), bg.BgBatchConfig(4096, 0, 3, 0), bg.BgBatchConfig(1024, 0, 0, 1 << 20)):
         for _, _, _, out, st in groups:
             out.zero_()
             st.fill_(7)
@@ -115,7 +116,7 @@ def test_batch_config_variants_and_autotune():
             assert torch.equal(out, ref)
         _check_oracle(groups)
     best, ms = bg.Batch.autotune(groups, reps=1)
-    assert best.tile_points in (256, 1024, 4096) and ms > 0
+    assert best.tile_points in (256, 1024, 4096) and best.lanes_max_items in (0, 2048) and ms > 0
     for _, _, _, out, st in groups:
         out.zero_()
         st.fill_(7)
@@ -137,14 +138,38 @@ def test_autotune_cache(tmp_path, monkeypatch):
     lines = cache.read_text().split("\n")
     lines = [l for l in lines if l.strip()]
     assert len(lines) == 1
-    key, t, fc, cc, m = lines[0].split()
-    assert (int(t), int(fc), int(cc)) == (best.tile_points, best.fp_blocks_per_sm, best.c64_blocks_per_sm)
+    key, t, fc, cc, ln, m = lines[0].split()
+    assert (int(t), int(fc), int(cc), int(ln)) == (best.tile_points, best.fp_blocks_per_sm, best.c64_blocks_per_sm,
+                                                   best.lanes_max_items)
     again, ms2 = bg.Batch.autotune(groups, reps=1)
-    assert (again.tile_points, again.fp_blocks_per_sm, again.c64_blocks_per_sm) == \
-        (best.tile_points, best.fp_blocks_per_sm, best.c64_blocks_per_sm)
+    assert (again.tile_points, again.fp_blocks_per_sm, again.c64_blocks_per_sm, again.lanes_max_items) == \
+        (best.tile_points, best.fp_blocks_per_sm, best.c64_blocks_per_sm, best.lanes_max_items)
     assert abs(ms2 - float(m)) < 1e-5
     assert len([l for l in cache.read_text().split("\n") if l.strip()]) == 1
     other = [_group(bg, *s, seed=130 + i) for i, s in enumerate(SPECS[3:5])]
     bg.Batch.autotune(other, reps=1)
     keys = [l.split()[0] for l in cache.read_text().split("\n") if l.strip()]
     assert len(keys) == 2 and keys[0] != keys[1]
+
+
+def test_small_groups_on_lane_groups():
+    """A batch of small groups (every configuration of the uneven workload, a
+    few dozen points each) with lane groups for groups up to 2048 items: every
+    group equals the oracle, and equals the same batch run one item per
+    thread bit for bit over F_p."""
+    import torch
+    from paper_2502_07060_gb300 import bg
+    specs = [(f, n, d, d, m, 20 + 7 * i) for i, (f, n, d, m) in enumerate(
+        [(f, n, d, m) for f in ("fp", "c64", "c64r") for n in (4, 7, 12) for d in (4, 6, 8) for m in (0, 1)])]
+    groups = [_group(bg, *s[:5], s[5], seed=300 + i) for i, s in enumerate(specs)]
+    lanes = bg.Batch(groups, config=bg.BgBatchConfig(256, 0, 0, 2048))
+    lanes.launch()
+    torch.cuda.synchronize()
+    _check_oracle(groups)
+    got = [out.clone() for _, _, _, out, _ in groups]
+    plain = bg.Batch(groups, config=bg.BgBatchConfig(256, 0, 0, 0))
+    plain.launch()
+    torch.cuda.synchronize()
+    for (plan, _, _, out, _), g in zip(groups, got):
+        if plan.field == bg.FIELD_FP:
+            assert torch.equal(out, g)
