@@ -319,7 +319,9 @@ bg_status bg_batch_workspace_size(const bg_group* groups, int n_groups,
 /* bg_batch_create -- order, tile, upload the tables into `workspace` (device,
  * 256-byte aligned, owned by the batch until bg_batch_destroy) and capture the
  * graph.  The groups' buffers are bound into the graph: each launch evaluates
- * whatever they hold.  cfg may be NULL (defaults).  Synchronous. */
+ * whatever they hold.  cfg may be NULL: 256-point tiles, the F_p kernel held
+ * to 2 blocks per SM when the batch also has complex groups, lane groups for
+ * groups of at most 2048 work items.  Synchronous. */
 bg_status bg_batch_create(const bg_group* groups, int n_groups, const bg_batch_config* cfg,
                           void* workspace, size_t workspace_bytes, bg_batch** out);
 

@@ -26,7 +26,7 @@ namespace {
 
 using bgk::kBlockC64Batch;
 using bgk::kBlockFpBatch;
-constexpr int kTuneTiles[] = {256, 1024, 4096};     // autotune candidates (points per tile)
+constexpr int kTuneTiles[] = {64, 256, 1024, 4096}; // autotune candidates (points per tile)
 constexpr int kTuneFpCaps[] = {0, 4, 2};            // F_p blocks per SM (0 = all that fit)
 constexpr int kTuneC64Caps[] = {0, 3, 2, 1};        // C64 blocks per SM
 constexpr int kTuneLanes[] = {0, 2048};             // lane groups for groups of at most this many items
@@ -112,11 +112,15 @@ bg_status build_layout(const bg_group* groups, int n_groups, const bg_batch_conf
         fpart.words = std::max(fpart.words, bgk::Geometry{pl->n - 1}.words(D, DS));
         fpart.words = std::max(fpart.words, bgk::LaneGeometry{pl->n - 1}.words());
         const int64_t items = g.E * pl->H;
-        for (int64_t first = 0; first < items; first += tile) {
+        // a group on lane groups takes tiles of one pass of a block (block / L
+        // items): its items have the longest latency per block, so they spread
+        // over as many blocks as possible
+        const int gtile = bgd.lanes ? (pl->field == BG_FIELD_FP ? kBlockFpBatch : kBlockC64Batch) / bgd.lanes : tile;
+        for (int64_t first = 0; first < items; first += gtile) {
             bgk::BatchTile t;
             t.group = gidx;
             t.first = first;
-            t.count = (int)std::min<int64_t>(tile, items - first);
+            t.count = (int)std::min<int64_t>(gtile, items - first);
             fpart.tiles.push_back(t);
         }
     }
@@ -199,6 +203,19 @@ bg_status bg_batch_create(const bg_group* groups, int n_groups, const bg_batch_c
     bg_batch* b = new (std::nothrow) bg_batch();
     if (!b) return bgi::fail(BG_ERR_NOMEM, "host allocation failed");
     b->device = dev;
+    // cfg NULL: the configuration the autotuner picked most often on GB300 --
+    // small tiles, the F_p kernel held to 2 blocks per SM when complex groups
+    // share the GPU (their FP64 work then overlaps the integer work), lane
+    // groups for small groups (measured on the 54-group uneven batch:
+    // 83.1 ms against 92.5 ms with 1024-point tiles and no caps)
+    bg_batch_config dflt{256, 0, 0, 2048};
+    if (!cfg && groups) {
+        bool fp = false, cx = false;
+        for (int gi = 0; gi < n_groups; ++gi)
+            if (groups[gi].plan && groups[gi].E > 0) (groups[gi].plan->field == BG_FIELD_FP ? fp : cx) = true;
+        if (fp && cx) dflt.fp_blocks_per_sm = 2;
+        cfg = &dflt;
+    }
     bg_status st = build_layout(groups, n_groups, cfg, dev, &b->L);
     if (st != BG_OK) { delete b; return st; }
     if (!workspace || workspace_bytes < b->L.bytes || (uintptr_t)workspace % 256) {
