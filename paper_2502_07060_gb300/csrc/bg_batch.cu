@@ -178,15 +178,18 @@ bg_status bg_batch_workspace_size(const bg_group* groups, int n_groups, const bg
         *bytes = L.bytes;
         return BG_OK;
     }
-    // no configuration: the largest workspace any autotune candidate needs
+    // no configuration: the largest workspace any autotune candidate (or the
+    // default configuration of bg_batch_create) needs; uncapped residency is
+    // the largest grid
     size_t mx = 0;
-    for (int t : kTuneTiles) {
-        bg_batch_config c{t, 0, 0};
-        Layout L;
-        bg_status st = build_layout(groups, n_groups, &c, dev, &L);
-        if (st != BG_OK) return st;
-        mx = std::max(mx, L.bytes);
-    }
+    for (int t : kTuneTiles)
+        for (int ln : kTuneLanes) {
+            bg_batch_config c{t, 0, 0, ln};
+            Layout L;
+            bg_status st = build_layout(groups, n_groups, &c, dev, &L);
+            if (st != BG_OK) return st;
+            mx = std::max(mx, L.bytes);
+        }
     *bytes = mx;
     return BG_OK;
 }

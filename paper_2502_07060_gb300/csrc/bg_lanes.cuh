@@ -13,11 +13,12 @@
 // and gaps are the compact kernel's (same regrouped sum, same Sec. 2.2
 // recursion), run in lock step by the L lanes of a point.
 //
-// Each lane keeps its own words in shared memory -- its component of every
-// current and prefix sum, and its copy of every per-range scalar (SA, 1/P^2,
-// which all lanes of a point compute identically) -- at [word][thread], so no
-// lane ever reads another lane's shared memory and only the shuffles
-// exchange data.  Per lane: NJ + (N+1) + 2 NS words (75 at n = 8).
+// Each lane keeps its own words in shared memory (bg_lanes_kernel) or in its
+// block's global table region (the uneven-batch kernel) -- its component of
+// every current and prefix sum, and its copy of every per-range scalar (SA,
+// 1/P^2, which all lanes of a point compute identically) -- at
+// [word][thread], so no lane ever reads another lane's words and only the
+// shuffles exchange data.  Per lane: NJ + (N+1) + 2 NS words (75 at n = 8).
 //
 // F_p: the same Montgomery levels as FpOps; a contraction sums the lanes'
 // products (L = 4: four products below 2^64; L = 8: each product first taken
