@@ -82,7 +82,8 @@ def test_batch_matches_per_group_eval():
             refs.append(None)
             continue
         refs.append(plan.eval(k, e))
-    batch = bg.Batch(groups)
+    # one item per thread everywhere: bit for bit the per-group bg_eval
+    batch = bg.Batch(groups, config=bg.BgBatchConfig(256, 0, 0, 0))
     for rep in range(2):                               # counters are reset per launch
         for _, _, _, out, st in groups:
             out.zero_()
@@ -97,6 +98,18 @@ def test_batch_matches_per_group_eval():
         if rep == 0:
             _check_oracle(groups)
     assert "tiles" in batch.describe()
+    # the default configuration (lane groups for the small groups): the oracle,
+    # and bit for bit over F_p
+    default = bg.Batch(groups)
+    for _, _, _, out, st in groups:
+        out.zero_()
+        st.fill_(7)
+    default.launch()
+    torch.cuda.synchronize()
+    _check_oracle(groups)
+    for (plan, k, _, out, st), ref in zip(groups, refs):
+        if ref is not None and plan.field == bg.FIELD_FP:
+            assert torch.equal(out, ref[0]) and torch.equal(st, ref[1])
 
 
 def test_batch_config_variants_and_autotune():
