@@ -4,7 +4,8 @@ F_p: bit-exact against the C oracle (itself pinned against the exact Python
 oracle).  C64: |A_gpu - A_ref| <= 1e-10 max(|A_ref|, S_pt) (reading G8) with
 A_ref the double-double evaluation of the C oracle (pinned against mpmath);
 on the few points where plain FP64 cannot reach 1e-10 (ill-conditioned
-points, measured by the literal FP64 oracle's own error) the bound is 8x that
+points, measured by the literal FP64 oracle's own error over leg orderings
+and over inputs moved by one rounding) the bound is 8x that
 FP64 noise floor, and the share of such points is bounded.  Sizes span several
 thread blocks and a ragged tail; both shared-memory and global-scratch table
 placements are exercised.
@@ -125,11 +126,23 @@ def c64_tolerance(k, eps, metric, hi, lo, spt=None):
     double-double value, widened only where FP64 itself cannot reach it: to 8x
     the FP64 noise floor nu_pt, the largest error of the literal FP64 oracle
     over three cyclic orderings of the legs (A is cyclically symmetric, so the
-    orderings differ only in rounding).  Returns (tol, fraction widened)."""
+    orderings differ only in rounding) and over two copies of the inputs with
+    every real component moved by one unit roundoff (relative 2^-53, seeded
+    random signs: the spread of A under the rounding of its inputs, i.e. the
+    point's conditioning).  Returns (tol, fraction widened)."""
     scale = np.abs(hi) if spt is None else np.maximum(np.abs(hi), spt)
     nu = np.zeros(len(hi))
     for r in range(3):
         a, _ = C.amp_c64(np.roll(k, -r, axis=1), np.roll(eps, -r, axis=1), metric)
+        nu = np.maximum(nu, np.abs((a - hi) - lo))
+    rng = np.random.default_rng(20250207)
+
+    def moved(x):
+        def part(v):
+            return v * (1.0 + rng.choice([-1.0, 1.0], size=v.shape) * 2.0 ** -53)
+        return np.ascontiguousarray(part(x.real) + 1j * part(x.imag))
+    for _ in range(2):
+        a, _ = C.amp_c64(moved(k), moved(eps), metric)
         nu = np.maximum(nu, np.abs((a - hi) - lo))
     tol = np.maximum(TOL_C64 * scale, 8.0 * nu)
     widened = float(np.mean(8.0 * nu > TOL_C64 * scale))
@@ -158,7 +171,7 @@ def test_c64_within_tolerance(n, d, Ds, metric):
     _, rst = C.amp_c64(k, eps, metric)
     out, st, plan = run_c64(k, eps, metric)
     assert np.array_equal(st, rst)
-    check_c64(out, k, eps, metric, max_widened=0.02)   # measured: at most 2 of 157 points
+    check_c64(out, k, eps, metric, max_widened=0.02)   # measured: at most 3 of 157 points
 
 
 def test_c64_metric_workload_strict():
