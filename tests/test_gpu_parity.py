@@ -301,6 +301,52 @@ def test_full_size_metric_workload_sampled():
     check_c64(outc[sample], kc[sample], ec[sample], 0, max_widened=0.0)
 
 
+def _resident_threads(plan):
+    import torch
+    desc = dict(x.split("=", 1) for x in plan.describe().split() if "=" in x)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return int(desc["blocks_per_sm"]) * int(desc["block"]) * sms
+
+
+@pytest.mark.parametrize("field,table", [("fp", None), ("fp", "split"), ("c64", None), ("c64r", None)])
+def test_several_points_per_thread(field, table):
+    """Batches of a little over two resident waves with a ragged last warp: the
+    table region of a thread serves several points in turn (its lines are
+    dropped from L2 between points), so points after the first of a thread,
+    and the last partial warp, are checked against the oracle."""
+    import torch
+    bg = _bg()
+    n, d = 8, 6
+    with _env(BG_TABLE=table):
+        if field == "fp":
+            plan = bg.Plan(n, d, d, bg.FIELD_FP, P, 0)
+        else:
+            plan = bg.Plan(n, d, d, bg.FIELD_C64_REAL if field == "c64r" else bg.FIELD_C64, 0, 0)
+    if table:
+        assert "table=" + table in plan.describe()
+    else:
+        assert "table=global" in plan.describe()
+    R = _resident_threads(plan)
+    E = 2 * R + 77
+    rng = np.random.default_rng(7)
+    sample = np.unique(np.concatenate([rng.choice(np.arange(R, E), 1500, replace=False), np.arange(E - 96, E)]))
+    if field == "fp":
+        k, e = G.fp_batch(2100, E, n, d, d, P, 0)
+        out, st = plan.eval(_dev_u32(k), _dev_u32(e))
+        torch.cuda.synchronize()
+        ref, rst = C.amp_fp(k[sample], e[sample], P, 0)
+        assert np.array_equal(out.cpu().numpy().view(np.uint32)[sample], ref)
+        assert np.array_equal(st.cpu().numpy()[sample], rst)
+    else:
+        k, e = G.c64_batch(2101, E, n, d, d, 0)
+        kd = torch.from_numpy(np.ascontiguousarray(k.real)).cuda() if field == "c64r" else _dev_c(k)
+        out, st = plan.eval(kd, _dev_c(e))
+        torch.cuda.synchronize()
+        _, rst = C.amp_c64(k[sample], e[sample], 0)
+        assert np.array_equal(st.cpu().numpy()[sample], rst)
+        check_c64(out.cpu().numpy()[sample], k[sample], e[sample], 0, max_widened=0.01)
+
+
 @pytest.mark.parametrize("field,pinned", [("fp", True), ("fp", False), ("c64", True)])
 def test_eval_host_pipeline_matches_device_eval(field, pinned):
     """bg_eval_host (host buffers, chunked and double buffered) returns exactly
