@@ -10,7 +10,8 @@
 // resident block takes the next tile, runs the recursion of bg_compact.cuh on
 // its items (the (D, D_s, metric) body the group needs), and repeats until the
 // queue is empty.  The tables of a block live in a global scratch region sized
-// for the largest group of the batch.  Blocks never wait for one another.
+// for the largest group of the batch; a one-item-per-thread item drops its
+// table lines from L2 when it is done.  Blocks never wait for one another.
 #pragma once
 #include <cstdint>
 
@@ -62,6 +63,9 @@ __device__ __forceinline__ C64Ops batch_field<C64Ops>(const BatchGroup&) { retur
 template <class F, int D, int DS, int M, int BLOCK>
 __device__ __noinline__ void batch_point(const F f, const CompactArgs* a, typename F::T* tab, int64_t u) {
     bg_point<F, D, DS, M, BLOCK>(f, *a, tab, u);
+    // the item's table is dead: drop its lines from L2 (bg_compact.cuh)
+    const Geometry g{a->n - 1};
+    discard_point_table<F, D, DS, BLOCK, true>(g, tab, tab + g.off_k(DS) * BLOCK);
 }
 
 template <class F, int BLOCK>

@@ -671,7 +671,10 @@ __device__ __noinline__ void discard_point_table(const Geometry g, const typenam
                                                  const typename F::T* aux) {
     using T = typename F::T;
     using TK = typename F::TK;
-    if (__activemask() != 0xffffffffu) return;
+    // every entry point hands the kernels 256-byte aligned scratch; a table
+    // that is not 128-byte aligned is never discarded (the lines would not
+    // be the warp's own)
+    if (__activemask() != 0xffffffffu || (reinterpret_cast<uintptr_t>(tab) & 127u) != 0) return;
     __syncwarp();                                   // every lane is done with the point
     const int lane = threadIdx.x & 31, w0 = threadIdx.x & ~31;
     constexpr int ES = sizeof(T), KS = sizeof(TK);
