@@ -521,6 +521,12 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
         C mom_c = f.czero();
         TK mom_v[DL];
         bool mom_pending = false;
+        // The gap-pair loop unrolled twice gives the scheduler two pairs of
+        // loads and contractions at a time.  Measured on the F_p kernel with
+        // D = D_s = 6: 0.9 % faster at the same 94-96 registers; at other
+        // dimensions and for the complex kernels the unrolled loop takes up
+        // to 40 more registers (fewer resident blocks), so it stays rolled.
+        constexpr int kGapUnroll = (F::kIsFp && !MIXED && D == 6 && DS == 6) ? 2 : 1;
 #pragma unroll 1
         for (int b = 0; b < m - 1; ++b) {
             const int lenA = b + 1, lenB = m - 1 - b;   // [i, i+b] | [i+b+1, j]
@@ -557,7 +563,7 @@ __device__ __forceinline__ void bg_point(const F& f, const CompactArgs& a, typen
             int off_pq = i * SLOTB, step_pq = N * SLOTB;
             int off_iq = off_es, step_iq = (N - b + 1) * SLOTB;
             int q = 0;
-#pragma unroll 1
+#pragma unroll(kGapUnroll)
             for (; q + 1 < b; q += 2) {
                 T pa0[DSL], pa1[DSL], in0[DSL], in1[DSL];
                 IO::template load_live<DS, DSL>(at(off_pq, 1), pa0);
