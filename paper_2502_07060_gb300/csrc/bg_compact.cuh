@@ -671,10 +671,9 @@ __device__ __forceinline__ void discard_rows(const void* base, int rows, int row
     }
 }
 
-// Not inlined: its addresses then hold no registers across the point loop.
 template <class F, int D, int DS, int BLOCK, bool AUX>
-__device__ __noinline__ void discard_point_table(const Geometry g, const typename F::T* tab,
-                                                 const typename F::T* aux) {
+__device__ __forceinline__ void discard_point_table_body(const Geometry& g, const typename F::T* tab,
+                                                         const typename F::T* aux) {
     using T = typename F::T;
     using TK = typename F::TK;
     // every entry point hands the kernels 256-byte aligned scratch; a table
@@ -682,6 +681,9 @@ __device__ __noinline__ void discard_point_table(const Geometry g, const typenam
     // be the warp's own)
     if (__activemask() != 0xffffffffu || (reinterpret_cast<uintptr_t>(tab) & 127u) != 0) return;
     __syncwarp();                                   // every lane is done with the point
+    // opaque to the compiler, so that the line addresses are formed here and
+    // not hoisted out of the point loop into registers held across the points
+    asm volatile("" : "+l"(tab), "+l"(aux));
     const int lane = threadIdx.x & 31, w0 = threadIdx.x & ~31;
     constexpr int ES = sizeof(T), KS = sizeof(TK);
     const T* sa = aux + (g.off_sa(D, DS) - g.off_k(DS)) * BLOCK + w0;     // SA and 1/P^2, 2 ns rows
@@ -699,6 +701,25 @@ __device__ __noinline__ void discard_point_table(const Geometry g, const typenam
         }
     }
     __syncwarp();                                   // before any lane writes the next point's table
+}
+
+// The same as a function of its own (not inlined).  Which of the two keeps
+// the point loop faster depends on the kernel's register pressure (measured on
+// GB300, F_p): inlined, the D = D_s = 6 kernel ran 3-5 % slower at n = 8..12;
+// called, the D_s = 8 kernel ran 2-8 % slower (n = 6..12), and inlined it ran
+// as fast as without any discard.  The complex kernels measured the same
+// either way and call it.
+template <class F, int D, int DS, int BLOCK, bool AUX>
+__device__ __noinline__ void discard_point_table_call(const Geometry g, const typename F::T* tab,
+                                                      const typename F::T* aux) {
+    discard_point_table_body<F, D, DS, BLOCK, AUX>(g, tab, aux);
+}
+
+template <class F, int D, int DS, int BLOCK, bool AUX>
+__device__ __forceinline__ void discard_point_table(const Geometry& g, const typename F::T* tab,
+                                                    const typename F::T* aux) {
+    if constexpr (F::kIsFp && DS == 8) discard_point_table_body<F, D, DS, BLOCK, AUX>(g, tab, aux);
+    else discard_point_table_call<F, D, DS, BLOCK, AUX>(g, tab, aux);
 }
 
 template <class F, int D, int DS, int METRIC, int BLOCK, int PLACE, bool MIXED>
