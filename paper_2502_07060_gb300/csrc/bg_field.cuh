@@ -118,32 +118,20 @@ struct FpOps {
         constexpr int nneg = []() { int c = 0; for (int mu = 0; mu < D; ++mu) c += msign<METRIC>(mu) < 0; return c; }();
         constexpr int flip = (nneg * 2 > D) ? -1 : 1;   // sign that is NOT negated
         static_assert(D <= 8, "two groups of four products at most");
-        // Up to six products are summed as a tree (pairs, then pairs of
-        // pairs): the sums are exact, and the dependency chain is two
-        // additions deep instead of four multiply-adds (measured 0.5 % on the
-        // n=8, d=6 kernel).  Eight are summed as two chains of four: the tree
-        // keeps eight 64-bit products live, and the d=8 kernels measured 1-8 %
-        // slower with it.
-        uint64_t s0 = 0, s1 = 0;
-        if constexpr (D <= 6) {
-            uint64_t pr[8];
+        // products summed as a tree (pairs, then pairs of pairs): the sums are
+        // exact, and the dependency chain is two additions deep instead of
+        // four multiply-adds (measured 0.5 % on the n=8, d=6 kernel, the same
+        // time as two chains of four at d=8)
+        uint64_t pr[8];
 #pragma unroll
-            for (int mu = 0; mu < D; ++mu) {
-                const uint32_t x = (msign<METRIC>(mu) == flip) ? a[mu] : (p - a[mu]);
-                pr[mu] = static_cast<uint64_t>(x) * b[mu];
-            }
-#pragma unroll
-            for (int mu = D; mu < 8; ++mu) pr[mu] = 0;
-            s0 = (pr[0] + pr[1]) + (pr[2] + pr[3]);
-            s1 = pr[4] + pr[5];
-        } else {
-#pragma unroll
-            for (int mu = 0; mu < D; ++mu) {
-                const uint32_t x = (msign<METRIC>(mu) == flip) ? a[mu] : (p - a[mu]);
-                if (mu < 4) s0 += static_cast<uint64_t>(x) * b[mu];
-                else s1 += static_cast<uint64_t>(x) * b[mu];
-            }
+        for (int mu = 0; mu < D; ++mu) {
+            const uint32_t x = (msign<METRIC>(mu) == flip) ? a[mu] : (p - a[mu]);
+            pr[mu] = static_cast<uint64_t>(x) * b[mu];
         }
+#pragma unroll
+        for (int mu = D; mu < 8; ++mu) pr[mu] = 0;
+        const uint64_t s0 = (pr[0] + pr[1]) + (pr[2] + pr[3]);
+        const uint64_t s1 = (pr[4] + pr[5]) + (pr[6] + pr[7]);
         uint32_t r;
         if constexpr (D <= 4) {
             r = fold(redc(redc_full(s0)));             // flip * dot, level 0, [0, p)
