@@ -9,7 +9,6 @@
 //   cadd / csub / cdbl / cneg     coefficient arithmetic
 //   acc1<K>(acc, c, v)            acc[0..K) += c v
 //   acc2<K>(acc, c1, v1, c2, v2)  acc[0..K) += c1 v1 + c2 v2
-//   acc4<K>(acc, c1, v1, .., c4, v4)  four terms
 //   finish(acc, inv) -> T[]       J = R / P^2 from the accumulator
 //   amplitude(acc, eps_last)      A = eps_n . R_top
 //   TK, kdot / kkdot / kacc1 / kacc2: the same for momentum components
@@ -170,14 +169,6 @@ struct FpOps {
         for (int mu = 0; mu < K; ++mu)
             add96(acc[mu], static_cast<uint64_t>(c1) * v1[mu] + static_cast<uint64_t>(c2) * v2[mu]);
     }
-    template <int K>
-    __device__ __forceinline__ void acc4(A* acc, C c1, const T* v1, C c2, const T* v2, C c3, const T* v3, C c4,
-                                         const T* v4) const {
-#pragma unroll
-        for (int mu = 0; mu < K; ++mu)
-            add96(acc[mu], static_cast<uint64_t>(c1) * v1[mu] + static_cast<uint64_t>(c2) * v2[mu] +
-                               static_cast<uint64_t>(c3) * v3[mu] + static_cast<uint64_t>(c4) * v4[mu]);
-    }
     // 96-bit sum -> divided by R^2 (two Montgomery steps), in [0, 2p): redc_full of
     // the low word shifts the sum down by 2^32 (it stays far below p 2^32:
     // a range sums fewer than 2^8 products, a contraction eight), then one redc
@@ -310,12 +301,6 @@ struct C64Ops {
     __device__ __forceinline__ void acc2(A* acc, C c1, const T* v1, C c2, const T* v2) const {
         acc1<K>(acc, c1, v1);
         acc1<K>(acc, c2, v2);
-    }
-    template <int K>
-    __device__ __forceinline__ void acc4(A* acc, C c1, const T* v1, C c2, const T* v2, C c3, const T* v3, C c4,
-                                         const T* v4) const {
-        acc2<K>(acc, c1, v1, c2, v2);
-        acc2<K>(acc, c3, v3, c4, v4);
     }
     template <int K>
     __device__ __forceinline__ void finish(const A* acc, T inv, T* out) const {
