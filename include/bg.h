@@ -234,8 +234,11 @@ bg_status bg_host_staging_size(const bg_plan* plan, int64_t chunk, size_t* bytes
  * ones such as complex FP64 at n = 8 -- one kernel instead reads the inputs
  * and writes the results in place, with no copies and the workspace at the
  * start of `staging`; light, large batches (F_p) keep the copies, which move
- * data faster than the kernels' scattered loads.  Results are identical on
- * both paths.  Asynchronous: the host buffers hold the results once `stream`
+ * data faster than the kernels' scattered loads.  The rate of those loads
+ * over the host link is measured once per device, on the first such batch
+ * larger than 64 MiB (a probe kernel reads 32 MiB of page-locked memory;
+ * freeing it waits for the device, so that first call may wait for work
+ * already queued).  Results are identical on both paths.  Asynchronous: the host buffers hold the results once `stream`
  * reaches the call.  Host buffers should be page-locked (pageable memory
  * works but the copies serialise).
  *
@@ -369,7 +372,9 @@ bg_status bg_batch_autotune(const bg_group* groups, int n_groups, void* workspac
  *   - page-locked host memory mapped into the device's address space (as
  *     cudaHostAlloc / cudaMallocHost give under unified addressing), also
  *     used in place: the kernel reads the inputs and writes the results over
- *     the host link, without copy-engine transfers;
+ *     the host link, without copy-engine transfers (unless the request is
+ *     large and light per point; the decision of bg_eval_host, with the
+ *     host-link rate measured when the server is created);
  *   - pageable host memory, staged through the arena by copies.
  * All buffers must stay valid, and inputs unchanged, until bg_serve_wait
  * returns.  Every result equals what bg_eval gives for the request alone.
@@ -455,9 +460,11 @@ bg_status bg_debug_bounds_report(int* checked, uint64_t* first_violation);
  * 64 MiB, or batches whose arithmetic per point hides the link traffic), 0
  * when copies should move them; *ops = the field multiplications per
  * amplitude of the literal recursion that the estimate uses.  Pure host
- * arithmetic for a 152-SM GB300 (the library's own decision scales the
- * kernels' rates by the plan device's SM count): needs no device.  BG_ERR_INVALID_ARG for arguments out of the
- * ranges of bg_plan_create, H < 1, E < 0 or NULL outputs.
+ * arithmetic for a 152-SM GB300 with in-place reads at 100 GB/s (the
+ * library's own decision scales the kernels' rates by the plan device's SM
+ * count and uses the read rate measured on the device): needs no device.
+ * BG_ERR_INVALID_ARG for arguments out of the ranges of bg_plan_create,
+ * H < 1, E < 0 or NULL outputs.
  */
 bg_status bg_debug_in_place_pays(bg_field field, int n, int d, int D_s, int H, int64_t E,
                                  size_t host_bytes, int* in_place, double* ops);

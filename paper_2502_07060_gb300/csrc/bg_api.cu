@@ -220,22 +220,28 @@ double ops_per_amplitude(int n, int d, int D) {
 
 // The kernels sustain about 4.3e12 (F_p), 2.5e11 (complex, real momenta) and
 // 1.9e11 (complex momenta) of these multiplications per second (n = 8, d = 6
-// on a GB300), and their per-thread loads of mapped host memory reach about
-// 100 GB/s over the host link: in place pays while the batch needs at most
-// 80 GB/s of it.  At n = 8, d = 6 that keeps F_p batches (about 350 GB/s)
-// on copies and takes complex ones (about 60 GB/s) in place.
-bool in_place_pays_for(int field, int n, int d, int Ds, int H, int64_t E, size_t host_bytes, double sm_scale) {
+// on a GB300), and their per-thread loads of mapped host memory reach
+// link_bytes_per_s over the host link (about 100 GB/s on a GB300 host): in
+// place pays while the batch needs at most 80 % of that.  At n = 8, d = 6
+// that keeps F_p batches (about 350 GB/s) on copies and takes complex ones
+// (about 60 GB/s) in place.
+bool in_place_pays_for(int field, int n, int d, int Ds, int H, int64_t E, size_t host_bytes, double sm_scale,
+                       double link_bytes_per_s) {
     if (host_bytes <= kInPlaceBytes) return true;
     const double rate = sm_scale * (field == BG_FIELD_FP ? 4.3e12 : field == BG_FIELD_C64_REAL ? 2.5e11 : 1.9e11);
     const double seconds = (double)E * H * ops_per_amplitude(n, d, Ds) / rate;
-    return (double)host_bytes <= 80e9 * seconds;
+    return (double)host_bytes <= 0.8 * link_bytes_per_s * seconds;
 }
 
-// The rates above were measured on a 152-SM GB300; a device with another SM
-// count scales them (the kernels are bound by per-SM pipes).
+// The compute rates above were measured on a 152-SM GB300; a device with
+// another SM count scales them (the kernels are bound by per-SM pipes).  The
+// host-link rate is measured on the device itself (mapped_read_rate), since
+// it differed from host to host.
 bool in_place_pays(const bg_plan* plan, int64_t E, size_t host_bytes) {
+    if (host_bytes <= kInPlaceBytes) return true;
     const double sm_scale = plan->sm_count > 0 ? plan->sm_count / 152.0 : 1.0;
-    return in_place_pays_for(plan->field, plan->n, plan->d, plan->Ds, plan->H, E, host_bytes, sm_scale);
+    return in_place_pays_for(plan->field, plan->n, plan->d, plan->Ds, plan->H, E, host_bytes, sm_scale,
+                             mapped_read_rate());
 }
 
 int round_dim(int x) { return x <= 4 ? 4 : (x <= 6 ? 6 : 8); }
@@ -401,7 +407,7 @@ bg_status bg_debug_in_place_pays(bg_field field, int n, int d, int D_s, int H, i
         (field != BG_FIELD_C64 && field != BG_FIELD_FP && field != BG_FIELD_C64_REAL))
         return fail(BG_ERR_INVALID_ARG, "bad argument to bg_debug_in_place_pays");
     *ops = bgi::ops_per_amplitude(n, d, D_s);
-    *in_place = bgi::in_place_pays_for((int)field, n, d, D_s, H, E, host_bytes, 1.0) ? 1 : 0;
+    *in_place = bgi::in_place_pays_for((int)field, n, d, D_s, H, E, host_bytes, 1.0, bgi::kMappedReadRateDefault) ? 1 : 0;
     return BG_OK;
 }
 

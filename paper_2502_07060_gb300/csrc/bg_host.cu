@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include <mutex>
 
@@ -63,6 +64,64 @@ bg_status pipe_for(int dev, HostPipe** out) {
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Probe of the host link as the kernels use it when they read page-locked
+// host memory in place: each thread reads whole rows of 384 bytes (one point's
+// F_p inputs at n = 8, d = 6) with streaming 16-byte loads, consecutive
+// threads consecutive rows.  `sink` keeps the loads from being removed.
+constexpr int kProbeRowVec = 24;            // 16-byte vectors per row
+__global__ void host_link_probe(const uint4* __restrict__ rows, int64_t n_rows, unsigned* sink) {
+    unsigned acc = 0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows; r += (int64_t)gridDim.x * blockDim.x) {
+        const uint4* q = rows + r * kProbeRowVec;
+#pragma unroll 4
+        for (int v = 0; v < kProbeRowVec; ++v) {
+            const uint4 x = __ldcs(q + v);
+            acc ^= x.x + x.y + x.z + x.w;
+        }
+    }
+    if (acc == 0x9e3779b9u) sink[0] = acc;  // practically never taken
+}
+
+// Bytes per second of in-place reads over the host link, measured on the
+// current device: 32 MiB of page-locked memory read twice by four resident
+// blocks of 128 threads per SM (the compute kernels' residency), timed with
+// events after one warm-up pass.  0 when the probe cannot run.
+double probe_mapped_read_rate(int dev) {
+    constexpr size_t kBytes = size_t(32) << 20;
+    const int64_t n_rows = (int64_t)(kBytes / (kProbeRowVec * sizeof(uint4)));
+    void* host = nullptr;
+    unsigned* sink = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double rate = 0;
+    int sms = 0;
+    void* dptr = nullptr;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaHostAlloc(&host, kBytes, cudaHostAllocMapped) == cudaSuccess &&
+        cudaHostGetDevicePointer(&dptr, host, 0) == cudaSuccess && cudaMalloc(&sink, sizeof(unsigned)) == cudaSuccess &&
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        memset(host, 1, kBytes);
+        const int blocks = 4 * sms;
+        host_link_probe<<<blocks, 128, 0, st>>>(static_cast<const uint4*>(dptr), n_rows, sink);
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 2; ++rep)
+            host_link_probe<<<blocks, 128, 0, st>>>(static_cast<const uint4*>(dptr), n_rows, sink);
+        cudaEventRecord(e1, st);
+        float ms = 0;
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0)
+            rate = 2.0 * (double)kBytes / (ms * 1e-3);
+    }
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (sink) cudaFree(sink);
+    if (host) cudaFreeHost(host);
+    cudaGetLastError();
+    return rate;
+}
+
 struct Slot {
     size_t k, eps, out, status;   // bytes per chunk of each buffer (256-rounded)
     size_t total() const { return k + eps + out + status; }
@@ -79,6 +138,33 @@ Slot slot_sizes(const bg_plan* pl, int64_t chunk) {
 }
 
 }  // namespace
+
+namespace bgi {
+
+// Measured once per device (the first large in-place decision, or a server's
+// creation), then cached.  The probe's cudaFreeHost waits for the device, so
+// the first call may wait for work already queued.
+double mapped_read_rate() {
+    static std::mutex mu;
+    static bool done[kMaxDevices] = {};
+    static double rate[kMaxDevices] = {};
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return kMappedReadRateDefault;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        done[dev] = true;
+        const double r = probe_mapped_read_rate(dev);
+        rate[dev] = r > 0 ? r : kMappedReadRateDefault;
+        log("device %d: in-place reads over the host link %.1f GB/s (%s)", dev, rate[dev] / 1e9,
+            r > 0 ? "measured" : "probe failed, default");
+    }
+    return rate[dev];
+}
+
+}  // namespace bgi
 
 extern "C" bg_status bg_host_staging_size(const bg_plan* plan, int64_t chunk, size_t* bytes) {
     if (!plan || !bytes || chunk < 1) return bgi::fail(BG_ERR_INVALID_ARG, "bad argument to bg_host_staging_size");

@@ -313,6 +313,7 @@ bg_status bg_serve_create(size_t budget_bytes, int max_inflight, bg_server** out
         return bgi::fail(BG_ERR_CUDA, "no current CUDA device");
     }
     s->budget = budget_bytes & ~(kGranule - 1);
+    bgi::mapped_read_rate();          // measured now, not in a submit while requests run
     if (bgi::fault(BG_FAULT_DEVICE_ALLOC) || cudaMalloc(&s->arena_mem, s->budget) != cudaSuccess) {
         cudaGetLastError();
         delete s;

@@ -44,3 +44,24 @@ def test_complex_real_momenta_large_batch_in_place():
     hk = torch.from_numpy(np.ascontiguousarray(k.real)).pin_memory()
     he = torch.from_numpy(e).pin_memory()
     _check(plan, hk, he, chunk=E // 4)
+
+
+def test_host_link_rate_is_measured():
+    """The in-place decision uses the rate of in-place reads over the host
+    link measured on the device (logged under BG_LOG when a server is
+    created): a plausible figure, reported as measured."""
+    import os
+    import re
+    import subprocess
+    import sys
+    code = ("import torch; from paper_2502_07060_gb300 import bg; torch.zeros(1, device='cuda'); "
+            "s = bg.Server(1 << 26, max_inflight=1); s.close()")
+    env = dict(os.environ, BG_LOG="1")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    m = re.search(r"in-place reads over the host link ([0-9.]+) GB/s \((\w+)", r.stderr)
+    assert m, r.stderr[-2000:]
+    assert m.group(2) == "measured"
+    assert 5.0 < float(m.group(1)) < 2000.0
