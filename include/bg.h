@@ -460,7 +460,7 @@ bg_status bg_debug_bounds_report(int* checked, uint64_t* first_violation);
  * 64 MiB, or batches whose arithmetic per point hides the link traffic), 0
  * when copies should move them; *ops = the field multiplications per
  * amplitude of the literal recursion that the estimate uses.  Pure host
- * arithmetic for a 152-SM GB300 with in-place reads at 100 GB/s (the
+ * arithmetic for a 152-SM GB300 with a host-link probe rate of 135 GB/s (the
  * library's own decision scales the kernels' rates by the plan device's SM
  * count and uses the read rate measured on the device): needs no device.
  * BG_ERR_INVALID_ARG for arguments out of the ranges of bg_plan_create,

@@ -220,17 +220,18 @@ double ops_per_amplitude(int n, int d, int D) {
 
 // The kernels sustain about 4.3e12 (F_p), 2.5e11 (complex, real momenta) and
 // 1.9e11 (complex momenta) of these multiplications per second (n = 8, d = 6
-// on a GB300), and their per-thread loads of mapped host memory reach
-// link_bytes_per_s over the host link (about 100 GB/s on a GB300 host): in
-// place pays while the batch needs at most 80 % of that.  At n = 8, d = 6
-// that keeps F_p batches (about 350 GB/s) on copies and takes complex ones
-// (about 60 GB/s) in place.
+// on a GB300).  link_bytes_per_s is the rate of the host-link probe
+// (mapped_read_rate); the kernels' own loads of mapped host memory, mixed
+// with their arithmetic, reach about three quarters of it (103 against 135
+// GB/s on a GB300 host), and in place pays while the batch needs at most 80 %
+// of that.  At n = 8, d = 6 that keeps F_p batches (about 350 GB/s) on copies
+// and takes complex ones (about 60 GB/s) in place.
 bool in_place_pays_for(int field, int n, int d, int Ds, int H, int64_t E, size_t host_bytes, double sm_scale,
                        double link_bytes_per_s) {
     if (host_bytes <= kInPlaceBytes) return true;
     const double rate = sm_scale * (field == BG_FIELD_FP ? 4.3e12 : field == BG_FIELD_C64_REAL ? 2.5e11 : 1.9e11);
     const double seconds = (double)E * H * ops_per_amplitude(n, d, Ds) / rate;
-    return (double)host_bytes <= 0.8 * link_bytes_per_s * seconds;
+    return (double)host_bytes <= 0.8 * 0.76 * link_bytes_per_s * seconds;
 }
 
 // The compute rates above were measured on a 152-SM GB300; a device with

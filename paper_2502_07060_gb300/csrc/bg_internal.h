@@ -101,10 +101,10 @@ constexpr size_t kInPlaceBytes = size_t(64) << 20;
 bool in_place_pays(const bg_plan* plan, int64_t E, size_t host_bytes);
 bool in_place_pays_for(int field, int n, int d, int Ds, int H, int64_t E, size_t host_bytes, double sm_scale,
                        double link_bytes_per_s);
-// Bytes per second that kernels reading page-locked host memory in place get
-// over the host link on the current device (measured once, bg_host.cu); the
-// default is the figure measured on a GB300 host.
-constexpr double kMappedReadRateDefault = 1.0e11;
+// Bytes per second of the host-link probe, reading page-locked host memory in
+// place on the current device (measured once, bg_host.cu); the default is the
+// figure measured on a GB300 host.
+constexpr double kMappedReadRateDefault = 1.35e11;
 double mapped_read_rate();
 double ops_per_amplitude(int n, int d, int D);
 int round_dim(int x);
