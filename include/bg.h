@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define BG_VERSION 2
+#define BG_VERSION 3
 
 typedef enum {
     BG_OK = 0,
@@ -304,7 +304,11 @@ typedef struct {
 
 typedef struct {
     int tile_points;          /* work items per tile; 0 = 1024                     */
-    int fp_blocks_per_sm;     /* residency cap of the F_p kernel; 0 = all that fit */
+    int fp_blocks_per_sm;     /* residency cap of the F_p kernel; 0 = all that fit.
+                                 The F_p kernel has two builds: caps 1-2 take the
+                                 one built for few resident blocks (up to 255
+                                 registers, two blocks fit), 0 and 3-4 the one
+                                 built for four (at most 128 registers)         */
     int c64_blocks_per_sm;    /* residency cap of the complex kernel; 0 = all      */
     int lanes_max_items;      /* groups of at most this many work items run one
                                  item per group of 4 or 8 lanes (the lane-group
@@ -322,9 +326,10 @@ bg_status bg_batch_workspace_size(const bg_group* groups, int n_groups,
 /* bg_batch_create -- order, tile, upload the tables into `workspace` (device,
  * 256-byte aligned, owned by the batch until bg_batch_destroy) and capture the
  * graph.  The groups' buffers are bound into the graph: each launch evaluates
- * whatever they hold.  cfg may be NULL: 256-point tiles, the F_p kernel held
- * to 2 blocks per SM when the batch also has complex groups, lane groups for
- * groups of at most 2048 work items.  Synchronous. */
+ * whatever they hold.  cfg may be NULL: 256-point tiles, lane groups for
+ * groups of at most 2048 work items, and the F_p kernel held to 2 blocks per
+ * SM when the batch also has complex groups or when most of its F_p work items
+ * run on lane groups (otherwise all that fit).  Synchronous. */
 bg_status bg_batch_create(const bg_group* groups, int n_groups, const bg_batch_config* cfg,
                           void* workspace, size_t workspace_bytes, bg_batch** out);
 

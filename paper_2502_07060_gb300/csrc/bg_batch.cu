@@ -27,7 +27,7 @@ namespace {
 using bgk::kBlockC64Batch;
 using bgk::kBlockFpBatch;
 constexpr int kTuneTiles[] = {64, 256, 1024, 4096}; // autotune candidates (points per tile)
-constexpr int kTuneFpCaps[] = {0, 4, 2};            // F_p blocks per SM (0 = all that fit)
+constexpr int kTuneFpCaps[] = {0, 3, 2};            // F_p blocks per SM (0 = all that fit; see fp_wide)
 constexpr int kTuneC64Caps[] = {0, 3, 2, 1};        // C64 blocks per SM
 constexpr int kTuneLanes[] = {0, 2048};             // lane groups for groups of at most this many items
 
@@ -52,6 +52,7 @@ struct FieldPart {
     std::vector<bgk::BatchTile> tiles;
     int words = 0;                      // largest table, elements per thread
     int blocks = 0;                     // grid
+    bool wide = true;                   // F_p: the kernel built for 1-2 blocks per SM
     size_t off_groups = 0, off_tiles = 0, off_tables = 0;
 };
 
@@ -59,6 +60,11 @@ struct Layout {
     FieldPart part[2];                  // [0] = complex (C64, C64_REAL), [1] = F_p
     size_t bytes = 0;
 };
+
+// The F_p kernel build a residency cap selects: caps of one or two blocks per
+// SM take the build for few blocks (no body spills much); no cap or three to
+// four blocks take the build for four (bg_batch.cuh).
+bool fp_wide(int cap) { return cap == 1 || cap == 2; }
 
 bg_status build_layout(const bg_group* groups, int n_groups, const bg_batch_config* cfg, int dev,
                        Layout* L) {
@@ -129,14 +135,15 @@ bg_status build_layout(const bg_group* groups, int n_groups, const bg_batch_conf
     for (int f = 0; f < 2; ++f) {
         FieldPart& P = L->part[f];
         if (P.tiles.empty()) continue;
-        const void* func = f ? bgk::batch_kernel_fp() : bgk::batch_kernel_c64();
+        const int cap = cfg ? (f ? cfg->fp_blocks_per_sm : cfg->c64_blocks_per_sm) : 0;
+        if (f) P.wide = fp_wide(cap);
+        const void* func = f ? bgk::batch_kernel_fp(P.wide) : bgk::batch_kernel_c64();
         const int block = f ? kBlockFpBatch : kBlockC64Batch;
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, block, 0) != cudaSuccess || occ < 1) {
             cudaGetLastError();
             return bgi::fail(BG_ERR_UNSUPPORTED, "batch kernel cannot be resident");
         }
-        const int cap = cfg ? (f ? cfg->fp_blocks_per_sm : cfg->c64_blocks_per_sm) : 0;
         if (cap > 0 && cap < occ) occ = cap;
         P.blocks = std::min<int64_t>((int64_t)occ * sms, (int64_t)P.tiles.size());
         const size_t elem = f ? 4 : 16;
@@ -216,7 +223,17 @@ bg_status bg_batch_create(const bg_group* groups, int n_groups, const bg_batch_c
         bool fp = false, cx = false;
         for (int gi = 0; gi < n_groups; ++gi)
             if (groups[gi].plan && groups[gi].E > 0) (groups[gi].plan->field == BG_FIELD_FP ? fp : cx) = true;
+        // F_p alone: the four-block build when most F_p work items run one per
+        // thread (large groups), the one-block build when most run on lane
+        // groups (small groups), as the autotuner picks on GB300
+        int64_t thread_items = 0, lane_items = 0;
+        for (int gi = 0; gi < n_groups; ++gi)
+            if (groups[gi].plan && groups[gi].E > 0 && groups[gi].plan->field == BG_FIELD_FP) {
+                const int64_t items = groups[gi].E * groups[gi].plan->H;
+                (items <= dflt.lanes_max_items ? lane_items : thread_items) += items;
+            }
         if (fp && cx) dflt.fp_blocks_per_sm = 2;
+        else if (fp) dflt.fp_blocks_per_sm = thread_items >= lane_items ? 0 : 2;
         cfg = &dflt;
     }
     bg_status st = build_layout(groups, n_groups, cfg, dev, &b->L);
@@ -274,7 +291,7 @@ bg_status bg_batch_create(const bg_group* groups, int n_groups, const bg_batch_c
         a.counter = reinterpret_cast<int*>(b->ws) + f;
         a.tables = b->ws + P.off_tables;
         a.words = P.words;
-        if (f) bgk::launch_batch_fp(a, P.blocks, s0);
+        if (f) bgk::launch_batch_fp(a, P.blocks, P.wide, s0);
         else bgk::launch_batch_c64(a, P.blocks, s1);
         err = cudaGetLastError();
     }
@@ -315,9 +332,10 @@ bg_status bg_batch_describe(const bg_batch* batch, char* buf, size_t len) {
     const FieldPart& F = batch->L.part[1];
     const FieldPart& C = batch->L.part[0];
     int w = snprintf(buf, len,
-                     "fp: groups=%zu tiles=%zu blocks=%d words=%d; c64: groups=%zu tiles=%zu blocks=%d "
-                     "words=%d; workspace=%zu",
-                     F.groups.size(), F.tiles.size(), F.blocks, F.words, C.groups.size(), C.tiles.size(),
+                     "fp: groups=%zu tiles=%zu blocks=%d words=%d kernel=%s; c64: groups=%zu tiles=%zu "
+                     "blocks=%d words=%d; workspace=%zu",
+                     F.groups.size(), F.tiles.size(), F.blocks, F.words, F.wide ? "wide" : "narrow",
+                     C.groups.size(), C.tiles.size(),
                      C.blocks, C.words, batch->L.bytes);
     if (w < 0 || (size_t)w >= len) return bgi::fail(BG_ERR_INVALID_ARG, "buffer too small");
     return BG_OK;

@@ -130,8 +130,13 @@ __device__ __forceinline__ void batch_lanes_item(const F& f, const CompactArgs& 
     batch_lanes_dims<F, BLOCK>(f, a, L, variant & 1, tab, u);
 }
 
-template <class F, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1) bg_batch_kernel(const BatchArgs a) {
+// MINB: resident blocks per SM the kernel is built for.  The bodies are
+// functions of their own, so the kernel's register count covers the largest
+// of them: built for one block (up to 255 registers) no body spills much;
+// built for four F_p blocks (at most 128 registers) some bodies spill but
+// twice as many warps hide the table loads' latency.
+template <class F, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) bg_batch_kernel(const BatchArgs a) {
     using T = typename F::T;
     __shared__ int s_tile;
     T* tab = reinterpret_cast<T*>(a.tables) + static_cast<size_t>(blockIdx.x) * a.words * BLOCK;
@@ -157,14 +162,17 @@ __global__ void __launch_bounds__(BLOCK, 1) bg_batch_kernel(const BatchArgs a) {
     }
 }
 
-// The two batch kernels are instantiated in translation units of their own
+// The batch kernels are instantiated in translation units of their own
 // (bg_batch_fp.cu, bg_batch_c64.cu): each holds the recursion body of every
-// (D, D_s, metric), and compiled apart they build in parallel.
+// (D, D_s, metric), and compiled apart they build in parallel.  F_p has two
+// builds: `wide` for one resident block per SM and up (two fit), the other
+// for four (kFpNarrowBlocks); complex has one (four 64-thread blocks fit).
 constexpr int kBlockFpBatch = 128;
 constexpr int kBlockC64Batch = 64;
-const void* batch_kernel_fp();     // the __global__ functions (occupancy queries)
+constexpr int kFpNarrowBlocks = 4;
+const void* batch_kernel_fp(bool wide);   // the __global__ functions (occupancy queries)
 const void* batch_kernel_c64();
-void launch_batch_fp(const BatchArgs& a, int blocks, cudaStream_t s);
+void launch_batch_fp(const BatchArgs& a, int blocks, bool wide, cudaStream_t s);
 void launch_batch_c64(const BatchArgs& a, int blocks, cudaStream_t s);
 
 }  // namespace bgk

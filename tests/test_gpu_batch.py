@@ -117,12 +117,16 @@ def test_batch_config_variants_and_autotune():
     from paper_2502_07060_gb300 import bg
     groups = [_group(bg, *s, seed=80 + i) for i, s in enumerate(SPECS[:7])]
     refs = [plan.eval(k, e)[0] for plan, k, e, _, _ in groups]
-    # explicit configurations: caps, tile sizes, and every group on lane groups
-    for cfg in (bg.BgBatchConfig(256, 2, 1, 0), bg.BgBatchConfig(4096, 0, 3, 0), bg.BgBatchConfig(1024, 0, 0, 1 << 20)):
+    # explicit configurations: caps (both F_p kernel builds: caps 1-2 the wide
+    # one, 0 and 3-4 the one for four blocks), tile sizes, every group on lane
+    # groups
+    for cfg in (bg.BgBatchConfig(256, 2, 1, 0), bg.BgBatchConfig(4096, 0, 3, 0), bg.BgBatchConfig(64, 3, 2, 0),
+                bg.BgBatchConfig(1024, 0, 0, 1 << 20), bg.BgBatchConfig(256, 1, 0, 1 << 20)):
         for _, _, _, out, st in groups:
             out.zero_()
             st.fill_(7)
         batch = bg.Batch(groups, config=cfg)
+        assert ("kernel=wide" in batch.describe()) == (cfg.fp_blocks_per_sm in (1, 2))
         batch.launch()
         torch.cuda.synchronize()
         for (plan, _, _, out, _), ref in zip(groups, refs):

@@ -44,7 +44,7 @@ def test_strerror_and_version(lib):
     lib.bg_strerror.restype = ctypes.c_char_p
     assert lib.bg_strerror(0) == b"success"
     assert lib.bg_strerror(1) == b"invalid argument"
-    assert lib.bg_version() == 2
+    assert lib.bg_version() == 3
 
 
 def _create(lib, n=8, d=6, Ds=6, field=1, p=2147483629, metric=0, S=1, H=1, assign=None):
