@@ -328,8 +328,8 @@ bg_status bg_batch_workspace_size(const bg_group* groups, int n_groups,
  * graph.  The groups' buffers are bound into the graph: each launch evaluates
  * whatever they hold.  cfg may be NULL: 256-point tiles, lane groups for
  * groups of at most 2048 work items, and the F_p kernel held to 2 blocks per
- * SM when the batch also has complex groups or when most of its F_p work items
- * run on lane groups (otherwise all that fit).  Synchronous. */
+ * SM when most of its F_p work items run on lane groups (otherwise all that
+ * fit).  Synchronous. */
 bg_status bg_batch_create(const bg_group* groups, int n_groups, const bg_batch_config* cfg,
                           void* workspace, size_t workspace_bytes, bg_batch** out);
 

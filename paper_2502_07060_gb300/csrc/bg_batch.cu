@@ -214,26 +214,27 @@ bg_status bg_batch_create(const bg_group* groups, int n_groups, const bg_batch_c
     if (!b) return bgi::fail(BG_ERR_NOMEM, "host allocation failed");
     b->device = dev;
     // cfg NULL: the configuration the autotuner picked most often on GB300 --
-    // small tiles, the F_p kernel held to 2 blocks per SM when complex groups
-    // share the GPU (their FP64 work then overlaps the integer work), lane
-    // groups for small groups (measured on the 54-group uneven batch:
-    // 83.1 ms against 92.5 ms with 1024-point tiles and no caps)
+    // small tiles, lane groups for small groups, and the F_p kernel build
+    // below (the 54-group uneven batch measured 92.5 ms with 1024-point tiles,
+    // no lane groups and a single F_p build)
     bg_batch_config dflt{256, 0, 0, 2048};
     if (!cfg && groups) {
-        bool fp = false, cx = false;
+        bool fp = false;
         for (int gi = 0; gi < n_groups; ++gi)
-            if (groups[gi].plan && groups[gi].E > 0) (groups[gi].plan->field == BG_FIELD_FP ? fp : cx) = true;
-        // F_p alone: the four-block build when most F_p work items run one per
-        // thread (large groups), the one-block build when most run on lane
-        // groups (small groups), as the autotuner picks on GB300
+            if (groups[gi].plan && groups[gi].E > 0 && groups[gi].plan->field == BG_FIELD_FP) fp = true;
+        // the F_p kernel built for four blocks per SM when most F_p work items
+        // run one per thread (large groups), the one for two when most run on
+        // lane groups (small groups): the autotuner's picks on GB300 (54-group
+        // batch of 77672 points per group: 82.6 ms against 83.2 ms with the
+        // two-block build; 27 F_p groups of 155344 points: 7.85 against
+        // 9.15 ms; of 512 points: 0.155 ms against 0.26 ms the other way)
         int64_t thread_items = 0, lane_items = 0;
         for (int gi = 0; gi < n_groups; ++gi)
             if (groups[gi].plan && groups[gi].E > 0 && groups[gi].plan->field == BG_FIELD_FP) {
                 const int64_t items = groups[gi].E * groups[gi].plan->H;
                 (items <= dflt.lanes_max_items ? lane_items : thread_items) += items;
             }
-        if (fp && cx) dflt.fp_blocks_per_sm = 2;
-        else if (fp) dflt.fp_blocks_per_sm = thread_items >= lane_items ? 0 : 2;
+        if (fp) dflt.fp_blocks_per_sm = thread_items >= lane_items ? 0 : 2;
         cfg = &dflt;
     }
     bg_status st = build_layout(groups, n_groups, cfg, dev, &b->L);
