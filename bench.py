@@ -418,19 +418,21 @@ def run_field(field, E, steps, warmup, rank, dist, device, seed, e2e=True):
 def mixed_workload(args, device):
     """Uneven batches over n = 4..12, d = D_s in {4, 6, 8} and both number
     types (54 groups): 2^22 points spread evenly (about 78 k per group), and
-    54 small groups of 512 points (the request mix of a serving step).  Each
-    times (a) 54 plain per-group bg_eval launches (which take the lane-group
-    kernel for small groups), (b) one graph launch of the batch with the
-    default configuration and (c) with the autotuned configuration (tile size,
-    residency caps, lane groups for small groups)."""
+    54 small groups of 512 points (the request mix of a serving step), and
+    2^22 points over the 27 F_p groups alone.  Each times (a) the plain
+    per-group bg_eval launches (which take the lane-group kernel for small
+    groups), (b) one graph launch of the batch with the default configuration
+    and (c) with the autotuned configuration (tile size, residency caps and
+    with them the F_p kernel build, lane groups for small groups)."""
     return {"large": _mixed(args, device, (1 << args.log2_points) // 54, 3000),
-            "small": _mixed(args, device, 512, 3100)}
+            "small": _mixed(args, device, 512, 3100),
+            "fp_large": _mixed(args, device, (1 << args.log2_points) // 27, 3200, fields=("fp",))}
 
 
-def _mixed(args, device, per, seed0):
+def _mixed(args, device, per, seed0, fields=("fp", "c64")):
     import torch
     from paper_2502_07060_gb300 import bg
-    specs = [(f, n, d) for f in ("fp", "c64") for n in range(4, 13) for d in (4, 6, 8)]
+    specs = [(f, n, d) for f in fields for n in range(4, 13) for d in (4, 6, 8)]
     groups = []
     for i, (f, n, d) in enumerate(specs):
         if f == "fp":
@@ -464,7 +466,8 @@ def _mixed(args, device, per, seed0):
     tuned = bg.Batch(groups, config=best)
     ms_tuned = time_steps(lambda: tuned.launch(stream), steps, args.warmup, stream, None, device)
     n_pts = per * len(specs)
-    return {"workload": "uneven batch: 54 groups (n = 4..12, d = D_s in {4, 6, 8}, F_p and C64), "
+    what = "F_p and C64" if len(fields) == 2 else "F_p"
+    return {"workload": f"uneven batch: {len(specs)} groups (n = 4..12, d = D_s in {{4, 6, 8}}, {what}), "
                         f"{per} points each, {n_pts} points per step",
             "plain_launches": {"ms_per_step": ms_plain / steps, "value": n_pts / (ms_plain / steps / 1e3),
                                "launches_per_step": len(specs)},
