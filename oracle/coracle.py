@@ -130,9 +130,3 @@ def amp_c64dd(k, eps, metric=0, nthreads=0):
     return hi, lo, st
 
 
-def rel_error(a, hi, lo, scale=None):
-    """|a - (hi + lo)| / scale (default |hi|), evaluated without losing the
-    low part: a - hi is exact when a and hi agree to within a factor 2."""
-    diff = (a - hi) - lo
-    s = np.abs(hi) if scale is None else scale
-    return np.abs(diff) / np.maximum(s, 1e-300)
