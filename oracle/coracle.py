@@ -128,5 +128,3 @@ def amp_c64dd(k, eps, metric=0, nthreads=0):
     hi = out[:, 0] + 1j * out[:, 2]
     lo = out[:, 1] + 1j * out[:, 3]
     return hi, lo, st
-
-
