@@ -343,7 +343,8 @@ bg_status bg_batch_describe(const bg_batch* batch, char* buf, size_t len);
 bg_status bg_batch_destroy(bg_batch* batch);
 
 /* bg_batch_autotune -- time every candidate configuration (tile size x
- * residency caps of the two kernels x lane groups for small groups or not)
+ * residency caps of the two kernels, which also choose the F_p kernel's
+ * build, x lane groups for small groups or not)
  * on this batch, `reps` launches each on
  * `stream`, and return the fastest in *best (and its time per launch in
  * *best_ms if non-NULL).  Needs bg_batch_workspace_size(groups, n, NULL)
