@@ -55,7 +55,7 @@ typedef enum {
     BG_OK = 0,
     BG_ERR_INVALID_ARG = 1,   /* null pointer, size or parameter out of range  */
     BG_ERR_UNSUPPORTED = 2,   /* valid request this build has no kernel for    */
-    BG_ERR_NOMEM = 3,         /* host or device allocation failed (plan only)  */
+    BG_ERR_NOMEM = 3,         /* host or device allocation failed              */
     BG_ERR_CUDA = 4,          /* CUDA runtime error (launch, device mismatch)  */
     BG_ERR_TIMEOUT = 5,       /* serving: the wait's deadline passed           */
     BG_ERR_BUSY = 6           /* serving: the server is shutting down          */
@@ -190,7 +190,8 @@ bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes);
  *              2 precondition broken (checked builds only, see below)
  *   workspace  device buffer of >= bg_workspace_size(plan, E) bytes, 256-byte
  *              aligned, or NULL when that size is 0; concurrent calls need
- *              distinct workspaces
+ *              distinct workspaces.  Scratch: its contents are undefined after
+ *              the call (the kernel drops its dead lines from L2 unwritten)
  *   stream     CUDA stream (0 = legacy default stream)
  *
  * Buffers must be on the device that is current at the call, and momenta,
@@ -238,9 +239,9 @@ bg_status bg_host_staging_size(const bg_plan* plan, int64_t chunk, size_t* bytes
  * over the host link is measured once per device, on the first such batch
  * larger than 64 MiB (a probe kernel reads 32 MiB of page-locked memory;
  * freeing it waits for the device, so that first call may wait for work
- * already queued).  Results are identical on both paths.  Asynchronous: the host buffers hold the results once `stream`
- * reaches the call.  Host buffers should be page-locked (pageable memory
- * works but the copies serialise).
+ * already queued).  Results are identical on both paths.  Asynchronous: the
+ * host buffers hold the results once `stream` reaches the call.  Host buffers
+ * should be page-locked (pageable memory works but the copies serialise).
  *
  *   momenta, eps  host arrays with the layouts of bg_eval
  *   out, status   host arrays [E][H] and [E] (status is required here)
@@ -344,10 +345,9 @@ bg_status bg_batch_destroy(bg_batch* batch);
 
 /* bg_batch_autotune -- time every candidate configuration (tile size x
  * residency caps of the two kernels, which also choose the F_p kernel's
- * build, x lane groups for small groups or not)
- * on this batch, `reps` launches each on
- * `stream`, and return the fastest in *best (and its time per launch in
- * *best_ms if non-NULL).  Needs bg_batch_workspace_size(groups, n, NULL)
+ * build, x lane groups for small groups or not) on this batch, `reps`
+ * launches each on `stream`, and return the fastest in *best (and its time
+ * per launch in *best_ms if non-NULL).  Needs bg_batch_workspace_size(groups, n, NULL)
  * bytes of workspace.  Synchronises the stream.  When the environment
  * variable BG_AUTOTUNE_CACHE names a file, a result stored there for the same
  * device, library version and group mix (each group's configuration and its
