@@ -591,12 +591,14 @@ def sweep_workload(args, device):
 
 def lanes_workload(args, device):
     """Small batches: one bg_eval launch on the one-point-per-thread kernel
-    (BG_LANES=0) against the lane-group kernel (BG_LANES=1) for E = 2^6 ..
-    2^15 points: F_p (p = 2^31 - 19) at n = 5, 8, 12 and complex FP64 (real
-    momenta at n = 8 and 12, complex momenta at n = 6), mostly-minus metric.
-    Each entry: 3 warm-up calls, then the mean of 20 CUDA-event-timed calls;
-    F_p results compared bit for bit, complex ones by their largest relative
-    difference."""
+    (BG_LANES=0) against the lane-group kernel with one point per group of
+    lanes (BG_LANES=1) and per team of the groups of a warp (BG_LANES=2) for
+    E = 2^6 .. 2^15 points: F_p (p = 2^31 - 19) at n = 5, 8, 12 and complex
+    FP64 (real momenta at n = 8 and 12, complex momenta at n = 6),
+    mostly-minus metric.  Each entry: 3 warm-up calls, then the mean of 20
+    CUDA-event-timed calls; F_p results compared bit for bit, complex ones by
+    their largest relative difference; `default` names the form bg_eval
+    takes without BG_LANES."""
     import torch
     from paper_2502_07060_gb300 import bg
     stream = torch.cuda.current_stream(device)
@@ -615,7 +617,7 @@ def lanes_workload(args, device):
             ed = torch.from_numpy(e).to(device)
             fid, p = (bg.FIELD_C64_REAL if field == "c64r" else bg.FIELD_C64), 0
         plans = {}
-        for v in ("0", "1", "auto"):
+        for v in ("0", "1", "2", "auto"):
             old = os.environ.get("BG_LANES")
             os.environ["BG_LANES"] = v
             plans[v] = bg.Plan(n, d, d, fid, p, bg.MOSTLY_MINUS)
@@ -623,12 +625,14 @@ def lanes_workload(args, device):
                 os.environ.pop("BG_LANES")
             else:
                 os.environ["BG_LANES"] = old
-        cut = int(dict(x.split("=", 1) for x in plans["auto"].describe().split())["lanes_max_items"])
+        desc = dict(x.split("=", 1) for x in plans["auto"].describe().split())
+        cut, tcut = int(desc["lanes_max_items"]), int(desc["team_max_items"])
         for lg in range(6, lgmax + 1):
             m = 1 << lg
-            row = {"field": field, "n": n, "d": d, "E": m, "default": "lanes" if m <= cut else "per_thread"}
+            row = {"field": field, "n": n, "d": d, "E": m,
+                   "default": "team" if m <= tcut else "lanes" if m <= cut else "per_thread"}
             outs = {}
-            for v, key in (("0", "per_thread_ms"), ("1", "lanes_ms")):
+            for v, key in (("0", "per_thread_ms"), ("1", "lanes_ms"), ("2", "team_ms")):
                 plan = plans[v]
                 out = torch.empty(m, dtype=ed.dtype, device=device)
                 st = torch.empty(m, dtype=torch.uint8, device=device)
@@ -637,14 +641,17 @@ def lanes_workload(args, device):
                 row[key] = time_steps(fn, 20, 3, stream, None, device) / 20
                 outs[v] = out
             if field == "fp":
-                row["bit_identical"] = bool(torch.equal(outs["0"], outs["1"]))
+                row["bit_identical"] = bool(torch.equal(outs["0"], outs["1"]) and torch.equal(outs["0"], outs["2"]))
             else:
                 row["max_rel_diff"] = float(((outs["0"] - outs["1"]).abs() / outs["0"].abs()).max().item())
+                row["team_equals_lanes"] = bool(torch.equal(outs["1"], outs["2"]))
             row["speedup"] = row["per_thread_ms"] / row["lanes_ms"]
+            row["team_speedup"] = row["per_thread_ms"] / row["team_ms"]
             rows.append(row)
         del kd, ed
         torch.cuda.empty_cache()
-    return {"workload": "small batches, one bg_eval launch: per-thread kernel against the lane-group kernel",
+    return {"workload": "small batches, one bg_eval launch: per-thread kernel against the lane-group kernel "
+                        "(one point per group, per team)",
             "unit": "ms per call", "rows": rows}
 
 

@@ -334,32 +334,53 @@ bg_status setup_states(bg_plan* pl, const int* radix, const char* tenv) {
 // short tables): BG_LANES unset takes it up to max(16 (complex) or 24 (F_p,
 // n >= 7) items per SM, half a resident wave of the lanes kernel);
 // BG_LANES=0 never, BG_LANES=1 always (when the plan has one).
-bg_status setup_lanes(bg_plan* pl) {
-    const int L = round_dim(pl->Ds) <= 4 ? 4 : 8;
+// The entry of the lanes kernel with L lanes per group and G groups per
+// point, its shared memory and resident blocks per SM; false (entry cleared)
+// when the plan's tables do not fit.
+bool lanes_variant(bg_plan* pl, int L, int G, const bgk::LanesEntry** entry, size_t* smem_out, int* occ_out) {
+    *entry = nullptr;
     for (const auto& e : bgi::lanes_registry())
-        if (e.field == (int)pl->field && e.L == L && e.metric == (int)pl->metric) pl->lentry = &e;
-    if (!pl->lentry) return BG_OK;
-    const size_t smem = (size_t)bgk::LaneGeometry{pl->n - 1}.words() * pl->lentry->block * pl->lentry->elem_bytes;
+        if (e.field == (int)pl->field && e.L == L && e.G == G && e.metric == (int)pl->metric) *entry = &e;
+    if (!*entry) return false;
+    const size_t smem = (size_t)bgk::LaneGeometry{pl->n - 1}.words() * ((*entry)->block / G) * (*entry)->elem_bytes;
     int occ = 0;
-    if (smem > 227 * 1024 || bgi::ensure_smem_limit(pl->lentry->func, pl->device, smem) != BG_OK ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pl->lentry->func, pl->lentry->block, smem) !=
-            cudaSuccess ||
+    if (smem > 227 * 1024 || bgi::ensure_smem_limit((*entry)->func, pl->device, smem) != BG_OK ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (*entry)->func, (*entry)->block, smem) != cudaSuccess ||
         occ < 1) {
         cudaGetLastError();
         g_last_error.clear();
-        pl->lentry = nullptr;            // the compact kernel serves every size
-        return BG_OK;
+        *entry = nullptr;                // the compact kernel serves every size
+        return false;
     }
-    pl->lanes_smem = smem;
-    pl->lanes_blocks_per_sm = occ;
+    *smem_out = smem;
+    *occ_out = occ;
+    return true;
+}
+
+// One point per team (a warp of G = 32 / L groups evaluating the ranges of
+// each length in parallel) shortens a point's recursion further but takes
+// four to eight times the lanes per point: it serves batches up to one
+// resident wave of teams.  BG_LANES=2 takes the team form always.
+bg_status setup_lanes(bg_plan* pl) {
+    const int L = round_dim(pl->Ds) <= 4 ? 4 : 8;
+    if (!lanes_variant(pl, L, 1, &pl->lentry, &pl->lanes_smem, &pl->lanes_blocks_per_sm)) return BG_OK;
+    lanes_variant(pl, L, 32 / L, &pl->tentry, &pl->team_smem, &pl->team_blocks_per_sm);
     const char* env = getenv("BG_LANES");
-    if (env && strcmp(env, "0") == 0) pl->lanes_max_items = 0;
-    else if (env && strcmp(env, "1") == 0) pl->lanes_max_items = INT64_MAX;
-    else {
-        const int64_t wave = (int64_t)occ * pl->sm_count * (pl->lentry->block / pl->lentry->L);
+    if (env && strcmp(env, "0") == 0) {
+        pl->lanes_max_items = 0;
+    } else if (env && strcmp(env, "1") == 0) {
+        pl->lanes_max_items = INT64_MAX;
+    } else if (env && strcmp(env, "2") == 0) {
+        pl->lanes_max_items = INT64_MAX;
+        pl->team_max_items = pl->tentry ? INT64_MAX : 0;
+    } else {
+        const int64_t wave = (int64_t)pl->lanes_blocks_per_sm * pl->sm_count * (pl->lentry->block / L);
         const int64_t per_sm = pl->field == BG_FIELD_FP ? 24 : 16;
         pl->lanes_max_items = (pl->field == BG_FIELD_FP && pl->n < 7) ? 0
                             : std::max(per_sm * pl->sm_count, wave / 2);
+        if (pl->tentry && pl->lanes_max_items > 0)
+            pl->team_max_items = std::min(pl->lanes_max_items,
+                                          (int64_t)pl->team_blocks_per_sm * pl->sm_count * (pl->tentry->block / 32));
     }
     return BG_OK;
 }
@@ -650,14 +671,16 @@ bool uses_lanes(const bg_plan* plan, int64_t select_items) {
 }
 
 bg_status launch_lanes(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
-                       uint8_t* status, int dev, cudaStream_t stream) {
-    const bgk::LanesEntry* le = plan->lentry;
+                       uint8_t* status, int dev, cudaStream_t stream, int64_t select_items) {
+    const bool team = plan->tentry && select_items <= plan->team_max_items;
+    const bgk::LanesEntry* le = team ? plan->tentry : plan->lentry;
+    const size_t smem = team ? plan->team_smem : plan->lanes_smem;
     bg_status st;
-    if (dev != plan->device && (st = ensure_smem_limit(le->func, dev, plan->lanes_smem)) != BG_OK) return st;
+    if (dev != plan->device && (st = ensure_smem_limit(le->func, dev, smem)) != BG_OK) return st;
     const int64_t items = E * plan->H;
-    const int64_t ppb = le->block / le->L;
+    const int64_t ppb = le->block / (le->L * le->G);
     int64_t blocks = (items + ppb - 1) / ppb;
-    const int64_t cap = (int64_t)plan->lanes_blocks_per_sm * plan->sm_count;
+    const int64_t cap = (int64_t)(team ? plan->team_blocks_per_sm : plan->lanes_blocks_per_sm) * plan->sm_count;
     if (blocks > cap) blocks = cap;
     bgk::CompactArgs a;
     a.E = E; a.H = plan->H; a.S = plan->S; a.n = plan->n;
@@ -666,7 +689,7 @@ bg_status launch_lanes(const bg_plan* plan, int64_t E, const void* momenta, cons
     a.assign = plan->d_assign; a.ws = nullptr;
     a.four_d_legs = 0;
     a.violation = violation_word(dev);
-    le->launch(compact_params(plan), &a, dim3((unsigned)blocks), plan->lanes_smem, stream);
+    le->launch(compact_params(plan), &a, dim3((unsigned)blocks), smem, stream);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return fail(BG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(err));
     return BG_OK;
@@ -712,12 +735,13 @@ bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len) {
     int w = snprintf(buf, len,
                      "field=%s n=%d d=%d D_s=%d kernel=compact kernel_D=%d kernel_D_s=%d metric=%s "
                      "table=%s block=%d blocks_per_sm=%d smem=%zu words_per_thread=%d elem_bytes=%d "
-                     "four_dim_legs=0x%x lanes=%d lanes_max_items=%lld",
+                     "four_dim_legs=0x%x lanes=%d lanes_max_items=%lld team_max_items=%lld",
                      field_name(plan->field), plan->n, plan->d, plan->Ds, e->D, e->DS,
                      plan->metric == BG_METRIC_MOSTLY_MINUS ? "mostly_minus" : "alternating",
                      e->split ? "split" : e->global_table ? "global" : "shared", e->block, plan->blocks_per_sm,
                      plan->smem_bytes, plan->words, e->elem_bytes, plan->four_d_legs,
-                     plan->lentry ? plan->lentry->L : 0, (long long)plan->lanes_max_items);
+                     plan->lentry ? plan->lentry->L : 0, (long long)plan->lanes_max_items,
+                     (long long)plan->team_max_items);
     if (w < 0 || (size_t)w >= len) return fail(BG_ERR_INVALID_ARG, "buffer too small");
     return BG_OK;
 }
@@ -783,7 +807,8 @@ bg_status eval_impl(const bg_plan* plan, int64_t E, const void* momenta, const v
     }
     if (bgi::fault(BG_FAULT_LAUNCH)) return fail(BG_ERR_CUDA, "launch failed: injected fault");
     const int64_t items = E * plan->H;
-    if (bgi::uses_lanes(plan, select_items)) return bgi::launch_lanes(plan, E, momenta, eps, out, status, dev, stream);
+    if (bgi::uses_lanes(plan, select_items))
+        return bgi::launch_lanes(plan, E, momenta, eps, out, status, dev, stream, select_items);
     int64_t blocks = (items + e->block - 1) / e->block;
     const int64_t cap = e->global_table ? resident_blocks(plan) : resident_blocks(plan) * 256;
     if (blocks > cap) blocks = cap;

@@ -37,6 +37,12 @@ struct bg_plan {
     size_t lanes_smem = 0;
     int lanes_blocks_per_sm = 0;
     int64_t lanes_max_items = 0;
+    // the same kernel with one point per team (a warp of groups), for at most
+    // team_max_items work items (checked before lanes_max_items)
+    const bgk::LanesEntry* tentry = nullptr;
+    size_t team_smem = 0;
+    int team_blocks_per_sm = 0;
+    int64_t team_max_items = 0;
     // all S^n assignments with sub-current reuse (assign == NULL, H == S^n > 1)
     bool all_states = false;
     const bgk::StatesEntry* sentry = nullptr;
@@ -83,12 +89,14 @@ bg_status eval_part(const bg_plan* plan, int64_t E, const void* momenta, const v
                     uint8_t* status, void* workspace, size_t workspace_bytes, cudaStream_t stream,
                     int64_t batch_items);
 // Whether a batch of select_items work items runs on the plan's lane-group
-// kernel, and the device workspace for E points when the kernel is chosen by
-// select_items (bg_workspace_size: select_items = E * H).
+// kernel (one point per group or per team), and the device workspace for E
+// points when the kernel is chosen by select_items (bg_workspace_size:
+// select_items = E * H).
 bool uses_lanes(const bg_plan* plan, int64_t select_items);
-// One launch of the plan's lane-group kernel on E points (checked arguments).
+// One launch of the plan's lane-group kernel on E points (checked
+// arguments), one point per team when select_items allows it.
 bg_status launch_lanes(const bg_plan* plan, int64_t E, const void* momenta, const void* eps, void* out,
-                       uint8_t* status, int dev, cudaStream_t stream);
+                       uint8_t* status, int dev, cudaStream_t stream, int64_t select_items);
 size_t workspace_bytes(const bg_plan* plan, int64_t E, int64_t select_items);
 // True when `p` is page-locked host memory mapped into the device's address
 // space at the same address (the kernels can read and write it directly).

@@ -131,8 +131,16 @@ struct LaneGeometry {
     __host__ __device__ int words() const { return off_inv() + ns(); }
 };
 
-template <class F, int L, int METRIC, int BLOCK>
+// G = 1: one point per group of L lanes, each lane's words its own.  G > 1
+// (L * G = 32): one point per warp ("team"): the G groups of the warp evaluate
+// the ranges of each length in parallel (group gi takes the ranges starting
+// at i = gi, gi + G, ...), with one table per team shared by its groups --
+// component mu of every vector at the word of lane mu of the team -- and a
+// warp barrier between lengths; group 0 loads the inputs and forms the prefix
+// sums and the inverses alone (a serial chain either way).
+template <class F, int L, int METRIC, int BLOCK, int G = 1>
 __device__ __forceinline__ void lanes_point(const F& f, const CompactArgs& a, unsigned char* smem, int64_t u) {
+    static_assert(G == 1 || L * G == 32, "a team is one warp");
     using T = typename F::T;
     using C = typename F::C;
     using Acc = typename F::A;
@@ -147,15 +155,19 @@ __device__ __forceinline__ void lanes_point(const F& f, const CompactArgs& a, un
     const LaneGeometry lg{NLEG - 1};
     const Geometry g{NLEG - 1};
     const int N = lg.N;
-    // this lane's words: word w at [w][thread]
-    T* W = reinterpret_cast<T*>(smem) + t;
-    TK* KW = reinterpret_cast<TK*>(reinterpret_cast<T*>(smem) + lg.off_k() * BLOCK) + t;
+    // word w of this lane's table at [w][column]: the column is the thread
+    // (G = 1) or lane mu of the team (G > 1), BLOCK / G columns per word
+    constexpr int STRIDE = BLOCK / G;
+    const int gi = G > 1 ? (t / L) % G : 0;
+    const int col = G > 1 ? (t / 32) * L + mu : t;
+    T* W = reinterpret_cast<T*>(smem) + col;
+    TK* KW = reinterpret_cast<TK*>(reinterpret_cast<T*>(smem) + lg.off_k() * STRIDE) + col;
     const int NJ = lg.nj(), NSW = lg.ns();
     // word addressing of the four regions (checked in BG_CHECKED builds)
-    auto J = [&](int slot) -> T& { return W[checked_slot(a.violation, slot, NJ, 21) * BLOCK]; };
-    auto Kv = [&](int i) -> TK& { return KW[checked_slot(a.violation, i, N + 1, 22) * BLOCK]; };
-    auto SA = [&](int s) -> T& { return W[(lg.off_sa() + checked_slot(a.violation, s, NSW, 23)) * BLOCK]; };
-    auto IV = [&](int s) -> T& { return W[(lg.off_inv() + checked_slot(a.violation, s, NSW, 23)) * BLOCK]; };
+    auto J = [&](int slot) -> T& { return W[checked_slot(a.violation, slot, NJ, 21) * STRIDE]; };
+    auto Kv = [&](int i) -> TK& { return KW[checked_slot(a.violation, i, N + 1, 22) * STRIDE]; };
+    auto SA = [&](int s) -> T& { return W[(lg.off_sa() + checked_slot(a.violation, s, NSW, 23)) * STRIDE]; };
+    auto IV = [&](int s) -> T& { return W[(lg.off_inv() + checked_slot(a.violation, s, NSW, 23)) * STRIDE]; };
 
     int64_t e = u;
     int h = 0;
@@ -168,8 +180,10 @@ __device__ __forceinline__ void lanes_point(const F& f, const CompactArgs& a, un
 #else
     constexpr bool violated = false;
 #endif
-    // a1: this lane's components of the prefix sums and of the states
-    {
+    // a1: this lane's components of the prefix sums and of the states (in a
+    // team, group 0 alone: the other groups read them after the barrier)
+    const bool stage = G == 1 || gi == 0;
+    if (stage) {
         const kio_t* kp = static_cast<const kio_t*>(a.k) + e * NLEG * a.d_in;
         TK K = f.kzero();
         Kv(0) = K;
@@ -181,7 +195,7 @@ __device__ __forceinline__ void lanes_point(const F& f, const CompactArgs& a, un
     }
     T eL = f.zero();
 #pragma unroll 1
-    for (int l = 0; l < NLEG; ++l) {
+    for (int l = 0; l < (stage ? NLEG : 0); ++l) {
         const int s = (a.assign != nullptr) ? a.assign[h * NLEG + l] : 0;
         const io_t* ep = static_cast<const io_t*>(a.eps) + ((e * NLEG + l) * a.S + s) * a.ds_in;
         T v = f.zero();
@@ -203,7 +217,7 @@ __device__ __forceinline__ void lanes_point(const F& f, const CompactArgs& a, un
         else return lo.template dot<METRIC>(x, y, mu);
     };
 #pragma unroll 1
-    for (int m = 2; m < N; ++m) {
+    for (int m = 2; m < (stage ? N : 0); ++m) {
 #pragma unroll 1
         for (int i = 0; i + m - 1 < N; ++i) {
             const TK P = f.ksub(Kv(i + m), Kv(i));
@@ -212,7 +226,8 @@ __device__ __forceinline__ void lanes_point(const F& f, const CompactArgs& a, un
     }
     bool singular = false;
     const int NS = g.ns();
-    if constexpr (F::kIsFp) {
+    if (!stage) {
+    } else if constexpr (F::kIsFp) {
         T c = SA(0);
         IV(0) = c;
 #pragma unroll 1
@@ -237,99 +252,114 @@ __device__ __forceinline__ void lanes_point(const F& f, const CompactArgs& a, un
             IV(s) = f.inv_scalar(x);
         }
     }
-    // a4: ranges by right end, as in bg_compact.cuh
+    if constexpr (G > 1) __syncwarp();      // the team's staged words are visible
+
+    // a4: every range [i, i+m-1]; one point per group: by right end, as in
+    // bg_compact.cuh; a team: by length, the ranges of one length spread over
+    // the groups and a barrier before the next length reads them
     io_t result = f.zero_io();
+    auto range = [&](const int m, const int i) {
+        const TK Ki = Kv(i), Kj = Kv(i + m);
+        const TK KiKj = f.kadd(Ki, Kj), P = f.ksub(Kj, Ki);
+        Acc acc[1];
+        f.template acc_zero<1>(acc);
+        C sa = f.czero();
+        int ps = i, ss = g.jbase(m - 1) + i + 1, es = i - N;
 #pragma unroll 1
-    for (int jj = 1; jj < N; ++jj) {
+        for (int b = 0; b < m - 1; ++b) {
+            const int lenA = b + 1, lenB = m - 1 - b;
+            const T pb = J(ps), sf = J(ss);
+            const TK Kt = Kv(i + b + 1);
+            const C adj = lo.template dot<METRIC>(pb, sf, mu);
+            const C pa_jb = kdot(P, sf);
+            const C pb_ja = kdot(P, pb);
+            sa = f.cadd(sa, adj);
+            C csuf = f.cdbl(pb_ja);
+            if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(SA(ps - N)));
+            C cpre = f.cneg(f.cdbl(pa_jb));
+            if (lenB >= 2) cpre = f.csub(cpre, f.t_to_c(SA(ss - N)));
+            f.template acc2<1>(acc, csuf, &sf, cpre, &pb);
+            f.template kacc1<1>(acc, f.cdbl(adj), &Kt);
+            // gaps in pairs: two independent shuffle contractions in flight
+            int pq = i, dp = N, iq = es, di = N - b + 1;
+            int q = 0;
 #pragma unroll 1
-        for (int i = jj - 1; i >= 0; --i) {
-            const int m = jj - i + 1;
-            const TK Ki = Kv(i), Kj = Kv(i + m);
-            const TK KiKj = f.kadd(Ki, Kj), P = f.ksub(Kj, Ki);
-            Acc acc[1];
-            f.template acc_zero<1>(acc);
-            C sa = f.czero();
-            int ps = i, ss = g.jbase(m - 1) + i + 1, es = i - N;
-#pragma unroll 1
-            for (int b = 0; b < m - 1; ++b) {
-                const int lenA = b + 1, lenB = m - 1 - b;
-                const T pb = J(ps), sf = J(ss);
-                const TK Kt = Kv(i + b + 1);
-                const C adj = lo.template dot<METRIC>(pb, sf, mu);
-                const C pa_jb = kdot(P, sf);
-                const C pb_ja = kdot(P, pb);
-                sa = f.cadd(sa, adj);
-                C csuf = f.cdbl(pb_ja);
-                if (lenA >= 2) csuf = f.csub(csuf, f.t_to_c(SA(ps - N)));
-                C cpre = f.cneg(f.cdbl(pa_jb));
-                if (lenB >= 2) cpre = f.csub(cpre, f.t_to_c(SA(ss - N)));
-                f.template acc2<1>(acc, csuf, &sf, cpre, &pb);
-                f.template kacc1<1>(acc, f.cdbl(adj), &Kt);
-                // gaps in pairs: two independent shuffle contractions in flight
-                int pq = i, dp = N, iq = es, di = N - b + 1;
-                int q = 0;
-#pragma unroll 1
-                for (; q + 1 < b; q += 2) {
-                    const T pa0 = J(pq), in0 = J(iq);
-                    pq += dp; iq -= di;
-                    const T pa1 = J(pq), in1 = J(iq);
-                    pq += dp - 1; iq -= di + 1;
-                    dp -= 2; di += 2;
-                    const C g0 = f.cdbl(lo.template dot<METRIC>(pa0, sf, mu));
-                    const C g1 = f.cdbl(lo.template dot<METRIC>(pa1, sf, mu));
-                    f.template acc2<1>(acc, g0, &in0, g1, &in1);
-                }
-                if (q < b) {
-                    const T pa0 = J(pq), in0 = J(iq);
-                    const C g0 = f.cdbl(lo.template dot<METRIC>(pa0, sf, mu));
-                    f.template acc1<1>(acc, g0, &in0);
-                }
-                ps += N - b;
-                ss -= N - lenB + 1;
-                es += N - b + 1;
+            for (; q + 1 < b; q += 2) {
+                const T pa0 = J(pq), in0 = J(iq);
+                pq += dp; iq -= di;
+                const T pa1 = J(pq), in1 = J(iq);
+                pq += dp - 1; iq -= di + 1;
+                dp -= 2; di += 2;
+                const C g0 = f.cdbl(lo.template dot<METRIC>(pa0, sf, mu));
+                const C g1 = f.cdbl(lo.template dot<METRIC>(pa1, sf, mu));
+                f.template acc2<1>(acc, g0, &in0, g1, &in1);
             }
-            f.template kacc1<1>(acc, f.cneg(sa), &KiKj);
-            if (m < N) {
-                const int sidx = g.sbase(m) + i;
-                T Jn;
-                f.template finish<1>(acc, IV(sidx), &Jn);
-                J(g.jbase(m) + i) = Jn;
-                SA(sidx) = f.c_to_t(sa);
+            if (q < b) {
+                const T pa0 = J(pq), in0 = J(iq);
+                const C g0 = f.cdbl(lo.template dot<METRIC>(pa0, sf, mu));
+                f.template acc1<1>(acc, g0, &in0);
+            }
+            ps += N - b;
+            ss -= N - lenB + 1;
+            es += N - b + 1;
+        }
+        f.template kacc1<1>(acc, f.cneg(sa), &KiKj);
+        if (m < N) {
+            const int sidx = g.sbase(m) + i;
+            T Jn;
+            f.template finish<1>(acc, IV(sidx), &Jn);
+            J(g.jbase(m) + i) = Jn;
+            SA(sidx) = f.c_to_t(sa);
+        } else {
+            if constexpr (F::kIsFp) {
+                const T r = f.mmul(f.reduce96(acc[0]), f.rn3);
+                const C amp = lo.template dot<METRIC>(eL, r, mu);
+                result = amp == f.p ? 0u : amp;
             } else {
-                if constexpr (F::kIsFp) {
-                    const T r = f.mmul(f.reduce96(acc[0]), f.rn3);
-                    const C amp = lo.template dot<METRIC>(eL, r, mu);
-                    result = amp == f.p ? 0u : amp;
-                } else {
-                    result = lo.template dot<METRIC>(eL, acc[0], mu);
-                }
+                result = lo.template dot<METRIC>(eL, acc[0], mu);
             }
         }
+    };
+    if constexpr (G == 1) {
+#pragma unroll 1
+        for (int jj = 1; jj < N; ++jj) {
+#pragma unroll 1
+            for (int i = jj - 1; i >= 0; --i) range(jj - i + 1, i);
+        }
+    } else {
+#pragma unroll 1
+        for (int m = 2; m <= N; ++m) {
+#pragma unroll 1
+            for (int i = gi; i + m - 1 < N; i += G) range(m, i);
+            __syncwarp();
+        }
     }
-    if (mu == 0) {
+    if (mu == 0 && gi == 0) {
         st_once(static_cast<io_t*>(a.out) + u, (singular || violated) ? f.zero_io() : result);
         if (a.status != nullptr && h == 0) a.status[e] = violated ? 2 : singular ? 1 : 0;
     }
 }
 
-// One point per group of L lanes (L >= D_s: lanes beyond D_s hold zeros),
-// BLOCK / L points per block, grid-stride over the work items; the lane
-// table of the block in dynamic shared memory (LaneGeometry::words() x BLOCK
-// elements).
-template <class F, int L, int METRIC, int BLOCK>
+// One point per group of L lanes (L >= D_s: lanes beyond D_s hold zeros), or
+// per team of G such groups (one warp), BLOCK / (L G) points per block,
+// grid-stride over the work items; the tables of the block in dynamic shared
+// memory (LaneGeometry::words() x BLOCK / G elements).  A team's lanes run
+// the point loop together, so its barriers see the whole warp.
+template <class F, int L, int METRIC, int BLOCK, int G>
 __global__ void __launch_bounds__(BLOCK) bg_lanes_kernel(const F f, const CompactArgs a) {
-    constexpr int PPB = BLOCK / L;
+    constexpr int PPB = BLOCK / (L * G);
     extern __shared__ __align__(16) unsigned char bg_lane_smem[];
     const int64_t total = a.E * a.H;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * PPB;
-    for (int64_t u = static_cast<int64_t>(blockIdx.x) * PPB + threadIdx.x / L; u < total; u += stride)
-        lanes_point<F, L, METRIC, BLOCK>(f, a, bg_lane_smem, u);
+    for (int64_t u = static_cast<int64_t>(blockIdx.x) * PPB + threadIdx.x / (L * G); u < total; u += stride)
+        lanes_point<F, L, METRIC, BLOCK, G>(f, a, bg_lane_smem, u);
 }
 
 // Registry row of a lanes kernel.
 struct LanesEntry {
     int field;          // bg_field
-    int L;              // lanes per point (>= D_s)
+    int L;              // lanes per group (>= D_s)
+    int G;              // groups per point: 1, or 32 / L (a team of one warp)
     int metric;
     int block;          // threads per block
     int elem_bytes;     // sizeof(T)
@@ -337,10 +367,10 @@ struct LanesEntry {
     void (*launch)(const void* field_params, const void* args, dim3 grid, size_t smem, cudaStream_t stream);
 };
 
-template <class F, int L, int M, int B>
+template <class F, int L, int M, int B, int G>
 void launch_lanes(const void* fp, const void* args, dim3 grid, size_t smem, cudaStream_t s) {
-    bg_lanes_kernel<F, L, M, B><<<grid, B, smem, s>>>(*static_cast<const F*>(fp),
-                                                      *static_cast<const CompactArgs*>(args));
+    bg_lanes_kernel<F, L, M, B, G><<<grid, B, smem, s>>>(*static_cast<const F*>(fp),
+                                                         *static_cast<const CompactArgs*>(args));
 }
 
 // F_p: 128 threads (16 points) per block; complex: 64 threads (8 points),
@@ -351,15 +381,21 @@ constexpr int kBlockLanesC64 = 64;
 template <class F>
 void register_lanes(std::vector<LanesEntry>& v) {
     constexpr int B = F::kIsFp ? kBlockLanesFp : kBlockLanesC64;
-    auto add = [&](auto l, auto m) {
-        constexpr int L = decltype(l)::value, M = decltype(m)::value;
-        v.push_back(LanesEntry{F::kField, L, M, B, static_cast<int>(sizeof(typename F::T)),
-                               reinterpret_cast<const void*>(&bg_lanes_kernel<F, L, M, B>), &launch_lanes<F, L, M, B>});
+    auto add = [&](auto l, auto m, auto g) {
+        constexpr int L = decltype(l)::value, M = decltype(m)::value, G = decltype(g)::value;
+        v.push_back(LanesEntry{F::kField, L, G, M, B, static_cast<int>(sizeof(typename F::T)),
+                               reinterpret_cast<const void*>(&bg_lanes_kernel<F, L, M, B, G>),
+                               &launch_lanes<F, L, M, B, G>});
     };
-    add(std::integral_constant<int, 4>{}, std::integral_constant<int, 0>{});
-    add(std::integral_constant<int, 4>{}, std::integral_constant<int, 1>{});
-    add(std::integral_constant<int, 8>{}, std::integral_constant<int, 0>{});
-    add(std::integral_constant<int, 8>{}, std::integral_constant<int, 1>{});
+    using one = std::integral_constant<int, 1>;
+    add(std::integral_constant<int, 4>{}, std::integral_constant<int, 0>{}, one{});
+    add(std::integral_constant<int, 4>{}, std::integral_constant<int, 1>{}, one{});
+    add(std::integral_constant<int, 8>{}, std::integral_constant<int, 0>{}, one{});
+    add(std::integral_constant<int, 8>{}, std::integral_constant<int, 1>{}, one{});
+    add(std::integral_constant<int, 4>{}, std::integral_constant<int, 0>{}, std::integral_constant<int, 8>{});
+    add(std::integral_constant<int, 4>{}, std::integral_constant<int, 1>{}, std::integral_constant<int, 8>{});
+    add(std::integral_constant<int, 8>{}, std::integral_constant<int, 0>{}, std::integral_constant<int, 4>{});
+    add(std::integral_constant<int, 8>{}, std::integral_constant<int, 1>{}, std::integral_constant<int, 4>{});
 }
 
 }  // namespace bgk

@@ -92,7 +92,7 @@ extern "C" bg_status bg_eval_noalloc(const bg_plan* plan, int64_t E, const void*
     // in shared memory, so it needs no scratch at all.
     if (bgi::uses_lanes(plan, E * plan->H)) {
         if (bgi::fault(BG_FAULT_LAUNCH)) return bgi::fail(BG_ERR_CUDA, "launch failed: injected fault");
-        return bgi::launch_lanes(plan, E, momenta, eps, out, status, dev, stream);
+        return bgi::launch_lanes(plan, E, momenta, eps, out, status, dev, stream, E * plan->H);
     }
     // The compact kernel with its table in global memory, same dimensions and
     // metric as the plan's own kernel.

@@ -35,7 +35,7 @@ def main():
                           four_d=mask or 0)
         if table:
             os.environ["BG_TABLE"] = table
-        os.environ["BG_LANES"] = "1" if lanes else "0"
+        os.environ["BG_LANES"] = lanes if isinstance(lanes, str) else ("1" if lanes else "0")
         plan = bg.Plan(n, d, Ds, bg.FIELD_FP, p, metric, S, assign, four_dim_legs=mask)
         os.environ.pop("BG_TABLE", None)
         os.environ.pop("BG_LANES", None)
@@ -68,7 +68,7 @@ def main():
         nonlocal cases, mismatches
         k, e = G.c64_batch(200 + n * 10 + d, E, n, d, Ds, metric, workers=1)
         field = bg.FIELD_C64_REAL if real else bg.FIELD_C64
-        os.environ["BG_LANES"] = "1" if lanes else "0"
+        os.environ["BG_LANES"] = lanes if isinstance(lanes, str) else ("1" if lanes else "0")
         plan = bg.Plan(n, d, Ds, field, 0, metric)
         os.environ.pop("BG_LANES", None)
         kd = torch.from_numpy(np.ascontiguousarray(k.real if real else k)).cuda()
@@ -101,9 +101,10 @@ def main():
     fp_case(12, 8, 8, 0, P, None, mode="noalloc")
     fp_case(9, 6, 6, 0, P, None, mode="host")
     for n in (4, 8, 12):                         # lane-group kernel of small batches
-        fp_case(n, 4, 4, 1, PM, None, lanes=True)
-        fp_case(n, 5, 7, 0, P, None, lanes=True)
-        c64_case(n, 6, 6, 0, real=(n != 8), lanes=True)
+        for form in ("1", "2"):                  # one point per group, per team
+            fp_case(n, 4, 4, 1, PM, None, lanes=form)
+            fp_case(n, 5, 7, 0, P, None, lanes=form)
+            c64_case(n, 6, 6, 0, real=(n != 8), lanes=form)
     checked, violation = bg.bounds_report()
     print(json.dumps({"checked": checked, "violation": violation, "cases": cases, "mismatches": mismatches}))
 

@@ -57,7 +57,7 @@ def main():
     k, e = G.fp_batch(71, E, 7, 6, 6, P, 0, workers=1)
     ref, _ = C.amp_fp(k, e, P, 0)
     kb, eb = corrupt_fp(k, e[:, :, None, :], P)
-    for table, lanes in (("shared", "0"), ("global", "0"), ("global", "1")):
+    for table, lanes in (("shared", "0"), ("global", "0"), ("global", "1"), ("global", "2")):
         os.environ["BG_TABLE"] = table
         os.environ["BG_LANES"] = lanes
         plan = bg.Plan(7, 6, 6, bg.FIELD_FP, P, bg.MOSTLY_MINUS)
@@ -65,7 +65,8 @@ def main():
         os.environ.pop("BG_LANES")
         out, st = plan.eval(dev_u32(kb), dev_u32(eb[:, :, 0, :]))
         torch.cuda.synchronize()
-        record(f"fp_compact_{table}" if lanes == "0" else "fp_lanes", out.cpu().numpy().view(np.uint32), st, ref)
+        name = f"fp_compact_{table}" if lanes == "0" else "fp_lanes" if lanes == "1" else "fp_team"
+        record(name, out.cpu().numpy().view(np.uint32), st, ref)
     # F_p, uneven-batch kernel (the same point body inside the persistent kernel)
     plan = bg.Plan(7, 6, 6, bg.FIELD_FP, P, bg.MOSTLY_MINUS)
     out = torch.empty(E, dtype=torch.int32, device="cuda")

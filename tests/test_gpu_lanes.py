@@ -1,9 +1,11 @@
 """The lane-group kernel for small batches (one point per group of 4 or 8
-lanes, one vector component per lane): bit-exact against the oracle over F_p
-and within the complex tolerance of reading G8, for n = 4..12, every
-dimension pair, both metrics and primes, explicit state-assignment tables and
-singular points; the default choice takes it for small batches only, and the
-two kernels agree at the switch-over size."""
+lanes, one vector component per lane; or per team of the groups of a warp,
+which evaluate the ranges of each length in parallel): bit-exact against the
+oracle over F_p and within the complex tolerance of reading G8, for n =
+4..12, every dimension pair, both metrics and primes, explicit
+state-assignment tables and singular points, in both forms; the team form
+gives the group form's values bit for bit; the default choice takes them for
+small batches only, and the kernels agree at the switch-over size."""
 
 import os
 
@@ -20,7 +22,8 @@ P, PM = G.P_DEFAULT, G.P_MERSENNE
 
 
 class _lanes:
-    """BG_LANES for the plans created inside the block ("1" always, "0" never)."""
+    """BG_LANES for the plans created inside the block ("1" always, one point
+    per group; "2" always, one point per team; "0" never)."""
 
     def __init__(self, v):
         self.v = v
@@ -55,12 +58,16 @@ FP_CASES = [(4, 4, 4, 0, P), (5, 4, 6, 1, PM), (6, 6, 6, 0, P), (7, 5, 7, 0, P),
             (12, 8, 8, 1, PM)]
 
 
+MODES = ["1", "2"]                  # one point per group of lanes, per team
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("n,d,Ds,metric,p", FP_CASES)
-def test_lanes_fp_bit_exact(n, d, Ds, metric, p):
+def test_lanes_fp_bit_exact(n, d, Ds, metric, p, mode):
     from paper_2502_07060_gb300 import bg
     E = 3 * 16 + 5                              # several blocks of 16 points and a ragged tail
     k, e = G.fp_batch(1500 + 7 * n + d, E, n, d, Ds, p, metric, workers=1)
-    with _lanes("1"):
+    with _lanes(mode):
         plan = bg.Plan(n, d, Ds, bg.FIELD_FP, p, metric)
     assert "lanes=%d" % (4 if Ds <= 4 else 8) in plan.describe()
     out, st = _eval(plan, k, e)
@@ -70,42 +77,51 @@ def test_lanes_fp_bit_exact(n, d, Ds, metric, p):
 @pytest.mark.parametrize("field", ["c64", "c64r"])
 @pytest.mark.parametrize("n,d,Ds,metric", [(4, 4, 4, 0), (6, 6, 6, 1), (8, 6, 6, 0), (9, 4, 8, 0), (12, 8, 8, 0)])
 def test_lanes_complex_within_tolerance(field, n, d, Ds, metric):
+    """Both forms against the oracle; the team form equals the group form bit
+    for bit (every range runs the same operations in the same order)."""
     from paper_2502_07060_gb300 import bg
     E = 2 * 8 + 3
     k, e = G.c64_batch(1600 + 7 * n + d, E, n, d, Ds, metric, workers=1)
     fid = bg.FIELD_C64_REAL if field == "c64r" else bg.FIELD_C64
-    with _lanes("1"):
-        plan = bg.Plan(n, d, Ds, fid, 0, metric)
-    out, st = _eval(plan, np.ascontiguousarray(k.real) if field == "c64r" else k, e)
-    check_complex(out, st, k, e, metric)
+    kk = np.ascontiguousarray(k.real) if field == "c64r" else k
+    outs = []
+    for mode in MODES:
+        with _lanes(mode):
+            plan = bg.Plan(n, d, Ds, fid, 0, metric)
+        out, st = _eval(plan, kk, e)
+        check_complex(out, st, k, e, metric)
+        outs.append((out, st))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("field", ["fp", "c64"])
-def test_lanes_assignment_table(field):
+def test_lanes_assignment_table(field, mode):
     from paper_2502_07060_gb300 import bg
     n, d, S, E = 6, 4, 2, 21
     table = np.array([[(h >> l) & 1 for l in range(n)] for h in range(1 << n)], dtype=np.uint8)
     if field == "fp":
         k, e = G.fp_batch(1700, E, n, d, d, PM, 1, S=S, workers=1)
-        with _lanes("1"):
+        with _lanes(mode):
             plan = bg.Plan(n, d, d, bg.FIELD_FP, PM, bg.ALTERNATING, S, table)
         out, st = _eval(plan, k, e)
         check_fp(out, st, k, e, PM, 1, table)
     else:
         k, e = G.c64_batch(1700, E, n, d, d, 0, S=S, workers=1)
-        with _lanes("1"):
+        with _lanes(mode):
             plan = bg.Plan(n, d, d, bg.FIELD_C64, 0, bg.MOSTLY_MINUS, S, table)
         out, st = _eval(plan, k, e)
         check_complex(out, st, k, e, 0, table, max_widened=0.0)
 
 
-def test_lanes_singular_point():
+@pytest.mark.parametrize("mode", MODES)
+def test_lanes_singular_point(mode):
     from paper_2502_07060_gb300 import bg
     from tests.test_oracle_c import singular_fp_point
     k1, e1 = singular_fp_point(3, 8, 6, 6)
     k, e = G.fp_batch(5, 40, 8, 6, 6, workers=1)
     k[17], e[17] = k1[0], e1[0]
-    with _lanes("1"):
+    with _lanes(mode):
         plan = bg.Plan(8, 6, 6, bg.FIELD_FP, P)
     out, st = _eval(plan, k, e)
     assert st[17] == 1 and out[17] == 0

@@ -26,7 +26,7 @@ def test_checked_build_reports_broken_preconditions():
     assert r.returncode == 0, r.stderr[-3000:]
     rep = json.loads(r.stdout.strip().splitlines()[-1])
     assert rep["checked"], "the library loaded is not the checked build"
-    assert len(rep["cases"]) == 7
+    assert len(rep["cases"]) == 8
     for c in rep["cases"]:
         assert c["status2"] == [3, 7, 11, 13], c
         assert c["bad_out_zero"] and c["good_equal"] and c["good_status0"], c
