@@ -174,9 +174,13 @@ bg_status bg_workspace_size(const bg_plan* plan, int64_t E, size_t* bytes);
  * larger: bg_plan_describe's lanes_max_items -- run each item on a
  * group of 4 or 8 lanes, one vector component per lane, which shortens the
  * call when most of the GPU would otherwise idle (the flat part of the
- * time-against-points curve of Sec. 3.2).  Both give the same F_p residues;
- * complex results agree to rounding.  The environment variable BG_LANES=0
- * (never) or 1 (always) read at plan creation overrides the choice.
+ * time-against-points curve of Sec. 3.2); the smallest -- up to
+ * team_max_items, about 5 (F_p) or n - 5 (complex) items per warp scheduler
+ * -- on a team of the groups of one warp, which evaluate the ranges of each
+ * length in parallel.  All give the same F_p residues; complex results agree
+ * to rounding (the two lane forms bit for bit).  The environment variable
+ * BG_LANES=0 (never), 1 (always, one item per group) or 2 (always, one item
+ * per team) read at plan creation overrides the choice.
  * bg_eval_host and bg_eval_noalloc take the same kernel as bg_eval for the
  * same batch (bg_eval_host chooses by the whole batch, not by chunk).
  *

@@ -358,9 +358,13 @@ bool lanes_variant(bg_plan* pl, int L, int G, const bgk::LanesEntry** entry, siz
 }
 
 // One point per team (a warp of G = 32 / L groups evaluating the ranges of
-// each length in parallel) shortens a point's recursion further but takes
-// four to eight times the lanes per point: it serves batches up to one
-// resident wave of teams.  BG_LANES=2 takes the team form always.
+// each length in parallel) shortens a point's recursion further (measured on
+// GB300 up to 512 points: complex n = 8, d = 6 0.10 against 0.18 ms, n = 12,
+// d = 8 0.35 against 0.82 ms; F_p n = 12, d = 8 0.066 against 0.128 ms) but
+// takes G times the lanes per point, so it stops paying once the warps fill
+// the schedulers: at about 5 points per scheduler for F_p and n - 5 for the
+// complex fields (more ranges per length at larger n keep more of a team's
+// groups busy).  BG_LANES=2 takes the team form always.
 bg_status setup_lanes(bg_plan* pl) {
     const int L = round_dim(pl->Ds) <= 4 ? 4 : 8;
     if (!lanes_variant(pl, L, 1, &pl->lentry, &pl->lanes_smem, &pl->lanes_blocks_per_sm)) return BG_OK;
@@ -378,9 +382,10 @@ bg_status setup_lanes(bg_plan* pl) {
         const int64_t per_sm = pl->field == BG_FIELD_FP ? 24 : 16;
         pl->lanes_max_items = (pl->field == BG_FIELD_FP && pl->n < 7) ? 0
                             : std::max(per_sm * pl->sm_count, wave / 2);
-        if (pl->tentry && pl->lanes_max_items > 0)
-            pl->team_max_items = std::min(pl->lanes_max_items,
-                                          (int64_t)pl->team_blocks_per_sm * pl->sm_count * (pl->tentry->block / 32));
+        if (pl->tentry && pl->lanes_max_items > 0) {
+            const int64_t per_scheduler = pl->field == BG_FIELD_FP ? 5 : std::max(1, pl->n - 5);
+            pl->team_max_items = std::min(pl->lanes_max_items, per_scheduler * 4 * pl->sm_count);
+        }
     }
     return BG_OK;
 }
