@@ -167,14 +167,15 @@ def test_default_choice_and_switch_over(field):
     torch.cuda.synchronize()
 
 
-def test_lanes_host_pipeline_and_empty_batch():
+@pytest.mark.parametrize("mode", MODES)
+def test_lanes_host_pipeline_and_empty_batch(mode):
     """bg_eval_host with small chunks runs the lanes kernel per chunk; E = 0
     launches nothing."""
     import torch
     from paper_2502_07060_gb300 import bg
     n, d, E = 9, 6, 500
     k, e = G.fp_batch(1900, E, n, d, d, workers=1)
-    with _lanes("1"):
+    with _lanes(mode):
         plan = bg.Plan(n, d, d, bg.FIELD_FP, P)
     out = torch.empty(E, dtype=torch.int32).pin_memory()
     st = torch.empty(E, dtype=torch.uint8).pin_memory()

@@ -29,7 +29,8 @@ def _inputs(field, seed, E, n, d):
     return torch.from_numpy(k).cuda(), torch.from_numpy(e).cuda()
 
 
-@pytest.mark.parametrize("field,n,d,E", [("fp", 8, 6, 70000), ("fp", 12, 8, 3000), ("c64", 8, 6, 20000)])
+@pytest.mark.parametrize("field,n,d,E", [("fp", 8, 6, 70000), ("fp", 12, 8, 3000), ("c64", 8, 6, 20000),
+                                         ("fp", 12, 8, 300), ("c64", 8, 6, 200)])   # last two: one point per warp
 def test_noalloc_matches_bg_eval_on_two_calls(field, n, d, E):
     import torch
     plan = _plan(field, n, d)
