@@ -523,6 +523,28 @@ static bg_status create_plan(int n, int d, int D_s, bg_field field, uint32_t p, 
                 e.mixed == want_mixed)
                 best = &e;
         }
+        // F_p with D_s = 8 and the table in global scratch: the prefix sums, SA
+        // and 1/P^2 in shared memory (split) measured 3.7-7 % faster on GB300
+        // at n = 6..8 while it keeps the resident blocks per SM; from n = 9 it
+        // loses blocks and time, and at D_s = 6 it did not pay at n = 8.
+        if (!tenv && best && field == BG_FIELD_FP && DSk == 8 && !want_mixed && best->global_table && !best->split) {
+            const bgk::KernelEntry* sp = nullptr;
+            for (const auto& e : registry())
+                if (e.field == (int)field && e.D == Dk && e.DS == DSk && e.metric == (int)metric && e.split &&
+                    !e.mixed)
+                    sp = &e;
+            int dev = -1, occ_g = 0, occ_s = 0;
+            const size_t ssm = sp ? (size_t)geo.aux_words(Dk, DSk) * sp->block * sp->elem_bytes : 0;
+            const std::string kept = g_last_error;           // a refused smem limit is not this call's error
+            if (sp && cudaGetDevice(&dev) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_g, best->func, best->block, 0) == cudaSuccess &&
+                ssm <= 227 * 1024 && bgi::ensure_smem_limit(sp->func, dev, ssm) == BG_OK &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, sp->func, sp->block, ssm) == cudaSuccess &&
+                occ_s >= occ_g && occ_s > 0)
+                best = sp;
+            cudaGetLastError();
+            g_last_error = kept;
+        }
         if (best && best->split) words = geo.cur_words(DSk);
         if (!best)      // the complex fields have only the global placement, mixed F_p no split
             for (const auto& e : registry())

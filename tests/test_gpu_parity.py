@@ -121,6 +121,21 @@ def test_fp_split_placement_bit_exact(n, d, Ds, metric, p):
     assert np.array_equal(st, rst) and np.array_equal(out, ref)
 
 
+@pytest.mark.parametrize("n,d,expect", [(6, 8, "split"), (8, 7, "split"), (8, 6, "global"), (12, 8, "global")])
+def test_fp_default_placement(n, d, expect):
+    """Without BG_TABLE, F_p plans with D_s = 8 keep the prefix sums, SA and
+    1/P^2 in shared memory while that keeps the resident blocks of the global
+    placement (n <= 8 here), and the result is the oracle's."""
+    E = 2 * 97280 + 33                           # past one resident wave of threads
+    k, eps = G.fp_batch(900 + n + d, E, n, d, d, P, 0)
+    out, st, plan = run_fp(k, eps, P, 0)
+    assert f"table={expect}" in plan.describe(), plan.describe()
+    rng = np.random.default_rng(n)
+    sample = np.unique(np.concatenate([rng.choice(E, 1500, replace=False), np.arange(E - 64, E)]))
+    ref, rst = C.amp_fp(k[sample], eps[sample], P, 0)
+    assert np.array_equal(out[sample], ref) and np.array_equal(st[sample], rst)
+
+
 def c64_tolerance(k, eps, metric, hi, lo, spt=None):
     """Per-point tolerance of reading G8: 1e-10 max(|A|, S_pt) against the
     double-double value, widened only where FP64 itself cannot reach it: to 8x
