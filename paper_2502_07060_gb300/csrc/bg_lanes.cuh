@@ -20,6 +20,13 @@
 // [word][thread], so no lane ever reads another lane's words and only the
 // shuffles exchange data.  Per lane: NJ + (N+1) + 2 NS words (75 at n = 8).
 //
+// Teams (G = 32 / L groups, one warp, per point) serve the smallest batches:
+// the groups evaluate the ranges of each length in parallel and share one
+// table per team, lane mu of every group reading and writing the words of
+// component mu ([word][team][mu]); group 0 stages the inputs, prefix sums and
+// inverses, and a warp barrier separates the lengths.  Every range runs the
+// same operations as in a group of its own, so the values are identical.
+//
 // F_p: the same Montgomery levels as FpOps; a contraction sums the lanes'
 // products (L = 4: four products below 2^64; L = 8: each product first taken
 // to 33 bits by redc_full) and reduces twice, so every coefficient equals
